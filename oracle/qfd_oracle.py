@@ -1,0 +1,339 @@
+"""Plain, slow FP64 CPU oracle of the imaginary-time FFT solver of arXiv:2006.16935.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+baseline leg of bench.py may import this module.  The product path (the CUDA
+library under paper_2006_16935_gb300/csrc and its Python binding) never calls
+it and shares no code, table or constant generator with it.
+
+Everything is complex128 / float64 and follows the paper's notation:
+lattice of N points per axis, spacing A, mass M, time step EPS = dtau,
+kinetic term KINTERM in {1, 2, 3}.
+
+Sections and equations cited below are those of the paper:
+  Sec. 2.1  kinetic terms: Eq. (eigenmodes), Eqs. (HK1)-(HK3), FFT/IFFT definitions
+  Sec. 2.2  iterative procedure: Eq. (iter_proced) and the coefficients A, B
+  Sec. 2.4  parity projection: Eq. (parity)
+  Sec. 5.1  SNAPUPDATE (normalise + symmetrise cadence), TOLERANCE (stop rule)
+  Sec. 5.3  hard-coded potentials (harmonic oscillator, Coulomb, Cornell)
+
+Readings of points the paper leaves open (all listed in the design doc):
+  * energy estimator: Rayleigh quotient <psi|H_K + V|psi> / <psi|psi>
+  * V_b = V, V_s = 0 (Sec. 5.1 recommends this)
+  * relativistic term: rest_mass=1 keeps sqrt(p^2+M^2) as printed in Eq. (HK3);
+    rest_mass=0 subtracts M (the sqrt(p^2+m^2)-m form)
+  * lattice centre: on-grid site N/2 (reflection x -> (N-x) mod N) by default,
+    or the paper's off-grid (N-1)/2 (reflection x -> N-1-x)
+  * cadence: after every `ortho_every`-th step apply parity, then classical
+    Gram-Schmidt against the lower states, then normalise; energy every
+    `check_every` steps; stop when |E_t - E_prev| <= tol * |E_t|
+
+Pins (tests/test_oracle_pins.py): DFT against a brute-force textbook 3D DFT,
+numpy.fft, deltas, plane waves and Parseval; H_K(2) against the periodic
+7-point finite-difference Laplacian; H_K(3)^2 = 2M H_K(2) + M^2; H_K(1) on a
+band-limited Gaussian against the continuum Laplacian; the update on plane
+waves with constant V; the converged iteration against dense eigen-solvers of
+independently assembled matrices (ground state, parity sector, Gram-Schmidt
+deflated state); the 3D oscillator levels 3/2 w and 5/2 w; the heavy-mass
+limit; parity and orthogonality invariants.  No function here is unpinned.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Sec. 2.1: momenta, DFT, kinetic symbols
+# --------------------------------------------------------------------------
+
+
+def k_modes(n: int) -> np.ndarray:
+    """Eq. (eigenmodes): k = A p for DFT index j; k = 2 pi j / N for j <= N/2,
+    2 pi (j - N) / N otherwise, so k lies in (-pi, pi] with Nyquist at +pi."""
+    j = np.arange(n)
+    m = np.where(j <= n // 2, j, j - n)
+    return 2.0 * np.pi * m / n
+
+
+def dft_matrix(n: int, sign: int) -> np.ndarray:
+    """F[j, k] = exp(sign * 2 pi i * (j k mod N) / N).
+
+    The exponent is reduced modulo N in integers before the angle is formed,
+    so every entry is one of the N roots of unity."""
+    j = np.arange(n)
+    m = np.outer(j, j) % n
+    ang = 2.0 * np.pi * m / n
+    return np.cos(ang) + 1j * sign * np.sin(ang)
+
+
+def dft_axis(x: np.ndarray, axis: int, sign: int) -> np.ndarray:
+    """Unnormalised 1D DFT along `axis`: X[k] = sum_j x[j] exp(sign 2 pi i j k / N)
+    (Sec. 2.1, FFT/IFFT definitions; sign -1 forward, +1 inverse)."""
+    n = x.shape[axis]
+    f = dft_matrix(n, sign)
+    y = np.tensordot(f, x, axes=([1], [axis]))  # new axis 0 = k
+    return np.moveaxis(y, 0, axis)
+
+
+def fft3(x: np.ndarray, method: str = "naive") -> np.ndarray:
+    """FFT[Psi](k) = sum_x Psi(x) exp(-i k.x), unnormalised (Sec. 2.1).
+
+    method 'naive' applies the DFT definition axis by axis; 'library' calls
+    numpy.fft.fftn (a library FFT, used only at lattice sizes where the naive
+    transform is too slow)."""
+    if method == "library":
+        return np.fft.fftn(x)
+    y = x.astype(np.complex128)
+    for ax in range(3):
+        y = dft_axis(y, ax, -1)
+    return y
+
+
+def ifft3(x: np.ndarray, method: str = "naive") -> np.ndarray:
+    """IFFT[Psi~](x) = sum_k Psi~(k) exp(+i k.x), unnormalised (Sec. 2.1)."""
+    if method == "library":
+        return np.fft.ifftn(x, norm="forward")
+    y = x.astype(np.complex128)
+    for ax in range(3):
+        y = dft_axis(y, ax, +1)
+    return y
+
+
+def kinetic_symbol(n: int, a: float, mass: float, kinterm: int, rest_mass: int = 0) -> np.ndarray:
+    """T(k1, k2, k3) on the [N, N, N] grid of DFT indices, without the 1/N^3.
+
+    Eq. (HK1):  T = sum_l k_l^2 / (2 A^2 M)
+    Eq. (HK2):  T = 4 sum_l sin^2(k_l / 2) / (2 A^2 M)
+    Eq. (HK3):  T = sqrt(4 sum_l sin^2(k_l / 2) + (A M)^2) / A   [- M if rest_mass == 0]
+    """
+    k = k_modes(n)
+    k1, k2, k3 = np.meshgrid(k, k, k, indexing="ij")
+    if kinterm == 1:
+        return (k1 ** 2 + k2 ** 2 + k3 ** 2) / (2.0 * a * a * mass)
+    s = 4.0 * (np.sin(k1 / 2) ** 2 + np.sin(k2 / 2) ** 2 + np.sin(k3 / 2) ** 2)
+    if kinterm == 2:
+        return s / (2.0 * a * a * mass)
+    if kinterm == 3:
+        t = np.sqrt(s + (a * mass) ** 2) / a
+        return t if rest_mass else t - mass
+    raise ValueError(f"kinetic term {kinterm} is not an FFT kinetic term")
+
+
+def kinetic_max(n: int, a: float, mass: float, kinterm: int, rest_mass: int = 0) -> float:
+    """Largest eigenvalue of H_K on the lattice (max of T over the modes)."""
+    return float(np.max(kinetic_symbol(n, a, mass, kinterm, rest_mass)))
+
+
+def apply_kinetic(psi: np.ndarray, T: np.ndarray, method: str = "naive") -> np.ndarray:
+    """H_K Psi = (1/N^3) IFFT[T * FFT[Psi]]  (Eqs. HK1-HK3)."""
+    n3 = psi.size
+    return ifft3(T * fft3(psi, method), method) / n3
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: the iterative procedure
+# --------------------------------------------------------------------------
+
+
+def update_coefficients(V: np.ndarray, dtau: float):
+    """A = (1 - dtau V/2) / (1 + dtau V/2),  B = 1 / (1 + dtau V/2)  (Sec. 2.2)."""
+    h = 0.5 * dtau * V
+    return (1.0 - h) / (1.0 + h), 1.0 / (1.0 + h)
+
+
+def imaginary_time_step(psi, V, T, dtau, method="naive"):
+    """Eq. (iter_proced): Psi(tau + dtau) = A Psi(tau) - B dtau H_K Psi(tau)."""
+    A, B = update_coefficients(V, dtau)
+    return A * psi - B * dtau * apply_kinetic(psi, T, method)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.4: parity; Sec. 2.2 / 5.1: Gram-Schmidt, normalisation, energy
+# --------------------------------------------------------------------------
+
+
+def reflect(psi: np.ndarray, centre: str = "grid") -> np.ndarray:
+    """Psi(-r) on the lattice: r measured from the potential's centre.
+
+    centre 'grid': centre at site N/2, so x -> (N - x) mod N.
+    centre 'offgrid': centre at (N-1)/2, so x -> N - 1 - x."""
+    n = psi.shape[0]
+    if centre == "grid":
+        idx = (n - np.arange(n)) % n
+    elif centre == "offgrid":
+        idx = n - 1 - np.arange(n)
+    else:
+        raise ValueError(centre)
+    return psi[np.ix_(idx, idx, idx)]
+
+
+def parity_project(psi, parity: int, centre: str = "grid"):
+    """Eq. (parity): P+- Psi(r) = (Psi(r) +- Psi(-r)) / 2; parity 0 leaves Psi alone."""
+    if parity == 0:
+        return psi
+    return 0.5 * (psi + parity * reflect(psi, centre))
+
+
+def inner(u, v) -> complex:
+    """<u|v> = sum_x conj(u(x)) v(x)."""
+    return complex(np.vdot(u.ravel(), v.ravel()))
+
+
+def gram_schmidt(psi, lower):
+    """Classical Gram-Schmidt: Psi <- Psi - sum_j <phi_j|Psi> phi_j, all overlaps
+    taken from the same input Psi (the lower states phi_j are orthonormal)."""
+    coeffs = [inner(phi, psi) for phi in lower]
+    out = psi.copy()
+    for c, phi in zip(coeffs, lower):
+        out = out - c * phi
+    return out
+
+
+def norm2(psi) -> float:
+    return float(np.sum(np.abs(psi) ** 2))
+
+
+def normalize(psi):
+    """Sum over the full lattice of |Psi|^2 = 1 (Sec. 2.2)."""
+    return psi / math.sqrt(norm2(psi))
+
+
+def energy(psi, V, T, method="naive") -> float:
+    """Rayleigh quotient <Psi|H_K + V|Psi> / <Psi|Psi> (energy estimator reading)."""
+    hk = apply_kinetic(psi, T, method)
+    num = inner(psi, hk + V * psi)
+    return num.real / norm2(psi)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.3: potentials (the synthetic workloads' forms)
+# --------------------------------------------------------------------------
+
+
+def displacement(n: int, centre: str = "grid") -> np.ndarray:
+    """Lattice displacement from the centre, per axis, in lattice units.
+
+    'grid': d = x - N/2 in [-N/2, N/2 - 1]; 'offgrid': d = x - (N-1)/2."""
+    x = np.arange(n, dtype=np.float64)
+    return x - (n // 2) if centre == "grid" else x - (n - 1) / 2.0
+
+
+def radius(n: int, a: float, centre: str = "grid") -> np.ndarray:
+    d = displacement(n, centre)
+    d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+    return a * np.sqrt(d1 * d1 + d2 * d2 + d3 * d3)
+
+
+def potential(n: int, a: float, kind: str, params=(), centre: str = "grid") -> np.ndarray:
+    """V(r) on the lattice, r = A |x - centre|.
+
+    'zero':      V = 0                                  (POTENTIAL 0)
+    'ho':        V = k r^2 / 2,   params (k,)           (POTENTIAL 4, read as +r^2/2)
+    'cornell':   V = -kappa / r + sigma r, r >= A/2     (POTENTIAL 6 without string breaking)
+    'coulomb':   V = -1 / r, r >= A/2                   (POTENTIAL 2 clamped at the origin)
+    'softcoul':  V = -1 / sqrt(r^2 + eps2), params (eps2,)
+    """
+    r = radius(n, a, centre)
+    if kind == "zero":
+        return np.zeros_like(r)
+    if kind == "ho":
+        k = params[0] if params else 1.0
+        return 0.5 * k * r * r
+    if kind == "cornell":
+        kappa, sigma = params
+        rc = np.maximum(r, 0.5 * a)
+        return -kappa / rc + sigma * rc
+    if kind == "coulomb":
+        rc = np.maximum(r, 0.5 * a)
+        return -1.0 / rc
+    if kind == "softcoul":
+        eps2 = params[0] if params else 0.01
+        return -1.0 / np.sqrt(r * r + eps2)
+    raise ValueError(kind)
+
+
+# --------------------------------------------------------------------------
+# The solve loop (Sec. 2.2 evolution; Sec. 5.1 SNAPUPDATE / TOLERANCE cadence)
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Problem:
+    n: int
+    a: float
+    mass: float
+    dtau: float
+    kinterm: int
+    V: np.ndarray
+    rest_mass: int = 0
+    centre: str = "grid"
+    ortho_every: int = 10
+    check_every: int = 100
+    method: str = "naive"
+    T: np.ndarray = field(default=None, repr=False)
+
+    def __post_init__(self):
+        if self.T is None:
+            self.T = kinetic_symbol(self.n, self.a, self.mass, self.kinterm, self.rest_mass)
+
+
+def cadence(psi, prob: Problem, parity: int, lower):
+    """Parity projection, then Gram-Schmidt against the lower states, then normalisation."""
+    psi = parity_project(psi, parity, prob.centre)
+    if lower:
+        psi = gram_schmidt(psi, lower)
+    return normalize(psi)
+
+
+def evolve(psi, prob: Problem, nsteps: int, t0: int = 0, parity: int = 0, lower=()):
+    """Advance nsteps steps of Eq. (iter_proced) from step counter t0; after each
+    step t with t % ortho_every == 0 apply the cadence.  Returns (psi, t)."""
+    t = t0
+    for _ in range(nsteps):
+        psi = imaginary_time_step(psi, prob.V, prob.T, prob.dtau, prob.method)
+        t += 1
+        if t % prob.ortho_every == 0:
+            psi = cadence(psi, prob, parity, lower)
+    return psi, t
+
+
+@dataclass
+class StateResult:
+    energy: float
+    psi: np.ndarray
+    steps: int
+    converged: bool
+    history: list
+
+
+def solve_state(psi0, prob: Problem, max_steps: int, tol: float, parity: int = 0, lower=()):
+    """One state: cadence at t = 0, then steps; every check_every steps the energy
+    is taken and the loop stops once |E_t - E_prev| <= tol |E_t| (tol < 0: never)."""
+    psi = cadence(psi0.astype(np.complex128), prob, parity, lower)
+    t = 0
+    e_prev = None
+    hist = []
+    converged = False
+    while t < max_steps:
+        psi, t = evolve(psi, prob, prob.check_every, t, parity, lower)
+        e = energy(psi, prob.V, prob.T, prob.method)
+        hist.append((t, e))
+        if tol >= 0 and e_prev is not None and abs(e - e_prev) <= tol * abs(e):
+            converged = True
+            break
+        e_prev = e
+    return StateResult(e, normalize(psi), t, converged, hist)
+
+
+def solve_states(psi0s, prob: Problem, max_steps: int, tol: float, parities=None):
+    """Ground and excited states in turn; state i is Gram-Schmidt deflated
+    against the converged states 0..i-1 (each normalised)."""
+    out = []
+    lower = []
+    for i, p0 in enumerate(psi0s):
+        par = 0 if parities is None else parities[i]
+        res = solve_state(p0, prob, max_steps, tol, par, tuple(lower))
+        out.append(res)
+        lower.append(res.psi)
+    return out

@@ -1,0 +1,410 @@
+"""Pins for the FP64 oracle against things other than itself.
+
+Each test fixes a part of oracle/qfd_oracle.py by a closed form, a brute-force
+computation, a library routine, or a dense eigen-solver applied to a matrix
+assembled here independently of the oracle's FFT code.  A plausible mistake
+(a dropped term, a wrong sign, index or mode mapping, a transposed operand)
+fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qfd_oracle as O
+from paper_2006_16935_gb300 import inputs
+
+RNG = np.random.default_rng(12345)
+
+
+def rand_psi(n, seed=0):
+    return inputs.uniform_psi(n, seed)
+
+
+# ----------------------------------------------------------------- DFT ----
+
+def test_k_modes_match_eigenmode_set():
+    # Eq. (eigenmodes): {-pi + 2pi/N, ..., 0, 2pi/N, ..., pi}
+    for n in (4, 6, 8, 12):
+        expect = np.array([2 * math.pi * m / n for m in range(-n // 2 + 1, n // 2 + 1)])
+        assert np.allclose(np.sort(O.k_modes(n)), expect, atol=1e-15)
+        assert O.k_modes(n)[n // 2] == pytest.approx(math.pi)  # Nyquist is +pi
+
+
+def test_dft_delta_and_shifted_delta():
+    n = 6
+    x = np.zeros((n, n, n), complex)
+    x[0, 0, 0] = 1
+    assert np.allclose(O.fft3(x), 1.0, atol=1e-15)
+    x0 = (1, 4, 5)
+    x = np.zeros((n, n, n), complex)
+    x[x0] = 1
+    j = np.arange(n)
+    j1, j2, j3 = np.meshgrid(j, j, j, indexing="ij")
+    expect = np.exp(-2j * np.pi * (j1 * x0[0] + j2 * x0[1] + j3 * x0[2]) / n)
+    assert np.allclose(O.fft3(x), expect, atol=1e-13)
+
+
+def test_dft_plane_wave_gives_scaled_delta():
+    n = 8
+    nvec = (3, 4, 7)
+    j = np.arange(n)
+    j1, j2, j3 = np.meshgrid(j, j, j, indexing="ij")
+    pw = np.exp(2j * np.pi * (nvec[0] * j1 + nvec[1] * j2 + nvec[2] * j3) / n)
+    X = O.fft3(pw)
+    expect = np.zeros_like(X)
+    expect[nvec] = n ** 3
+    assert np.max(np.abs(X - expect)) < 1e-10
+
+
+def test_dft_against_bruteforce_textbook_3d_dft():
+    # O(N^6) sum with the full phase exp(-2 pi i k.x / N) formed at once
+    n = 5
+    x = rand_psi(n, 3)
+    idx = np.array(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")).reshape(3, -1)
+    phase = np.exp(-2j * np.pi * (idx.T @ idx) / n)  # [k, x]
+    X = (phase @ x.ravel()).reshape(n, n, n)
+    assert np.max(np.abs(O.fft3(x) - X)) < 1e-11
+    Xi = (np.conj(phase) @ x.ravel()).reshape(n, n, n)
+    assert np.max(np.abs(O.ifft3(x) - Xi)) < 1e-11
+
+
+def test_dft_against_numpy_fft_and_library_mode():
+    n = 16
+    x = rand_psi(n, 4)
+    assert np.max(np.abs(O.fft3(x) - np.fft.fftn(x))) < 1e-10
+    assert np.max(np.abs(O.ifft3(x) - np.fft.ifftn(x) * n ** 3)) < 1e-10
+    assert np.max(np.abs(O.fft3(x, "library") - O.fft3(x))) < 1e-10
+    assert np.max(np.abs(O.ifft3(x, "library") - O.ifft3(x))) < 1e-10
+
+
+def test_parseval_and_roundtrip():
+    n = 8
+    x = rand_psi(n, 5)
+    X = O.fft3(x)
+    assert np.sum(np.abs(X) ** 2) == pytest.approx(n ** 3 * np.sum(np.abs(x) ** 2), rel=1e-13)
+    assert np.max(np.abs(O.ifft3(X) - n ** 3 * x)) < 1e-10
+
+
+# ------------------------------------------------------ kinetic terms ----
+
+def fd_laplacian_kinetic(psi, a, mass):
+    """Periodic 7-point finite-difference kinetic term -(1/2M) Lap_lattice."""
+    out = 6 * psi
+    for ax in range(3):
+        out = out - np.roll(psi, 1, ax) - np.roll(psi, -1, ax)
+    return out / (2 * mass * a * a)
+
+
+@pytest.mark.parametrize("n", [6, 8])
+def test_HK2_equals_periodic_finite_difference_laplacian(n):
+    a, m = 0.3, 1.7
+    psi = rand_psi(n, 6)
+    T = O.kinetic_symbol(n, a, m, 2)
+    assert np.max(np.abs(O.apply_kinetic(psi, T) - fd_laplacian_kinetic(psi, a, m))) < 1e-11
+
+
+def test_HK3_squared_is_2M_HK2_plus_M2():
+    n, a, m = 8, 0.2, 2.5
+    psi = rand_psi(n, 7)
+    T2 = O.kinetic_symbol(n, a, m, 2)
+    T3 = O.kinetic_symbol(n, a, m, 3, rest_mass=1)
+    lhs = O.apply_kinetic(O.apply_kinetic(psi, T3), T3)
+    rhs = 2 * m * fd_laplacian_kinetic(psi, a, m) + m * m * psi
+    assert np.max(np.abs(lhs - rhs)) < 1e-10
+    # rest mass subtracted: (H3' + M)^2 = 2M H2 + M^2
+    T3s = O.kinetic_symbol(n, a, m, 3, rest_mass=0)
+    h = O.apply_kinetic(psi, T3s) + m * psi
+    lhs = O.apply_kinetic(h, T3s) + m * h
+    assert np.max(np.abs(lhs - rhs)) < 1e-10
+    del T2
+
+
+def test_HK1_on_band_limited_gaussian_is_continuum_laplacian():
+    # psi = exp(-r^2 / (2 s^2)): -Lap psi = (3/s^2 - r^2/s^4) psi; band-limited at
+    # a = 0.25 (e^-79 at k = pi/a) and periodic to e^-32 at the box edge
+    n, a, m, s = 64, 0.25, 1.3, 1.0
+    r = O.radius(n, a)
+    psi = np.exp(-r * r / (2 * s * s)).astype(complex)
+    T = O.kinetic_symbol(n, a, m, 1)
+    hk = O.apply_kinetic(psi, T)
+    expect = (3 / s ** 2 - r * r / s ** 4) * psi / (2 * m)
+    assert np.max(np.abs(hk - expect)) < 1e-11
+
+
+def test_plane_waves_are_eigenvectors_incl_nyquist():
+    n, a, m = 8, 0.15, 1.2
+    j = np.arange(n)
+    j1, j2, j3 = np.meshgrid(j, j, j, indexing="ij")
+    for kin in (1, 2, 3):
+        T = O.kinetic_symbol(n, a, m, kin)
+        for nvec in [(0, 0, 0), (4, 4, 4), (1, 6, 4), (7, 2, 3)]:
+            pw = np.exp(2j * np.pi * (nvec[0] * j1 + nvec[1] * j2 + nvec[2] * j3) / n)
+            kk = [2 * math.pi * (v if v <= n // 2 else v - n) / n for v in nvec]
+            if kin == 1:
+                lam = sum(k * k for k in kk) / (2 * a * a * m)
+            else:
+                s = sum(4 * math.sin(k / 2) ** 2 for k in kk)
+                lam = s / (2 * a * a * m) if kin == 2 else math.sqrt(s + (a * m) ** 2) / a - m
+            assert np.max(np.abs(O.apply_kinetic(pw, T) - lam * pw)) < 1e-10 * max(1, lam)
+
+
+def test_heavy_mass_limit_per_mode():
+    # sqrt(M^2 + 2 M T2) - M = T2 - T2^2 / (2M) + O(T2^3 / M^2)
+    n, a = 8, 0.1
+    for m in (10.0, 100.0, 1000.0):
+        T2 = O.kinetic_symbol(n, a, m, 2)
+        T3 = O.kinetic_symbol(n, a, m, 3, rest_mass=0)
+        rem = T3 - (T2 - T2 ** 2 / (2 * m))
+        assert np.all(np.abs(rem) <= 0.5 * T2 ** 3 / m ** 2 + 1e-12 * m)
+
+
+# ------------------------------------------------------------- update ----
+
+def test_step_on_plane_wave_with_constant_potential():
+    n, a, m, dt, v0 = 8, 0.2, 1.0, 0.003, 2.5
+    j = np.arange(n)
+    j1, j2, j3 = np.meshgrid(j, j, j, indexing="ij")
+    pw = np.exp(2j * np.pi * (1 * j1 + 3 * j2 + 4 * j3) / n)
+    T = O.kinetic_symbol(n, a, m, 2)
+    V = np.full((n, n, n), v0)
+    lam_T = T[1, 3, 4]
+    out = O.imaginary_time_step(pw, V, T, dt)
+    h = dt * v0 / 2
+    assert np.max(np.abs(out - ((1 - h) / (1 + h) - dt * lam_T / (1 + h)) * pw)) < 1e-13
+
+
+# -------------------------------------------------- dense eigen pins ----
+
+def kron3(m1):
+    n = m1.shape[0]
+    i = np.eye(n)
+    return np.kron(np.kron(m1, i), i) + np.kron(np.kron(i, m1), i) + np.kron(np.kron(i, i), m1)
+
+
+def dense_HK(n, a, m, kin, rest_mass=0):
+    """Dense H_K assembled without the oracle's DFT code."""
+    l1 = 2 * np.eye(n) - np.roll(np.eye(n), 1, 0) - np.roll(np.eye(n), -1, 0)
+    h2 = kron3(l1) / (2 * m * a * a)
+    if kin == 2:
+        return h2
+    if kin == 3:
+        w, u = np.linalg.eigh(h2)
+        h3 = (u * np.sqrt(2 * m * w.clip(min=0) + m * m)) @ u.T
+        return h3 if rest_mass else h3 - m * np.eye(n ** 3)
+    # kin 1: K[x, x'] = (1/N) sum_m (2 pi m / N)^2 cos(2 pi m (x - x') / N)
+    freqs = np.fft.fftfreq(n) * n
+    d = np.subtract.outer(np.arange(n), np.arange(n))
+    k1 = sum((2 * np.pi * f / n) ** 2 * np.cos(2 * np.pi * f * d / n) for f in freqs) / n
+    return kron3(k1) / (2 * m * a * a)
+
+
+def aniso_ho(n, a):
+    d = O.displacement(n)
+    d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+    return 0.5 * a * a * (1.0 * d1 ** 2 + 3.0 * d2 ** 2 + 6.0 * d3 ** 2)
+
+
+def converge(psi, prob, parity=0, lower=(), tol=1e-13, max_steps=20000):
+    psi = O.cadence(psi, prob, parity, lower)
+    for _ in range(max_steps):
+        nxt = O.imaginary_time_step(psi, prob.V, prob.T, prob.dtau)
+        nxt = O.parity_project(nxt, parity, prob.centre)
+        if lower:
+            nxt = O.gram_schmidt(nxt, lower)
+        lam = O.inner(psi, nxt).real
+        nxt = O.normalize(nxt)
+        if np.max(np.abs(nxt - psi)) < tol:
+            return nxt, lam
+        psi = nxt
+    raise AssertionError("oracle iteration did not converge")
+
+
+@pytest.mark.parametrize("kin", [1, 2, 3])
+def test_fixed_point_matches_dense_eigensolver(kin):
+    # (1 - lam) / dtau is the lowest eigenvalue of H_K + ((1 + lam) / 2) V and
+    # psi its eigenvector (derived from Eq. (iter_proced) with the A, B of Sec. 2.2)
+    n, a, m, dt = 6, 0.5, 1.0, 0.02
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=1)
+    psi, lam = converge(rand_psi(n, 8), prob)
+    c = (1 + lam) / 2
+    H = dense_HK(n, a, m, kin) + c * np.diag(V.ravel())
+    w, u = np.linalg.eigh(H)
+    assert (1 - lam) / dt == pytest.approx(w[0], rel=1e-11)
+    assert abs(np.vdot(u[:, 0], psi.ravel())) == pytest.approx(1.0, abs=1e-10)
+    # Rayleigh quotient against the dense matrix (energy estimator pin)
+    Hfull = dense_HK(n, a, m, kin) + np.diag(V.ravel())
+    rq = np.vdot(psi.ravel(), Hfull @ psi.ravel()).real
+    assert O.energy(psi, V, prob.T) == pytest.approx(rq, rel=1e-12)
+
+
+def test_parity_sector_fixed_point_is_lowest_odd_eigenvector():
+    n, a, m, dt = 6, 0.5, 1.0, 0.02
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, 2, V, ortho_every=1)
+    psi, lam = converge(rand_psi(n, 9), prob, parity=-1)
+    c = (1 + lam) / 2
+    H = dense_HK(n, a, m, 2) + c * np.diag(V.ravel())
+    w, u = np.linalg.eigh(H)
+    # parity of each eigenvector under the lattice reflection x -> (N - x) mod N
+    R = np.eye(n ** 3)[O.reflect(np.arange(n ** 3).reshape(n, n, n)).ravel()]
+    par = np.einsum("ij,ik,kj->j", u, R, u)
+    odd = np.where(par < -0.5)[0]
+    assert (1 - lam) / dt == pytest.approx(w[odd[0]], rel=1e-11)
+    assert abs(np.vdot(u[:, odd[0]], psi.ravel())) == pytest.approx(1.0, abs=1e-10)
+    assert np.linalg.norm(O.parity_project(psi, +1)) < 1e-13
+
+
+def test_gram_schmidt_deflated_fixed_point_is_dominant_eigenvector_of_QMQ():
+    n, a, m, dt = 6, 0.5, 1.0, 0.02
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, 1, V, ortho_every=1)
+    phi0, _ = converge(rand_psi(n, 10), prob)
+    psi, lam = converge(rand_psi(n, 11), prob, lower=(phi0,))
+    A, B = (1 - dt * V / 2) / (1 + dt * V / 2), 1 / (1 + dt * V / 2)
+    Mstep = np.diag(A.ravel()) - dt * np.diag(B.ravel()) @ dense_HK(n, a, m, 1)
+    q = np.eye(n ** 3) - np.outer(phi0.ravel(), phi0.ravel().conj())
+    w, u = np.linalg.eig(q @ Mstep @ q)
+    top = np.argmax(w.real)
+    assert lam == pytest.approx(w[top].real, rel=1e-12)
+    assert abs(np.vdot(u[:, top] / np.linalg.norm(u[:, top]), psi.ravel())) == pytest.approx(1.0, abs=1e-9)
+    assert abs(O.inner(phi0, psi)) < 1e-13
+
+
+def test_rayleigh_energy_bias_is_second_order_in_dtau():
+    n, a, m = 6, 0.5, 1.0
+    V = aniso_ho(n, a)
+    e_true = np.linalg.eigvalsh(dense_HK(n, a, m, 2) + np.diag(V.ravel()))[0]
+    errs = []
+    for dt in (0.04, 0.02):
+        prob = O.Problem(n, a, m, dt, 2, V, ortho_every=1)
+        psi, _ = converge(rand_psi(n, 12), prob)
+        errs.append(O.energy(psi, V, prob.T) - e_true)
+    assert errs[0] > 0 and errs[1] > 0
+    assert errs[0] / errs[1] == pytest.approx(4.0, rel=0.1)
+
+
+# ------------------------------------------------ oscillator closed form ----
+
+def self_consistent_c(dt, level):
+    """c = (1 + lam) / 2 with lam = 1 - dt * level * sqrt(c) (oscillator, M = k = 1)."""
+    c = 1.0
+    for _ in range(200):
+        c = 1.0 - 0.5 * dt * level * math.sqrt(c)
+    return c
+
+
+@pytest.mark.parametrize("level", [1.5, 2.5])
+def test_oscillator_levels_one_step(level):
+    # H1 on N=64, A=0.25 equals the continuum for band-limited Gaussians: the
+    # exact fixed point exp(-w r^2/2) (times x for 5/2 w), w = sqrt(c), is mapped
+    # to lam * psi with lam = 1 - dt * level * w
+    n, a, dt = 64, 0.25, 0.004
+    c = self_consistent_c(dt, level)
+    w = math.sqrt(c)
+    r = O.radius(n, a)
+    psi = np.exp(-w * r * r / 2).astype(complex)
+    if level == 2.5:
+        d = O.displacement(n) * a
+        psi = psi * d[:, None, None]
+    V = O.potential(n, a, "ho", (1.0,))
+    T = O.kinetic_symbol(n, a, 1.0, 1)
+    out = O.imaginary_time_step(psi, V, T, dt)
+    lam = 1 - dt * level * w
+    assert np.max(np.abs(out - lam * psi)) < 1e-12 * np.max(np.abs(psi))
+    # Rayleigh energy of the fixed point: <H> = level w + (1 - c) <V> / c
+    e = O.energy(psi, V, T)
+    ev = (level / 2) * w / c  # virial: <V_c> = level w / 2 for V_c = c r^2 / 2
+    assert e == pytest.approx(level * w + (1 - c) * ev, rel=1e-11)
+
+
+# --------------------------------------------------------- parity / GS ----
+
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+def test_parity_projector_algebra(centre):
+    n = 8
+    psi = rand_psi(n, 13)
+    pp = O.parity_project(psi, +1, centre)
+    pm = O.parity_project(psi, -1, centre)
+    assert np.max(np.abs(pp + pm - psi)) < 1e-15
+    assert np.max(np.abs(O.parity_project(pp, +1, centre) - pp)) < 1e-15
+    assert abs(O.inner(pp, pm)) < 1e-12
+    assert O.norm2(pp) + O.norm2(pm) == pytest.approx(O.norm2(psi), rel=1e-14)
+    assert np.max(np.abs(O.reflect(O.reflect(psi, centre), centre) - psi)) == 0
+
+
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+def test_step_preserves_parity_sector_for_symmetric_potential(centre):
+    n, a, m, dt = 8, 0.2, 1.0, 0.002
+    V = O.potential(n, a, "cornell", (0.3, 0.2), centre)
+    assert np.max(np.abs(O.reflect(V, centre) - V)) == 0
+    for kin in (1, 2, 3):
+        T = O.kinetic_symbol(n, a, m, kin)
+        for par in (+1, -1):
+            psi = O.parity_project(rand_psi(n, 14), par, centre)
+            out = O.imaginary_time_step(psi, V, T, dt)
+            assert np.linalg.norm(O.parity_project(out, -par, centre)) < 1e-13 * np.linalg.norm(out)
+
+
+def test_gram_schmidt_leaves_no_overlap():
+    n = 8
+    phis = []
+    for s in range(3):
+        p = O.gram_schmidt(rand_psi(n, 20 + s), phis)
+        phis.append(O.normalize(p))
+    for i in range(3):
+        for j in range(3):
+            assert abs(O.inner(phis[i], phis[j]) - (i == j)) < 1e-13
+
+
+# ---------------------------------------------------------- potentials ----
+
+def test_potential_values_by_hand():
+    n, a = 8, 0.1
+    # centre site (4,4,4): r = 0, clamped to a/2 for the singular forms
+    assert O.potential(n, a, "ho")[4, 4, 4] == 0.0
+    assert O.potential(n, a, "cornell", (0.3, 0.2))[4, 4, 4] == pytest.approx(-0.3 / 0.05 + 0.2 * 0.05)
+    assert O.potential(n, a, "softcoul", (0.01,))[4, 4, 4] == pytest.approx(-10.0)
+    # corner site (0,0,0): displacement (-4,-4,-4), r = 0.1 sqrt(48)
+    r = 0.1 * math.sqrt(48)
+    assert O.potential(n, a, "ho")[0, 0, 0] == pytest.approx(0.5 * r * r)
+    assert O.potential(n, a, "cornell", (0.3, 0.2))[0, 0, 0] == pytest.approx(-0.3 / r + 0.2 * r)
+    assert O.potential(n, a, "softcoul", (0.01,))[0, 0, 0] == pytest.approx(-1 / math.sqrt(r * r + 0.01))
+    # site (5,4,3): displacement (1,0,-1)
+    assert O.potential(n, a, "ho")[5, 4, 3] == pytest.approx(0.5 * 0.02)
+    # off-grid centre 3.5: site (0,0,0) has displacement -3.5 per axis
+    assert O.potential(n, a, "ho", centre="offgrid")[0, 0, 0] == pytest.approx(0.5 * 3 * 0.35 ** 2)
+
+
+# ------------------------------------------------------------ solve loop ----
+
+def test_solve_state_stop_rule_and_step_count():
+    n, a, m, dt = 6, 0.5, 1.0, 0.05
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, 2, V, ortho_every=5, check_every=20)
+    res = O.solve_state(rand_psi(n, 30), prob, max_steps=4000, tol=1e-12)
+    assert res.converged and res.steps % 20 == 0
+    (t1, e1), (t2, e2) = res.history[-2:]
+    assert abs(e2 - e1) <= 1e-12 * abs(e2)
+    assert abs(res.history[-3][1] - e1) > 1e-12 * abs(e1)
+    assert O.norm2(res.psi) == pytest.approx(1.0, rel=1e-14)
+    # negative tolerance runs exactly to max_steps (rounded up to check_every)
+    res2 = O.solve_state(rand_psi(n, 30), prob, max_steps=50, tol=-1)
+    assert res2.steps == 60 and not res2.converged
+
+
+def test_solve_states_orders_energies_and_orthogonalises():
+    n, a, m, dt = 6, 0.5, 1.0, 0.05
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, 2, V, ortho_every=1, check_every=50)
+    res = O.solve_states([rand_psi(n, 40 + i) for i in range(3)], prob, 20000, 1e-13)
+    es = [r.energy for r in res]
+    assert es[0] < es[1] < es[2]
+    w = np.linalg.eigvalsh(dense_HK(n, a, m, 2) + np.diag(V.ravel()))
+    # each level within the O(dtau) iteration bias of the exact spectrum
+    for e, ex in zip(es, w[:3]):
+        assert abs(e - ex) < 0.02 * abs(ex)
+    for i in range(3):
+        for j in range(i):
+            assert abs(O.inner(res[i].psi, res[j].psi)) < 1e-12
