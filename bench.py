@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Site-updates/s of the imaginary-time FFT solver on one GB300 (arXiv:2006.16935).
+
+Workload (the 512^3 softened-Coulomb ground-state solve): N = 512, A = 0.05,
+M = 1, V = -1/sqrt(r^2 + 0.01) about the grid centre, the lattice sin^2
+kinetic term H_K(2) (Eq. HK2), dtau = 5e-4, uniform seeded start (seed 3),
+even parity.  One bench step = 10 imaginary-time steps of Eq. (iter_proced)
+(forward 3D FFT, T(k) multiply, inverse 3D FFT, A/B update, FP64 norm
+partials), then the cadence (parity projection + normalisation) and an energy
+check (Parseval <H_K> + <V>, FP64), i.e. every row of the hot path once.
+site-updates = N^3 * imaginary-time steps.
+
+Default: complex128 (`--precision c128`).  `--precision c64` times the complex64
+bulk arithmetic; `--solve` additionally runs the full ground-state solve to
+|dE|/|E| <= 1e-9 in complex128 and in complex64 + complex128 refinement.
+
+Multi-GPU: independent replicas (one whole solve per GPU, no collective on
+the data path); the only collectives are the barrier and the max over ranks of
+the timed region.
+
+`--impl reference` times the FP64 CPU oracle (library FFT) on the host cores on
+the same workload, one imaginary-time step per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N, A, MASS, DTAU, KIN, SEED = 512, 0.05, 1.0, 5e-4, 2, 3
+POT = ("softcoul", (0.01,))
+STEPS_PER_BENCH_STEP = 10
+METRIC = "site-updates/s at 512^3 (imaginary-time FFT step, softened Coulomb, H_K(2))"
+UNIT = "site-updates/s"
+
+# algorithmic bytes per site of one launch of each pass (reads + writes of the
+# lattices the pass must touch; complex128 / complex64) and FP64/FP32 flops per site
+PASS_BYTES = {
+    "c128": {"update_x": 80.0, "fwd_y": 32.0, "z_kinetic": 32.0, "inv_y": 32.0, "fwd_x": 48.0,
+             "gs_apply": 48.0},
+    "c64": {"update_x": 40.0, "fwd_y": 16.0, "z_kinetic": 16.0, "inv_y": 16.0, "fwd_x": 24.0,
+            "gs_apply": 24.0},
+}
+
+
+def fft_flops_per_point(n: int) -> float:
+    """Real flops per point of one length-n transform of the radix-8/4/2 plan:
+    a radix-8 butterfly is 56 adds/muls plus 7 twiddle products (6 flops each)
+    except in the first stage; radix 4 = 16 + 3*6, radix 2 = 4 + 6."""
+    p = int(round(np.log2(n)))
+    rad = [8] * (p // 3) + ([2] if p % 3 == 1 else [4] if p % 3 == 2 else [])
+    tot = 0.0
+    for s, r in enumerate(rad):
+        core = {8: 56, 4: 16, 2: 4}[r]
+        tw = 0 if s == 0 else 6 * (r - 1)
+        tot += (core + tw) / r
+    return tot
+
+
+def pass_flops(n: int):
+    f = fft_flops_per_point(n)
+    return {"update_x": 2 * f + 8 + 3, "fwd_y": f, "z_kinetic": 2 * f + 6 + 2, "inv_y": f, "fwd_x": f + 3,
+            "gs_apply": 8}
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 / FP32 vector peaks (no tensor cores): nominal GB300 figures from the
+# profiling recipe: FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def oracle_step_rate(steps: int):
+    """Times `steps` oracle imaginary-time steps of the workload (library FFT, all cores)."""
+    from oracle import qfd_oracle as O
+    from paper_2006_16935_gb300 import inputs
+
+    V = O.potential(N, A, POT[0], POT[1])
+    prob = O.Problem(N, A, MASS, DTAU, KIN, V, ortho_every=STEPS_PER_BENCH_STEP, method="library")
+    psi = inputs.uniform_psi(N, SEED)
+    times = []
+    t = 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        psi, t = O.evolve(psi, prob, 1, t, parity=1)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    times = oracle_step_rate(args.warmup + args.steps)[args.warmup:]
+    tot = sum(times)
+    value = N ** 3 * len(times) / tot
+    sample = (f"{len(times)} oracle imaginary-time steps of the 512^3 workload (library FFT on all cores), "
+              f"after {args.warmup} warm-up steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": workload_config(args, "c128"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, prec):
+    return {"workload": f"{N}^3 softened-Coulomb ground state, H_K(2), dtau={DTAU}, even parity",
+            "n": N, "a": A, "mass": MASS, "dtau": DTAU, "kinetic": KIN, "potential": "-1/sqrt(r^2+0.01)",
+            "precision": prec, "imaginary_steps_per_step": STEPS_PER_BENCH_STEP,
+            "cadence": "parity + normalise + energy check every 10 steps",
+            "l2": "inputs larger than L2 (one 512^3 lattice = %.2f GB)" % (N ** 3 * (16 if prec == "c128" else 8) / 1e9),
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def time_precision(torch, Q, args, prec, dev, want_roofline):
+    stream = torch.cuda.current_stream(dev)
+    plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=STEPS_PER_BENCH_STEP,
+                  check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP * max(1, args.warmup), tol=-1,
+                  stream=stream.cuda_stream)
+    plan.fill_potential(*POT)
+    plan.fill_psi_uniform(0, SEED)
+    es, _, _ = plan.solve_states(1, [1])  # warm-up: W bench steps
+    plan.set_limits(STEPS_PER_BENCH_STEP * args.steps, -1)
+    plan.fill_psi_uniform(0, SEED)
+    plan.timing(want_roofline)
+    plan.timing_reset()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    es, steps, _ = plan.solve_states(1, [1])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    launches = plan.launch_count()
+    per_pass = {}
+    if want_roofline:
+        for k in Q.PASS_KINDS:
+            cnt, tot = plan.timing_query(k)
+            if cnt:
+                per_pass[k] = {"launches": cnt, "total_ms": tot}
+    plan.timing(False)
+    return plan, ms, steps[0], es[0], launches, per_pass
+
+
+def roofline_for(prec, per_pass, peaks):
+    dom = max(per_pass, key=lambda k: per_pass[k]["total_ms"])
+    cnt, tot = per_pass[dom]["launches"], per_pass[dom]["total_ms"]
+    avg_s = tot / cnt / 1e3
+    sites = float(N) ** 3
+    bytes_launch = PASS_BYTES[prec].get(dom, 32.0) * sites
+    flops_launch = pass_flops(N).get(dom, 0.0) * sites
+    hbm = bytes_launch / avg_s / 1e9
+    alu_peak = FP64_PEAK_TFLOPS if prec == "c128" else FP32_PEAK_TFLOPS
+    alu = flops_launch / avg_s / 1e12
+    hbm_frac = hbm / peaks["hbm_gbs"]
+    alu_frac = alu / alu_peak
+    if prec == "c128" and alu_frac > hbm_frac:
+        r = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
+             "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (profiling recipe); no tensor cores used"}
+    else:
+        r = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+             "peak_source": "hbm_gbs of MEASURED_PEAKS.json (of measured)"}
+    r.update({"kernel": dom, "traffic": None, "avg_launch_ms": 1e3 * avg_s,
+              "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
+              "hbm_gbs_achieved": hbm, "hbm_frac": hbm_frac, "alu_tflops_achieved": alu,
+              "share_of_step": tot / sum(v["total_ms"] for v in per_pass.values())})
+    return r
+
+
+def e2e_rate(torch, Q, args, prec, dev):
+    """Same metric through the public API with host buffers: every bench step
+    copies psi from pinned host memory in (qfd_set_psi) and reads the energy
+    back (qfd_solve_states returns it to the host)."""
+    from paper_2006_16935_gb300 import inputs
+
+    stream = torch.cuda.current_stream(dev)
+    host = torch.from_numpy(inputs.uniform_psi(N, SEED).reshape(-1)).pin_memory()
+    plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=STEPS_PER_BENCH_STEP,
+                  check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP, tol=-1,
+                  stream=stream.cuda_stream)
+    plan.fill_potential(*POT)
+    for _ in range(max(1, args.warmup)):
+        plan.set_psi(0, host)
+        plan.solve_states(1, [1])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.set_psi(0, host)
+        es, _, _ = plan.solve_states(1, [1])
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    plan.close()
+    return {"value": float(N) ** 3 * STEPS_PER_BENCH_STEP * args.steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(host.numel() * 16), "d2h_bytes_per_step": 8 + 8,
+            "api": "qfd_set_psi(pinned host) + qfd_solve_states(10 steps) -> energy"}
+
+
+def run_qfd(args):
+    import torch
+
+    from paper_2006_16935_gb300 import build
+    from paper_2006_16935_gb300 import qfd as Q
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        build.build_library()
+    if world > 1:
+        dist.barrier()
+    peaks, peak_src = read_peaks()
+    prec = args.precision
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    plan, ms, steps, energy, launches, per_pass = time_precision(torch, Q, args, prec, dev, True)
+    clk = clocks.stop()
+    plan.close()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_units = float(N) ** 3 * steps * world
+    value = total_units / (ms / 1e3)
+    e2e = e2e_rate(torch, Q, args, prec, dev)
+    if world > 1:
+        t = torch.tensor([e2e["value"]], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        e2e["value"] = float(t.item()) * world
+    other = "c64" if prec == "c128" else "c128"
+    _, ms_o, steps_o, _, _, per_pass_o = time_precision(torch, Q, args, other, dev, True)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded uniform start, analytic potential)",
+        "config": workload_config(args, prec),
+        "roofline": roofline_for(prec, per_pass, peaks),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "energy_at_end": energy,
+        "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass.items()},
+        "peaks_source": peak_src,
+        other: {"value": float(N) ** 3 * steps_o / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
+                "roofline": roofline_for(other, per_pass_o, peaks),
+                "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass_o.items()}},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        if mem_available_gb() > 24:
+            times = oracle_step_rate(2)
+            t = min(times)
+            line["cpu_baseline"] = {"value": float(N) ** 3 / t, "unit": UNIT, "cores": cores_used(),
+                                    "kind": "oracle",
+                                    "sample": "1 oracle imaginary-time step of the 512^3 workload (library FFT, "
+                                              "all cores), best of 2"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                                    "sample": "skipped: less than 24 GB host memory available"}
+    if args.solve:
+        line["solve"] = full_solves(torch, Q, dev)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+    return 0
+
+
+def full_solves(torch, Q, dev):
+    """Ground state to |dE|/|E| <= 1e-9 in complex128 and in complex64 + refinement."""
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("c128", "c64_refine"):
+        plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=10, check_every=100, max_steps=400000,
+                      tol=1e-9, tol_bulk=1e-7, stream=stream.cuda_stream)
+        plan.fill_potential(*POT)
+        plan.fill_psi_uniform(0, SEED)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        es, steps, conv = plan.solve_states(1, [1], allow_unconverged=True)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        out[prec] = {"energy": es[0], "steps": steps[0], "converged": conv, "seconds": dt,
+                     "solves_per_s": 1.0 / dt, "site_updates_per_s": float(N) ** 3 * steps[0] / dt,
+                     **plan.stats(0)}
+        plan.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["qfd", "reference"], default="qfd")
+    ap.add_argument("--precision", choices=["c128", "c64"], default="c128")
+    ap.add_argument("--solve", action="store_true", help="also run the full 1e-9 solves (minutes)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qfd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * qfd.h - C ABI of the GB300 imaginary-time Schroedinger solver with FFT
+ * kinetic terms (arXiv:2006.16935, "quantumfdtd v3").
+ *
+ * The library evolves a wave-function psi on an N^3 periodic lattice with
+ * spacing A by the imaginary-time step of Sec. 2.2, Eq. (iter_proced):
+ *
+ *     psi(tau + dtau) = A psi(tau) - B dtau H_K psi(tau),
+ *     A = (1 - dtau V/2) / (1 + dtau V/2),   B = 1 / (1 + dtau V/2),
+ *
+ * where H_K is one of the FFT kinetic terms of Sec. 2.1, Eqs. (HK1)-(HK3),
+ * applied as (1/N^3) IFFT[T(k) FFT[psi]] with the unnormalised transforms of
+ * Sec. 2.1 and the momenta k_l of Eq. (eigenmodes).  Every SNAPUPDATE-like
+ * cadence (`ortho_every` steps, Sec. 5.1) the state is parity projected
+ * (Eq. (parity)), Gram-Schmidt deflated against the lower states and
+ * normalised to sum |psi|^2 = 1; every `check_every` steps the Rayleigh
+ * energy <psi|H_K + V|psi>/<psi|psi> is taken, and a solve stops once two
+ * successive energies agree to |dE| <= tol |E| (TOLERANCE, Sec. 5.1).
+ *
+ * Conventions for every entry point:
+ *  - Lattice arrays are row-major [x][y][z] (z fastest), N^3 sites, indexed
+ *    with 64-bit integers.  Complex arrays are interleaved (re, im) doubles.
+ *  - Pointers flagged `on_device` = 1 are CUDA device pointers of the current
+ *    device, otherwise host pointers (pinned host memory makes copies async).
+ *    Caller buffers are only read or written during the call; the library
+ *    copies inputs and owns all of its device memory.
+ *  - All work is ordered on the plan's CUDA stream (`qfd_params.stream`, or a
+ *    stream the plan creates).  Calls that return values to the host
+ *    synchronise that stream before returning.
+ *  - Every call returns a qfd_status; nothing aborts.  After an error,
+ *    qfd_last_error() describes it.  A plan is used by one host thread at a time.
+ *  - Only lattices N in {8, 16, 32, 64, 128, 256, 512, 1024} are supported.
+ */
+#ifndef QFD_H
+#define QFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qfd_plan_s* qfd_plan_t;
+
+typedef enum {
+  QFD_OK = 0,
+  QFD_ERR_ARG = -1,           /* invalid argument or unsupported size */
+  QFD_ERR_OOM = -2,           /* device allocation failed */
+  QFD_ERR_UNSTABLE_DT = -3,   /* dtau * max T(k) >= 2, or 1 + dtau V/2 <= 0 somewhere */
+  QFD_ERR_DIVERGED = -4,      /* energy or norm became non-finite */
+  QFD_ERR_TIMEOUT = -5,       /* reserved for bounded waits */
+  QFD_ERR_CUDA = -6,          /* a CUDA call failed */
+  QFD_ERR_NOT_CONVERGED = -7, /* max_steps reached before the tolerance */
+  QFD_ERR_STATE = -8          /* call out of order (e.g. stepping before a potential is set) */
+} qfd_status;
+
+/* Kinetic terms, numbered as the paper's KINTERM (Sec. 5.1). */
+enum { QFD_KIN_P2 = 1, QFD_KIN_SIN2 = 2, QFD_KIN_REL = 3 };
+/* Arithmetic of the steps: complex128; complex64; complex64 bulk followed by a
+ * complex128 refinement of the same iteration (reductions are FP64 in all). */
+enum { QFD_C128 = 0, QFD_C64 = 1, QFD_C64_REFINE = 2 };
+/* Parity projection of a state (Eq. (parity)): none, P+, P-. */
+enum { QFD_PAR_NONE = 0, QFD_PAR_EVEN = 1, QFD_PAR_ODD = -1 };
+/* Potential centre (Sec. 1.3 / 5.3): the grid site (N/2, N/2, N/2) with the
+ * reflection x -> (N - x) mod N, or the paper's off-grid point (N-1)/2 with
+ * x -> N - 1 - x. */
+enum { QFD_CENTRE_GRID = 0, QFD_CENTRE_OFFGRID = 1 };
+/* Analytic potentials of qfd_fill_potential (r = A |x - centre|):
+ *  ZERO      V = 0
+ *  HO        V = c0 r^2 / 2                       (harmonic oscillator, Sec. 5.3 item 4)
+ *  CORNELL   V = -c0 / r + c1 r, r >= A/2          (Cornell, Sec. 5.3 item 6, no string breaking)
+ *  COULOMB   V = -1 / r, r >= A/2                  (Sec. 5.3 item 2)
+ *  SOFTCOUL  V = -1 / sqrt(r^2 + c0)               (softened Coulomb) */
+enum { QFD_POT_ZERO = 0, QFD_POT_HO = 1, QFD_POT_CORNELL = 2, QFD_POT_COULOMB = 3, QFD_POT_SOFTCOUL = 4 };
+
+typedef struct {
+  int64_t n;            /* lattice points per axis (NUM) */
+  double a;             /* lattice spacing A (> 0) */
+  double mass;          /* mass M (> 0) */
+  double dtau;          /* imaginary time step EPS (> 0) */
+  int32_t kinetic;      /* QFD_KIN_* */
+  int32_t rest_mass;    /* HK3 only: 1 keeps sqrt(p^2 + M^2) of Eq. (HK3); 0 subtracts M */
+  int32_t nstates;      /* capacity of the state stack (1..8) */
+  int32_t precision;    /* QFD_C128, QFD_C64 or QFD_C64_REFINE */
+  int32_t ortho_every;  /* steps between parity / Gram-Schmidt / normalisation (>= 1) */
+  int32_t check_every;  /* steps between energy checks in qfd_solve_states (>= 1) */
+  int32_t centre;       /* QFD_CENTRE_* */
+  int32_t reserved;     /* must be 0 */
+  int64_t max_steps;    /* per state (per phase for QFD_C64_REFINE) */
+  double tol;           /* relative energy tolerance of the final phase (< 0: run max_steps) */
+  double tol_bulk;      /* relative energy tolerance of the complex64 bulk phase */
+  void* stream;         /* cudaStream_t to order all work on, or NULL for a plan-owned stream */
+} qfd_params;
+
+/* Creates a plan: checks the parameters, allocates every device buffer
+ * (state stack, one work lattice, potential and update coefficients,
+ * twiddles and per-axis kinetic tables) and rejects an unstable time step:
+ * dtau * max_k T(k) >= 2 gives QFD_ERR_UNSTABLE_DT (the highest mode of the
+ * update would not decay).  Sections 2.1-2.2. *out is NULL on failure. */
+qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out);
+
+/* Releases the plan and its device memory (NULL is ignored). */
+void qfd_destroy(qfd_plan_t plan);
+
+/* Message of the last error on `plan` (or of the last failed qfd_plan call of
+ * this thread when plan is NULL).  Owned by the library. */
+const char* qfd_last_error(qfd_plan_t plan);
+
+/* Copies a real potential V (N^3 doubles, [x][y][z]) and derives the update
+ * coefficients A, B of Sec. 2.2 on the device.  V_b = V, V_s = 0 (Sec. 5.1).
+ * QFD_ERR_UNSTABLE_DT if 1 + dtau V / 2 <= 0 or V is non-finite somewhere. */
+qfd_status qfd_set_potential(qfd_plan_t plan, const double* V, int on_device);
+
+/* Fills one of the QFD_POT_* potentials on the device (coefficients c0, c1 as
+ * listed at the enum; ncoeffs of them are read), then derives A, B as
+ * qfd_set_potential does. */
+qfd_status qfd_fill_potential(qfd_plan_t plan, int kind, const double* coeffs, int ncoeffs);
+
+/* Copies the potential V the plan holds (N^3 doubles) into the caller's buffer. */
+qfd_status qfd_get_potential(qfd_plan_t plan, double* V, int on_device);
+
+/* Copies state `state` in (interleaved complex128, N^3 sites) and resets its
+ * step counter.  In complex64 plans the values are rounded to complex64. */
+qfd_status qfd_set_psi(qfd_plan_t plan, int state, const double* psi, int on_device);
+
+/* Fills state `state` on the device with Re, Im i.i.d. U[-1, 1) from the
+ * counter-based SplitMix64 stream: value(site, part) = 2 u - 1 with
+ * u = (splitmix64(seed * 0x9E3779B97F4A7C15 ^ (2 site + part)) >> 11) 2^-53
+ * (part 0 = Re, 1 = Im); resets the step counter. */
+qfd_status qfd_fill_psi_uniform(qfd_plan_t plan, int state, uint64_t seed);
+
+/* Copies state `state` out (interleaved complex128) into the caller's buffer. */
+qfd_status qfd_get_psi(qfd_plan_t plan, int state, double* out, int on_device);
+
+/* Parity sector applied to `state` at every cadence (QFD_PAR_*). */
+qfd_status qfd_set_parity(qfd_plan_t plan, int state, int parity);
+
+/* Advances `state` by nsteps steps of Eq. (iter_proced).  After every step t
+ * of the state's counter with t % ortho_every == 0 the state is parity
+ * projected, Gram-Schmidt deflated against states 0..state-1 (which must be
+ * normalised) and normalised.  Steps in the plan's current arithmetic
+ * (complex64 for QFD_C64 and, before a refinement, QFD_C64_REFINE). */
+qfd_status qfd_step(qfd_plan_t plan, int state, int64_t nsteps);
+
+/* Rayleigh energy <psi|H_K + V|psi> / <psi|psi> of `state` (FP64 sums;
+ * <psi|H_K|psi> by Parseval, (1/N^3) sum_k T(k) |FFT psi|^2) and its squared
+ * norm sum |psi|^2.  Either output may be NULL. */
+qfd_status qfd_energy(qfd_plan_t plan, int state, double* E, double* norm2);
+
+/* Solves states 0..nstates-1 in turn from their current contents: state i is
+ * parity projected with parity[i] (parity may be NULL), deflated against the
+ * converged states 0..i-1, stepped until the relative energy change between
+ * two checks is <= tol (or max_steps), and left normalised.  For
+ * QFD_C64_REFINE each state first runs in complex64 to tol_bulk, then in
+ * complex128 to tol.  E_out[i] receives the final energy and steps_out[i]
+ * the total number of steps (both may be NULL).  Returns
+ * QFD_ERR_NOT_CONVERGED (outputs still filled) if a state reached
+ * max_steps, QFD_ERR_DIVERGED on a non-finite energy. */
+qfd_status qfd_solve_states(qfd_plan_t plan, int nstates, const int* parity, double* E_out, int64_t* steps_out);
+
+/* Replaces the plan's max_steps, tol and tol_bulk (same meaning as in
+ * qfd_params) for later qfd_solve_states calls. */
+qfd_status qfd_set_limits(qfd_plan_t plan, int64_t max_steps, double tol, double tol_bulk);
+
+/* Per-state statistics of the last qfd_solve_states: steps spent in
+ * complex64 and complex128 and the energy at the end of the complex64 phase
+ * (NaN if none).  Any output may be NULL. */
+qfd_status qfd_get_stats(qfd_plan_t plan, int state, int64_t* steps_c64, int64_t* steps_c128, double* e_bulk);
+
+/* Kernel timing: when enabled, every kernel launch of the plan is bracketed
+ * by CUDA events on the plan's stream.  qfd_timing_query synchronises and
+ * returns, for the pass kind (0 update-x, 1 forward-y, 2 z kinetic,
+ * 3 inverse-y, 4 forward-x, 5 GS overlaps, 6 GS apply, 7 reductions,
+ * 8 other), the number of launches and their summed duration in ms since the
+ * last reset.  qfd_launch_count returns all kernel launches since the reset. */
+qfd_status qfd_timing_enable(qfd_plan_t plan, int enable);
+qfd_status qfd_timing_reset(qfd_plan_t plan);
+qfd_status qfd_timing_query(qfd_plan_t plan, int kind, int64_t* launches, double* total_ms);
+int64_t qfd_launch_count(qfd_plan_t plan);
+
+/* The plan's CUDA stream (cudaStream_t) for event recording by the caller. */
+void* qfd_get_stream(qfd_plan_t plan);
+
+/* Blocks until all work queued on the plan's stream has finished. */
+qfd_status qfd_sync(qfd_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFD_H */

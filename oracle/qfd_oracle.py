@@ -43,6 +43,21 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+try:  # library FFT (multi-threaded) for the large-lattice mode
+    import scipy.fft as _libfft
+
+    def _lib_fftn(x):
+        return _libfft.fftn(x, workers=-1)
+
+    def _lib_ifftn_unnormalised(x):
+        return _libfft.ifftn(x, norm="forward", workers=-1)
+except ImportError:  # pragma: no cover
+    def _lib_fftn(x):
+        return np.fft.fftn(x)
+
+    def _lib_ifftn_unnormalised(x):
+        return np.fft.ifftn(x, norm="forward")
+
 # --------------------------------------------------------------------------
 # Sec. 2.1: momenta, DFT, kinetic symbols
 # --------------------------------------------------------------------------
@@ -80,10 +95,10 @@ def fft3(x: np.ndarray, method: str = "naive") -> np.ndarray:
     """FFT[Psi](k) = sum_x Psi(x) exp(-i k.x), unnormalised (Sec. 2.1).
 
     method 'naive' applies the DFT definition axis by axis; 'library' calls
-    numpy.fft.fftn (a library FFT, used only at lattice sizes where the naive
-    transform is too slow)."""
+    scipy.fft.fftn on all cores (a library FFT, used only at lattice sizes
+    where the naive transform is too slow)."""
     if method == "library":
-        return np.fft.fftn(x)
+        return _lib_fftn(x)
     y = x.astype(np.complex128)
     for ax in range(3):
         y = dft_axis(y, ax, -1)
@@ -93,7 +108,7 @@ def fft3(x: np.ndarray, method: str = "naive") -> np.ndarray:
 def ifft3(x: np.ndarray, method: str = "naive") -> np.ndarray:
     """IFFT[Psi~](x) = sum_k Psi~(k) exp(+i k.x), unnormalised (Sec. 2.1)."""
     if method == "library":
-        return np.fft.ifftn(x, norm="forward")
+        return _lib_ifftn_unnormalised(x)
     y = x.astype(np.complex128)
     for ax in range(3):
         y = dft_axis(y, ax, +1)

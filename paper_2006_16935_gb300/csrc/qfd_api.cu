@@ -1,0 +1,907 @@
+// C ABI and plan runtime of the imaginary-time FFT solver (see include/qfd.h).
+//
+// The runtime keeps, per plan, a stack of states, one work lattice W and a
+// small state machine recording how far the current step's passes have run on
+// W, so that an energy check reuses the next step's forward passes instead of
+// transforming psi again.  All arithmetic of the method runs in the kernels of
+// qfd_kernels.cuh and the small kernels below; the host only sequences
+// launches, sets up tables and takes the convergence decision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qfd.h"
+#include "qfd_kernels.cuh"
+#include "qfd_launch.h"
+
+using namespace qfd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Stage { ST_NONE = 0, ST_X = 1, ST_XY = 2, ST_C = 3, ST_D = 4 };
+// device scalar slots
+enum { SC_SUMS = 0, SC_N2 = 40, SC_PV = 41, SC_PT = 42, SC_SCALE = 43, SC_E = 44, SC_COUNT = 64 };
+enum { OP_SUMS = 0, OP_NORM = 1, OP_N2PV = 2, OP_ENERGY = 3 };
+constexpr int GS_BLOCKS = 4 * 152;
+constexpr int FIN_THREADS = 1024;
+
+}  // namespace
+
+// ============================================================ small kernels
+namespace qfd {
+
+__global__ void __launch_bounds__(FIN_THREADS)
+k_finalize_op(const double* __restrict__ part, int nq, int count, double* __restrict__ scal, int op) {
+  __shared__ double red[32];
+  __shared__ double sums[2 * MAX_LOWER];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < nq; ++q) {
+    double x = 0.0;
+    for (int i = threadIdx.x; i < count; i += FIN_THREADS) x += part[(int64_t)q * count + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      double y = red[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+      if (lane == 0) sums[q] = y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (op == OP_SUMS) {
+      for (int q = 0; q < nq; ++q) scal[SC_SUMS + q] = sums[q];
+    } else if (op == OP_NORM || op == OP_N2PV) {
+      scal[SC_N2] = sums[0];
+      scal[SC_PV] = sums[1];
+      if (op == OP_NORM) scal[SC_SCALE] = 1.0 / sqrt(sums[0]);
+    } else if (op == OP_ENERGY) {
+      scal[SC_PT] = sums[0];
+      scal[SC_E] = (sums[0] + scal[SC_PV]) / scal[SC_N2];
+    }
+  }
+}
+
+// Analytic potentials (r = A |x - centre|, see QFD_POT_*).
+__global__ void k_potential(double* __restrict__ V, int64_t n, double a, int kind, double c0, double c1,
+                            int offgrid) {
+  const int64_t n3 = n * n * n;
+  const double cen = offgrid ? 0.5 * (double)(n - 1) : (double)(n / 2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double dz = (double)(i % n) - cen, dy = (double)((i / n) % n) - cen, dx = (double)(i / (n * n)) - cen;
+    const double r = a * sqrt(dx * dx + dy * dy + dz * dz);
+    double v = 0.0;
+    if (kind == QFD_POT_HO) {
+      v = 0.5 * c0 * r * r;
+    } else if (kind == QFD_POT_CORNELL) {
+      const double rc = fmax(r, 0.5 * a);
+      v = -c0 / rc + c1 * rc;
+    } else if (kind == QFD_POT_COULOMB) {
+      v = -1.0 / fmax(r, 0.5 * a);
+    } else if (kind == QFD_POT_SOFTCOUL) {
+      v = -1.0 / sqrt(r * r + c0);
+    }
+    V[i] = v;
+  }
+}
+
+// Update coefficients of Sec. 2.2 from V: complex128 {A, B dtau}, complex64
+// {B dtau, 1 - A} (1 - A = dtau V B formed in FP64 before rounding).
+__global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double2* __restrict__ c64,
+                       float2* __restrict__ c32, int* __restrict__ bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = V[i];
+    const double h = 0.5 * dtau * v;
+    const double den = 1.0 + h;
+    if (!(den > 0.0) || !isfinite(v)) atomicOr(bad, 1);
+    const double A = (1.0 - h) / den, B = 1.0 / den;
+    if (c64) c64[i] = double2{A, B * dtau};
+    if (c32) c32[i] = float2{(float)(B * dtau), (float)(dtau * v * B)};
+  }
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename C>
+__global__ void k_fill_uniform(C* __restrict__ psi, int64_t n3, uint64_t seed) {
+  const uint64_t base = seed * 0x9E3779B97F4A7C15ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t z0 = splitmix64(base ^ (uint64_t)(2 * i)), z1 = splitmix64(base ^ (uint64_t)(2 * i + 1));
+    const double u0 = (double)(z0 >> 11) * 0x1.0p-53, u1 = (double)(z1 >> 11) * 0x1.0p-53;
+    psi[i] = C{(decltype(C().x))(2.0 * u0 - 1.0), (decltype(C().x))(2.0 * u1 - 1.0)};
+  }
+}
+
+template <typename CI, typename CO>
+__global__ void k_convert(const CI* __restrict__ in, CO* __restrict__ out, int64_t n3) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const CI v = in[i];
+    out[i] = CO{(decltype(CO().x))v.x, (decltype(CO().x))v.y};
+  }
+}
+
+// psi *= scal[SC_SCALE] (mode 0) or 1 / sqrt(scal[SC_N2]) (mode 1).
+template <typename C>
+__global__ void k_scale(C* __restrict__ psi, int64_t n3, const double* __restrict__ scal, int mode) {
+  const double f = mode == 0 ? scal[SC_SCALE] : 1.0 / sqrt(scal[SC_N2]);
+  using R = decltype(C().x);
+  const R fr = (R)f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    C v = psi[i];
+    psi[i] = C{v.x * fr, v.y * fr};
+  }
+}
+
+}  // namespace qfd
+
+// ================================================================== plan
+struct qfd_plan_s {
+  qfd_params p{};
+  int64_t n3 = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // device memory
+  double2* psi64 = nullptr;
+  float2* psi32 = nullptr;
+  double2* W = nullptr;
+  double2* coef64 = nullptr;
+  float2* coef32 = nullptr;
+  double* V = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double* ktab64 = nullptr;
+  float* ktab32 = nullptr;
+  KinParams* kin_host = nullptr;
+  double* partA = nullptr;
+  double* partC = nullptr;
+  double* partG = nullptr;
+  int npart = 0;
+  int nA = 0, nC = 0;
+  double* scal = nullptr;
+  int* flag = nullptr;
+  // host-side state
+  KinParams kin{};
+  double tmax = 0.0;
+  std::vector<int64_t> t;
+  std::vector<int> parity;
+  std::vector<int64_t> steps64, steps32;
+  std::vector<double> ebulk;
+  int w_state = -1, w_stage = ST_NONE, w_phase = -1;
+  bool pending = false;
+  int phase = 0;  // 0: complex128 buffers, 1: complex64 buffers
+  bool has_pot = false;
+  // instrumentation
+  bool timing = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev[PASS_COUNT];
+  size_t evused[PASS_COUNT] = {};
+};
+
+namespace {
+
+qfd_status fail(qfd_plan_t pl, qfd_status s, const std::string& msg) {
+  if (pl) pl->err = msg;
+  return s;
+}
+
+#define QFD_CK(call)                                                                             \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(pl, QFD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Launch f() (which returns cudaError_t), bracketed by timing events when enabled.
+template <class F>
+cudaError_t run(qfd_plan_t pl, int kind, F&& f) {
+  if (pl->timing) {
+    size_t& u = pl->evused[kind];
+    auto& v = pl->ev[kind];
+    if (u + 2 > v.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      v.push_back(a);
+      v.push_back(b);
+    }
+    cudaEventRecord(v[u], pl->st);
+    cudaError_t e = f();
+    cudaEventRecord(v[u + 1], pl->st);
+    u += 2;
+    ++pl->launches;
+    return e;
+  }
+  ++pl->launches;
+  return f();
+}
+
+#define QFD_RUN(kind, expr)                                                                      \
+  do {                                                                                           \
+    cudaError_t e_ = run(pl, kind, [&]() -> cudaError_t { return (expr); });                     \
+    if (e_ != cudaSuccess) return fail(pl, QFD_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+int grid_for(int64_t n3) {
+  int64_t g = (n3 + 255) / 256;
+  return (int)(g < 8 * 152 ? (g < 1 ? 1 : g) : 8 * 152);
+}
+
+// exp(-2 pi i e / n) with the angle reduced to the first octant in integers,
+// so quadrant points are exact and the table is symmetric.
+void unit_root(int64_t e, int64_t n, double* c, double* s) {
+  e %= n;
+  const int64_t q = (4 * e) / n;
+  const int64_t rem = 4 * e - q * n;  // angle = pi/2 * (q + rem/n)
+  double cp, sp;
+  if (2 * rem <= n) {
+    const double phi = (M_PI / 2) * (double)rem / (double)n;
+    cp = std::cos(phi);
+    sp = std::sin(phi);
+  } else {
+    const double phi = (M_PI / 2) * (double)(n - rem) / (double)n;
+    cp = std::sin(phi);
+    sp = std::cos(phi);
+  }
+  double ct, st;
+  switch (q) {
+    case 0: ct = cp; st = sp; break;
+    case 1: ct = -sp; st = cp; break;
+    case 2: ct = -cp; st = -sp; break;
+    default: ct = sp; st = -cp; break;
+  }
+  *c = ct;
+  *s = -st;
+}
+
+template <typename R> struct PhaseOf;
+template <> struct PhaseOf<double> { static constexpr int id = 0; };
+template <> struct PhaseOf<float> { static constexpr int id = 1; };
+
+template <typename R> typename CxT<R>::T* psi_of(qfd_plan_t pl, int s);
+template <> double2* psi_of<double>(qfd_plan_t pl, int s) { return pl->psi64 + (int64_t)s * pl->n3; }
+template <> float2* psi_of<float>(qfd_plan_t pl, int s) { return pl->psi32 + (int64_t)s * pl->n3; }
+template <typename R> const void* coef_of(qfd_plan_t pl) {
+  return PhaseOf<R>::id == 0 ? (const void*)pl->coef64 : (const void*)pl->coef32;
+}
+template <typename R> const void* tw_of(qfd_plan_t pl) {
+  return PhaseOf<R>::id == 0 ? (const void*)pl->tw64 : (const void*)pl->tw32;
+}
+template <typename R> const void* ktab_of(qfd_plan_t pl) {
+  return PhaseOf<R>::id == 0 ? (const void*)pl->ktab64 : (const void*)pl->ktab32;
+}
+
+template <typename R>
+LaunchArgs base_args(qfd_plan_t pl) {
+  LaunchArgs a;
+  a.n = pl->p.n;
+  a.W = pl->W;
+  a.tw = tw_of<R>(pl);
+  a.ktab = ktab_of<R>(pl);
+  a.kin = &pl->kin;
+  a.coef = coef_of<R>(pl);
+  a.V = pl->V;
+  a.stream = pl->st;
+  return a;
+}
+
+qfd_status finalize(qfd_plan_t pl, const double* part, int nq, int count, int op) {
+  QFD_RUN(PASS_FINALIZE, (k_finalize_op<<<1, FIN_THREADS, 0, pl->st>>>(part, nq, count, pl->scal, op), cudaGetLastError()));
+  return QFD_OK;
+}
+
+// forward DFT_x of src (times the pending scale if use_scale) into W; psi_out
+// optionally receives the scaled input.  Partials of |.|^2, V|.|^2 -> partA.
+template <typename R>
+qfd_status pass_forward_x(qfd_plan_t pl, const void* src, void* psi_out, bool use_scale, int check) {
+  LaunchArgs a = base_args<R>(pl);
+  a.src = src;
+  a.psi_out = psi_out;
+  a.scale = use_scale ? pl->scal + SC_SCALE : nullptr;
+  a.part = pl->partA;
+  a.check = check;
+  int nb = 0;
+  QFD_RUN(PASS_FWD_X, launch_forward_x<R>(a, &nb));
+  pl->nA = nb;
+  return QFD_OK;
+}
+
+template <typename R>
+qfd_status advance_to_d(qfd_plan_t pl, int parseval_at_c) {
+  LaunchArgs a = base_args<R>(pl);
+  if (pl->w_stage == ST_X) {
+    QFD_RUN(PASS_FWD_Y, launch_fft_y<R>(a, -1));
+    pl->w_stage = ST_XY;
+  }
+  if (pl->w_stage == ST_XY) {
+    a.part = pl->partC;
+    a.check = parseval_at_c;
+    int nb = 0;
+    QFD_RUN(PASS_ZKIN, launch_zpass<R>(a, &nb));
+    pl->nC = nb;
+    pl->w_stage = ST_C;
+    if (parseval_at_c) return QFD_OK;  // caller reads the Parseval partials before pass D
+  }
+  if (pl->w_stage == ST_C) {
+    QFD_RUN(PASS_INV_Y, launch_fft_y<R>(a, +1));
+    pl->w_stage = ST_D;
+  }
+  return QFD_OK;
+}
+
+template <typename R>
+qfd_status ensure_w(qfd_plan_t pl, int s) {
+  if (pl->w_state != s || pl->w_phase != PhaseOf<R>::id || pl->w_stage == ST_NONE) {
+    pl->pending = false;
+    qfd_status r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 0);
+    if (r != QFD_OK) return r;
+    pl->w_state = s;
+    pl->w_phase = PhaseOf<R>::id;
+    pl->w_stage = ST_X;
+  }
+  return QFD_OK;
+}
+
+// Parity projection, Gram-Schmidt against states 0..s-1, normalisation.
+// With neither projection nor lower states the normalisation factor is only
+// computed here and applied by the next pass A (the update is linear).
+template <typename R>
+qfd_status cadence(qfd_plan_t pl, int s, int check) {
+  const int k = s;
+  const int par = pl->parity[s];
+  const int offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
+  qfd_status r;
+  if (k > 0 || par != 0) {
+    if (pl->pending) return fail(pl, QFD_ERR_STATE, "internal: pending scale at projection");
+    auto* psi = psi_of<R>(pl, s);
+    auto* lower = psi_of<R>(pl, 0);
+    if (k > 0) {
+      QFD_RUN(PASS_GS_DOTS, launch_gs_dots<R>(psi, lower, k, par, offgrid, pl->p.n, pl->partG, GS_BLOCKS, pl->st));
+      if ((r = finalize(pl, pl->partG, 2 * k, GS_BLOCKS, OP_SUMS)) != QFD_OK) return r;
+    }
+    QFD_RUN(PASS_GS_APPLY, launch_gs_apply<R>(psi, lower, pl->scal + SC_SUMS, k, par, offgrid, pl->p.n, pl->W, pl->V,
+                                              pl->partG, 0, GS_BLOCKS, pl->st));
+    if ((r = finalize(pl, pl->partG, 2, GS_BLOCKS, OP_NORM)) != QFD_OK) return r;
+    if ((r = pass_forward_x<R>(pl, pl->W, psi, true, check)) != QFD_OK) return r;
+    if (check && (r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
+    pl->w_state = s;
+    pl->w_phase = PhaseOf<R>::id;
+    pl->w_stage = ST_X;
+    pl->pending = false;
+    return QFD_OK;
+  }
+  if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_NORM)) != QFD_OK) return r;
+  pl->pending = true;
+  return QFD_OK;
+}
+
+template <typename R>
+qfd_status step_once(qfd_plan_t pl, int s, int check) {
+  qfd_status r;
+  if ((r = ensure_w<R>(pl, s)) != QFD_OK) return r;
+  if ((r = advance_to_d<R>(pl, 0)) != QFD_OK) return r;
+  LaunchArgs a = base_args<R>(pl);
+  a.psi = psi_of<R>(pl, s);
+  a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
+  a.part = pl->partA;
+  a.check = check;
+  int nb = 0;
+  QFD_RUN(PASS_UPDATE_X, launch_update_x<R>(a, &nb));
+  pl->nA = nb;
+  pl->pending = false;
+  pl->w_stage = ST_X;
+  pl->t[s] += 1;
+  if (pl->t[s] % pl->p.ortho_every == 0) {
+    if ((r = cadence<R>(pl, s, check)) != QFD_OK) return r;
+  } else if (check) {
+    if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
+  }
+  return QFD_OK;
+}
+
+// Applies a pending normalisation factor to the stored state (W is dropped).
+template <typename R>
+qfd_status materialize(qfd_plan_t pl, int s) {
+  if (pl->pending) {
+    QFD_RUN(PASS_OTHER, (k_scale<<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<R>(pl, s), pl->n3, pl->scal, 0),
+                         cudaGetLastError()));
+    pl->pending = false;
+    pl->w_stage = ST_NONE;
+  }
+  return QFD_OK;
+}
+
+// Energy of the state whose partials (N2, PV) were just finalised and whose
+// x-transform sits in W: passes B and C (with the Parseval sum), then E.
+template <typename R>
+qfd_status energy_tail(qfd_plan_t pl, double* E, double* n2) {
+  qfd_status r;
+  if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
+  if ((r = advance_to_d<R>(pl, 1)) != QFD_OK) return r;
+  if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
+  double h[SC_COUNT];
+  QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  if (E) *E = h[SC_E];
+  if (n2) *n2 = h[SC_N2];
+  return QFD_OK;
+}
+
+template <typename R>
+qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
+  qfd_status r;
+  if ((r = materialize<R>(pl, s)) != QFD_OK) return r;
+  if ((r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 1)) != QFD_OK) return r;
+  pl->w_state = s;
+  pl->w_phase = PhaseOf<R>::id;
+  pl->w_stage = ST_X;
+  if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
+  return energy_tail<R>(pl, E, n2);
+}
+
+// One state in one arithmetic: cadence at t = 0, then blocks of check_every
+// steps, each followed by the energy and the relative-change test.
+template <typename R>
+qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, double* E_out, int64_t* steps,
+                       bool* converged) {
+  qfd_status r;
+  pl->t[s] = 0;
+  pl->pending = false;
+  pl->w_stage = ST_NONE;
+  if (s > 0 || pl->parity[s] != 0) {
+    if ((r = cadence<R>(pl, s, 0)) != QFD_OK) return r;
+  } else {
+    if ((r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 0)) != QFD_OK) return r;
+    pl->w_state = s;
+    pl->w_phase = PhaseOf<R>::id;
+    pl->w_stage = ST_X;
+    if ((r = cadence<R>(pl, s, 0)) != QFD_OK) return r;
+  }
+  double e = NAN, e_prev = NAN, n2 = NAN;
+  bool have_prev = false;
+  *converged = false;
+  const int ce = pl->p.check_every;
+  while (pl->t[s] < max_steps) {
+    for (int j = 0; j < ce; ++j)
+      if ((r = step_once<R>(pl, s, j == ce - 1)) != QFD_OK) return r;
+    if ((r = energy_tail<R>(pl, &e, &n2)) != QFD_OK) return r;
+    if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
+      return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
+    if (tol >= 0 && have_prev && std::fabs(e - e_prev) <= tol * std::fabs(e)) {
+      *converged = true;
+      break;
+    }
+    e_prev = e;
+    have_prev = true;
+  }
+  // leave the state normalised (its last finalised N2 is of the stored values
+  // times the pending factor, which equals 1 / sqrt(N2) when pending)
+  QFD_RUN(PASS_OTHER, (k_scale<<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<R>(pl, s), pl->n3, pl->scal, 1),
+                       cudaGetLastError()));
+  pl->pending = false;
+  pl->w_stage = ST_NONE;
+  *E_out = e;
+  *steps = pl->t[s];
+  return QFD_OK;
+}
+
+qfd_status convert_state(qfd_plan_t pl, int s, int to_phase) {
+  const int g = grid_for(pl->n3);
+  if (to_phase == 1) {
+    QFD_RUN(PASS_OTHER, (k_convert<<<g, 256, 0, pl->st>>>(pl->psi64 + s * pl->n3, pl->psi32 + s * pl->n3, pl->n3),
+                         cudaGetLastError()));
+  } else {
+    QFD_RUN(PASS_OTHER, (k_convert<<<g, 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->psi64 + s * pl->n3, pl->n3),
+                         cudaGetLastError()));
+  }
+  if (pl->w_state == s) pl->w_stage = ST_NONE;
+  return QFD_OK;
+}
+
+qfd_status check_state(qfd_plan_t pl, int s) {
+  if (!pl) return QFD_ERR_ARG;
+  if (s < 0 || s >= pl->p.nstates) return fail(pl, QFD_ERR_ARG, "state index out of range");
+  return QFD_OK;
+}
+
+qfd_status derive_coefficients(qfd_plan_t pl) {
+  QFD_CK(cudaMemsetAsync(pl->flag, 0, sizeof(int), pl->st));
+  QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau, pl->coef64, pl->coef32,
+                                                                     pl->flag),
+                       cudaGetLastError()));
+  int bad = 0;
+  QFD_CK(cudaMemcpyAsync(&bad, pl->flag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  if (bad) {
+    pl->has_pot = false;
+    return fail(pl, QFD_ERR_UNSTABLE_DT, "1 + dtau V/2 <= 0 or non-finite V at some site");
+  }
+  pl->has_pot = true;
+  return QFD_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
+  if (out) *out = nullptr;
+  if (!params || !out) {
+    g_create_error = "null argument";
+    return QFD_ERR_ARG;
+  }
+  const qfd_params& p = *params;
+  if (!supported_n(p.n)) {
+    g_create_error = "n must be one of 8, 16, 32, 64, 128, 256, 512, 1024";
+    return QFD_ERR_ARG;
+  }
+  if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 1 || p.kinetic > 3 || p.nstates < 1 ||
+      p.nstates > MAX_LOWER || p.precision < 0 || p.precision > 2 || p.ortho_every < 1 || p.check_every < 1 ||
+      (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || p.reserved != 0 || p.max_steps < 0 ||
+      (p.rest_mass != 0 && p.rest_mass != 1)) {
+    g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 1..3; nstates 1..8; cadences >= 1)";
+    return QFD_ERR_ARG;
+  }
+  const int64_t n = p.n;
+  // per-axis kinetic table and the largest T(k) (all three k at the table maximum)
+  std::vector<double> ktab(n);
+  double kmax = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t m = j <= n / 2 ? j : j - n;
+    if (p.kinetic == 1) {
+      const double k = 2.0 * M_PI * (double)m / (double)n;
+      ktab[j] = k * k;
+    } else {
+      const double sn = std::sin(M_PI * (double)(m < 0 ? -m : m) / (double)n);
+      ktab[j] = 4.0 * sn * sn;
+    }
+    kmax = std::fmax(kmax, ktab[j]);
+  }
+  const double n3d = (double)n * (double)n * (double)n;
+  KinParams kin{};
+  kin.kinterm = p.kinetic;
+  kin.pref = 1.0 / (2.0 * p.a * p.a * p.mass * n3d);
+  kin.am2 = (p.a * p.mass) * (p.a * p.mass);
+  kin.inv_a_n3 = 1.0 / (p.a * n3d);
+  kin.m0_n3 = p.rest_mass ? 0.0 : p.mass / n3d;
+  const double smax = 3.0 * kmax;
+  const double tmax = p.kinetic == 3 ? std::sqrt(smax + kin.am2) / p.a - (p.rest_mass ? 0.0 : p.mass)
+                                     : smax / (2.0 * p.a * p.a * p.mass);
+  if (!(p.dtau * tmax < 2.0)) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "unstable time step: dtau * max T(k) = %.6g >= 2", p.dtau * tmax);
+    g_create_error = buf;
+    return QFD_ERR_UNSTABLE_DT;
+  }
+
+  qfd_plan_t pl = new qfd_plan_s();
+  pl->p = p;
+  pl->n3 = n * n * n;
+  pl->kin = kin;
+  pl->tmax = tmax;
+  pl->t.assign(p.nstates, 0);
+  pl->parity.assign(p.nstates, 0);
+  pl->steps64.assign(p.nstates, 0);
+  pl->steps32.assign(p.nstates, 0);
+  pl->ebulk.assign(p.nstates, NAN);
+  pl->phase = p.precision == QFD_C128 ? 0 : 1;
+
+  auto cleanup_fail = [&](qfd_status s, const std::string& msg) {
+    g_create_error = msg;
+    qfd_destroy(pl);
+    return s;
+  };
+  if (p.stream) {
+    pl->st = (cudaStream_t)p.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&pl->st, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup_fail(QFD_ERR_CUDA, "cudaStreamCreate failed");
+    pl->own_stream = true;
+  }
+  const bool need64 = p.precision != QFD_C64, need32 = p.precision != QFD_C128;
+  const int64_t n3 = pl->n3;
+  const int npart = std::max(std::max(max_partials<double>(n), max_partials<float>(n)), GS_BLOCKS);
+  pl->npart = npart;
+  struct Alloc { void** ptr; size_t bytes; };
+  std::vector<Alloc> allocs = {
+      {(void**)&pl->W, (size_t)n3 * sizeof(double2)},
+      {(void**)&pl->V, (size_t)n3 * sizeof(double)},
+      {(void**)&pl->tw64, (size_t)n * sizeof(double2)},
+      {(void**)&pl->tw32, (size_t)n * sizeof(float2)},
+      {(void**)&pl->ktab64, (size_t)n * sizeof(double)},
+      {(void**)&pl->ktab32, (size_t)n * sizeof(float)},
+      {(void**)&pl->partA, (size_t)2 * npart * sizeof(double)},
+      {(void**)&pl->partC, (size_t)npart * sizeof(double)},
+      {(void**)&pl->partG, (size_t)2 * MAX_LOWER * npart * sizeof(double)},
+      {(void**)&pl->scal, SC_COUNT * sizeof(double)},
+      {(void**)&pl->flag, sizeof(int)},
+  };
+  if (need64) {
+    allocs.push_back({(void**)&pl->psi64, (size_t)p.nstates * n3 * sizeof(double2)});
+    allocs.push_back({(void**)&pl->coef64, (size_t)n3 * sizeof(double2)});
+  }
+  if (need32) {
+    allocs.push_back({(void**)&pl->psi32, (size_t)p.nstates * n3 * sizeof(float2)});
+    allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
+  }
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      char buf[128];
+      snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed", a.bytes);
+      return cleanup_fail(QFD_ERR_OOM, buf);
+    }
+  }
+  std::vector<double2> tw(n);
+  std::vector<float2> tw32(n);
+  std::vector<float> kt32(n);
+  for (int64_t e = 0; e < n; ++e) {
+    double c, s;
+    unit_root(e, n, &c, &s);
+    tw[e] = double2{c, s};
+    tw32[e] = float2{(float)c, (float)s};
+    kt32[e] = (float)ktab[e];
+  }
+  bool ok = cudaMemcpy(pl->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->tw32, tw32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->ktab64, ktab.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->ktab32, kt32.data(), n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess;
+  if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
+  *out = pl;
+  return QFD_OK;
+}
+
+void qfd_destroy(qfd_plan_t pl) {
+  if (!pl) return;
+  if (pl->st) cudaStreamSynchronize(pl->st);
+  void* bufs[] = {pl->psi64, pl->psi32, pl->W,     pl->coef64, pl->coef32, pl->V,    pl->tw64, pl->tw32,
+                  pl->ktab64, pl->ktab32, pl->partA, pl->partC, pl->partG, pl->scal, pl->flag};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto& v : pl->ev)
+    for (auto e : v) cudaEventDestroy(e);
+  if (pl->own_stream && pl->st) cudaStreamDestroy(pl->st);
+  delete pl;
+}
+
+const char* qfd_last_error(qfd_plan_t pl) { return pl ? pl->err.c_str() : g_create_error.c_str(); }
+
+qfd_status qfd_set_potential(qfd_plan_t pl, const double* V, int on_device) {
+  if (!pl || !V) return fail(pl, QFD_ERR_ARG, "null argument");
+  QFD_CK(cudaMemcpyAsync(pl->V, V, pl->n3 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         pl->st));
+  return derive_coefficients(pl);
+}
+
+qfd_status qfd_fill_potential(qfd_plan_t pl, int kind, const double* coeffs, int ncoeffs) {
+  if (!pl) return QFD_ERR_ARG;
+  if (kind < QFD_POT_ZERO || kind > QFD_POT_SOFTCOUL || ncoeffs < 0 || (ncoeffs > 0 && !coeffs))
+    return fail(pl, QFD_ERR_ARG, "unknown potential kind or missing coefficients");
+  const int need = kind == QFD_POT_CORNELL ? 2 : (kind == QFD_POT_HO || kind == QFD_POT_SOFTCOUL) ? 1 : 0;
+  if (ncoeffs < need) return fail(pl, QFD_ERR_ARG, "too few potential coefficients");
+  const double c0 = need > 0 ? coeffs[0] : 0.0, c1 = need > 1 ? coeffs[1] : 0.0;
+  QFD_RUN(PASS_OTHER, (k_potential<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->p.n, pl->p.a, kind, c0, c1,
+                                                                         pl->p.centre == QFD_CENTRE_OFFGRID),
+                       cudaGetLastError()));
+  return derive_coefficients(pl);
+}
+
+qfd_status qfd_get_potential(qfd_plan_t pl, double* V, int on_device) {
+  if (!pl || !V) return fail(pl, QFD_ERR_ARG, "null argument");
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "no potential set");
+  QFD_CK(cudaMemcpyAsync(V, pl->V, pl->n3 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         pl->st));
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  return QFD_OK;
+}
+
+qfd_status qfd_set_psi(qfd_plan_t pl, int s, const double* psi, int on_device) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!psi) return fail(pl, QFD_ERR_ARG, "null psi");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t bytes = pl->n3 * sizeof(double2);
+  if (pl->psi64) {
+    QFD_CK(cudaMemcpyAsync(pl->psi64 + s * pl->n3, psi, bytes, kind, pl->st));
+    if (pl->psi32) {
+      if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
+    }
+  } else {
+    QFD_CK(cudaMemcpyAsync(pl->W, psi, bytes, kind, pl->st));
+    QFD_RUN(PASS_OTHER, (k_convert<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->W, pl->psi32 + s * pl->n3, pl->n3),
+                         cudaGetLastError()));
+    pl->w_stage = ST_NONE;
+  }
+  pl->t[s] = 0;
+  if (pl->w_state == s) pl->w_stage = ST_NONE;
+  if (!on_device) QFD_CK(cudaStreamSynchronize(pl->st));  // caller may reuse its host buffer
+  return QFD_OK;
+}
+
+qfd_status qfd_fill_psi_uniform(qfd_plan_t pl, int s, uint64_t seed) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  const int g = grid_for(pl->n3);
+  if (pl->psi64)
+    QFD_RUN(PASS_OTHER, (k_fill_uniform<<<g, 256, 0, pl->st>>>(pl->psi64 + s * pl->n3, pl->n3, seed), cudaGetLastError()));
+  if (pl->psi32)
+    QFD_RUN(PASS_OTHER, (k_fill_uniform<<<g, 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->n3, seed), cudaGetLastError()));
+  pl->t[s] = 0;
+  if (pl->w_state == s) pl->w_stage = ST_NONE;
+  return QFD_OK;
+}
+
+qfd_status qfd_get_psi(qfd_plan_t pl, int s, double* out, int on_device) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!out) return fail(pl, QFD_ERR_ARG, "null output");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t bytes = pl->n3 * sizeof(double2);
+  if (pl->phase == 0) {
+    if ((r = materialize<double>(pl, s)) != QFD_OK) return r;
+    QFD_CK(cudaMemcpyAsync(out, pl->psi64 + s * pl->n3, bytes, kind, pl->st));
+  } else {
+    if ((r = materialize<float>(pl, s)) != QFD_OK) return r;
+    QFD_RUN(PASS_OTHER, (k_convert<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->W, pl->n3),
+                         cudaGetLastError()));
+    pl->w_stage = ST_NONE;
+    QFD_CK(cudaMemcpyAsync(out, pl->W, bytes, kind, pl->st));
+  }
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  return QFD_OK;
+}
+
+qfd_status qfd_set_parity(qfd_plan_t pl, int s, int parity) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (parity < -1 || parity > 1) return fail(pl, QFD_ERR_ARG, "parity must be -1, 0 or 1");
+  pl->parity[s] = parity;
+  return QFD_OK;
+}
+
+qfd_status qfd_step(qfd_plan_t pl, int s, int64_t nsteps) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before stepping");
+  if (nsteps < 0) return fail(pl, QFD_ERR_ARG, "nsteps < 0");
+  for (int64_t i = 0; i < nsteps; ++i) {
+    r = pl->phase == 0 ? step_once<double>(pl, s, 0) : step_once<float>(pl, s, 0);
+    if (r != QFD_OK) return r;
+  }
+  return pl->phase == 0 ? materialize<double>(pl, s) : materialize<float>(pl, s);
+}
+
+qfd_status qfd_energy(qfd_plan_t pl, int s, double* E, double* norm2) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before taking the energy");
+  return pl->phase == 0 ? energy_full<double>(pl, s, E, norm2) : energy_full<float>(pl, s, E, norm2);
+}
+
+qfd_status qfd_solve_states(qfd_plan_t pl, int nstates, const int* parity, double* E_out, int64_t* steps_out) {
+  if (!pl) return QFD_ERR_ARG;
+  if (nstates < 1 || nstates > pl->p.nstates) return fail(pl, QFD_ERR_ARG, "nstates out of range");
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before solving");
+  bool all_conv = true;
+  for (int s = 0; s < nstates; ++s) {
+    const int par = parity ? parity[s] : 0;
+    if (par < -1 || par > 1) return fail(pl, QFD_ERR_ARG, "parity must be -1, 0 or 1");
+    pl->parity[s] = par;
+    double e = NAN;
+    int64_t steps = 0;
+    bool conv = false;
+    qfd_status r = QFD_OK;
+    pl->steps32[s] = pl->steps64[s] = 0;
+    pl->ebulk[s] = NAN;
+    if (pl->p.precision == QFD_C128) {
+      pl->phase = 0;
+      r = solve_phase<double>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
+      pl->steps64[s] = steps;
+    } else if (pl->p.precision == QFD_C64) {
+      pl->phase = 1;
+      r = solve_phase<float>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
+      pl->steps32[s] = steps;
+    } else {
+      pl->phase = 1;
+      if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
+      r = solve_phase<float>(pl, s, pl->p.tol_bulk, pl->p.max_steps, &e, &steps, &conv);
+      if (r != QFD_OK) return r;
+      pl->steps32[s] = steps;
+      pl->ebulk[s] = e;
+      if ((r = convert_state(pl, s, 0)) != QFD_OK) return r;
+      pl->phase = 0;
+      r = solve_phase<double>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
+      if (r != QFD_OK) return r;
+      pl->steps64[s] = steps;
+      if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;  // lower state for later complex64 phases
+      steps = pl->steps32[s] + pl->steps64[s];
+    }
+    if (r != QFD_OK) return r;
+    if (E_out) E_out[s] = e;
+    if (steps_out) steps_out[s] = steps;
+    if (pl->p.tol >= 0 && !conv) all_conv = false;
+  }
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  if (!all_conv) return fail(pl, QFD_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
+  return QFD_OK;
+}
+
+qfd_status qfd_set_limits(qfd_plan_t pl, int64_t max_steps, double tol, double tol_bulk) {
+  if (!pl) return QFD_ERR_ARG;
+  if (max_steps < 0) return fail(pl, QFD_ERR_ARG, "max_steps < 0");
+  pl->p.max_steps = max_steps;
+  pl->p.tol = tol;
+  pl->p.tol_bulk = tol_bulk;
+  return QFD_OK;
+}
+
+qfd_status qfd_get_stats(qfd_plan_t pl, int s, int64_t* steps_c64, int64_t* steps_c128, double* e_bulk) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (steps_c64) *steps_c64 = pl->steps32[s];
+  if (steps_c128) *steps_c128 = pl->steps64[s];
+  if (e_bulk) *e_bulk = pl->ebulk[s];
+  return QFD_OK;
+}
+
+qfd_status qfd_timing_enable(qfd_plan_t pl, int enable) {
+  if (!pl) return QFD_ERR_ARG;
+  pl->timing = enable != 0;
+  return QFD_OK;
+}
+
+qfd_status qfd_timing_reset(qfd_plan_t pl) {
+  if (!pl) return QFD_ERR_ARG;
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  for (auto& u : pl->evused) u = 0;
+  pl->launches = 0;
+  return QFD_OK;
+}
+
+qfd_status qfd_timing_query(qfd_plan_t pl, int kind, int64_t* launches, double* total_ms) {
+  if (!pl) return QFD_ERR_ARG;
+  if (kind < 0 || kind >= PASS_COUNT) return fail(pl, QFD_ERR_ARG, "unknown pass kind");
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  double tot = 0;
+  for (size_t i = 0; i + 1 < pl->evused[kind]; i += 2) {
+    float ms = 0;
+    QFD_CK(cudaEventElapsedTime(&ms, pl->ev[kind][i], pl->ev[kind][i + 1]));
+    tot += ms;
+  }
+  if (launches) *launches = (int64_t)(pl->evused[kind] / 2);
+  if (total_ms) *total_ms = tot;
+  return QFD_OK;
+}
+
+int64_t qfd_launch_count(qfd_plan_t pl) { return pl ? pl->launches : -1; }
+
+void* qfd_get_stream(qfd_plan_t pl) { return pl ? (void*)pl->st : nullptr; }
+
+qfd_status qfd_sync(qfd_plan_t pl) {
+  if (!pl) return QFD_ERR_ARG;
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  return QFD_OK;
+}
+
+}  // extern "C"
+
+namespace qfd {
+bool supported_n(int64_t n) {
+  return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+}
+}  // namespace qfd

@@ -1,0 +1,6 @@
+// complex64 instantiation of the pass kernels and launchers.
+#include "qfd_launch_impl.cuh"
+
+namespace qfd {
+QFD_INSTANTIATE_LAUNCHERS(float)
+}  // namespace qfd

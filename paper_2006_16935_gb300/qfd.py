@@ -1,0 +1,239 @@
+"""ctypes binding of libqfd.so (the C ABI declared in include/qfd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library.  Arrays may be numpy arrays (host), or torch tensors on the
+CUDA device (passed as device pointers) or in (pinned) host memory.
+The binding refuses to work without the compiled library: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqfd.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "qfd.h")
+
+OK, ERR_ARG, ERR_OOM, ERR_UNSTABLE_DT, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_NOT_CONVERGED, ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+STATUS_NAMES = {0: "QFD_OK", -1: "QFD_ERR_ARG", -2: "QFD_ERR_OOM", -3: "QFD_ERR_UNSTABLE_DT",
+                -4: "QFD_ERR_DIVERGED", -5: "QFD_ERR_TIMEOUT", -6: "QFD_ERR_CUDA",
+                -7: "QFD_ERR_NOT_CONVERGED", -8: "QFD_ERR_STATE"}
+PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2}
+CENTRE = {"grid": 0, "offgrid": 1}
+POTENTIAL = {"zero": 0, "ho": 1, "cornell": 2, "coulomb": 3, "softcoul": 4}
+PASS_KINDS = {"update_x": 0, "fwd_y": 1, "z_kinetic": 2, "inv_y": 3, "fwd_x": 4,
+              "gs_dots": 5, "gs_apply": 6, "reduce": 7, "other": 8}
+
+
+class QfdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class QfdParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("a", ctypes.c_double), ("mass", ctypes.c_double),
+                ("dtau", ctypes.c_double), ("kinetic", ctypes.c_int32), ("rest_mass", ctypes.c_int32),
+                ("nstates", ctypes.c_int32), ("precision", ctypes.c_int32), ("ortho_every", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("centre", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions include/qfd.h declares."""
+    text = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w*]+\s*\*?\s*(qfd_\w+)\s*\(", text, re.M)))
+
+
+def load():
+    """Loads libqfd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2006_16935_gb300.build.build_library()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "qfd_plan": (I, [ctypes.POINTER(QfdParams), ctypes.POINTER(P)]),
+        "qfd_destroy": (None, [P]),
+        "qfd_last_error": (ctypes.c_char_p, [P]),
+        "qfd_set_potential": (I, [P, P, I]),
+        "qfd_fill_potential": (I, [P, I, ctypes.POINTER(D), I]),
+        "qfd_get_potential": (I, [P, P, I]),
+        "qfd_set_psi": (I, [P, I, P, I]),
+        "qfd_fill_psi_uniform": (I, [P, I, ctypes.c_uint64]),
+        "qfd_get_psi": (I, [P, I, P, I]),
+        "qfd_set_parity": (I, [P, I, I]),
+        "qfd_step": (I, [P, I, I64]),
+        "qfd_energy": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "qfd_set_limits": (I, [P, I64, D, D]),
+        "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
+        "qfd_timing_enable": (I, [P, I]),
+        "qfd_timing_reset": (I, [P]),
+        "qfd_timing_query": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D)]),
+        "qfd_launch_count": (I64, [P]),
+        "qfd_get_stream": (P, [P]),
+        "qfd_sync": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(arr, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of `dtype` layout."""
+    mod = type(arr).__module__
+    if mod.startswith("torch"):
+        import torch
+        want = torch.complex128 if dtype == np.complex128 else torch.float64
+        if arr.dtype != want or not arr.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return arr.data_ptr(), int(arr.is_cuda), arr
+    a = np.ascontiguousarray(arr, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+class Plan:
+    """One solver plan: a lattice, its kinetic term, potential and state stack."""
+
+    def __init__(self, n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision="c128",
+                 ortho_every=10, check_every=100, centre="grid", max_steps=100000, tol=1e-9,
+                 tol_bulk=1e-6, stream=None):
+        self.lib = load()
+        self.n = int(n)
+        p = QfdParams(n=self.n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=rest_mass,
+                      nstates=nstates, precision=PRECISION[precision], ortho_every=ortho_every,
+                      check_every=check_every, centre=CENTRE[centre], reserved=0, max_steps=max_steps,
+                      tol=tol, tol_bulk=tol_bulk, stream=stream)
+        self.params = p
+        h = ctypes.c_void_p()
+        st = self.lib.qfd_plan(ctypes.byref(p), ctypes.byref(h))
+        if st != OK:
+            raise QfdError(st, self.lib.qfd_last_error(None).decode())
+        self.h = h
+
+    # -- plumbing
+    def _check(self, st, ok=(OK,)):
+        if st not in ok:
+            raise QfdError(st, self.lib.qfd_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qfd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.n, self.n, self.n)
+
+    # -- inputs
+    def set_potential(self, V):
+        ptr, dev, keep = _ptr(V, np.float64)
+        self._check(self.lib.qfd_set_potential(self.h, ptr, dev))
+        del keep
+
+    def fill_potential(self, kind, coeffs=()):
+        c = (ctypes.c_double * max(1, len(coeffs)))(*coeffs)
+        self._check(self.lib.qfd_fill_potential(self.h, POTENTIAL[kind], c, len(coeffs)))
+
+    def get_potential(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, np.float64)
+        ptr, dev, keep = _ptr(out, np.float64)
+        self._check(self.lib.qfd_get_potential(self.h, ptr, dev))
+        return out
+
+    def set_psi(self, state, psi):
+        ptr, dev, keep = _ptr(psi, np.complex128)
+        self._check(self.lib.qfd_set_psi(self.h, state, ptr, dev))
+        del keep
+
+    def fill_psi_uniform(self, state, seed):
+        self._check(self.lib.qfd_fill_psi_uniform(self.h, state, seed))
+
+    def set_parity(self, state, parity):
+        self._check(self.lib.qfd_set_parity(self.h, state, parity))
+
+    # -- outputs
+    def get_psi(self, state, out=None):
+        if out is None:
+            out = np.empty(self.shape, np.complex128)
+        ptr, dev, keep = _ptr(out, np.complex128)
+        self._check(self.lib.qfd_get_psi(self.h, state, ptr, dev))
+        return out
+
+    def step(self, state, nsteps):
+        self._check(self.lib.qfd_step(self.h, state, nsteps))
+
+    def energy(self, state=0):
+        e, n2 = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.qfd_energy(self.h, state, ctypes.byref(e), ctypes.byref(n2)))
+        return e.value, n2.value
+
+    def solve_states(self, nstates, parity=None, allow_unconverged=False):
+        par = (ctypes.c_int * nstates)(*(parity or [0] * nstates))
+        es = (ctypes.c_double * nstates)()
+        steps = (ctypes.c_int64 * nstates)()
+        ok = (OK, ERR_NOT_CONVERGED) if allow_unconverged else (OK,)
+        st = self._check(self.lib.qfd_solve_states(self.h, nstates, par, es, steps), ok)
+        return list(es), list(steps), st == OK
+
+    def set_limits(self, max_steps, tol, tol_bulk=None):
+        tb = self.params.tol_bulk if tol_bulk is None else tol_bulk
+        self._check(self.lib.qfd_set_limits(self.h, int(max_steps), float(tol), float(tb)))
+        self.params.max_steps, self.params.tol, self.params.tol_bulk = int(max_steps), float(tol), float(tb)
+
+    def stats(self, state):
+        s64, s128, eb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.qfd_get_stats(self.h, state, ctypes.byref(s64), ctypes.byref(s128), ctypes.byref(eb)))
+        return {"steps_c64": s64.value, "steps_c128": s128.value, "e_bulk": eb.value}
+
+    # -- instrumentation
+    def timing(self, enable=True):
+        self._check(self.lib.qfd_timing_enable(self.h, int(enable)))
+
+    def timing_reset(self):
+        self._check(self.lib.qfd_timing_reset(self.h))
+
+    def timing_query(self, kind):
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.qfd_timing_query(self.h, PASS_KINDS[kind] if isinstance(kind, str) else kind,
+                                              ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def launch_count(self):
+        return self.lib.qfd_launch_count(self.h)
+
+    @property
+    def stream(self):
+        return self.lib.qfd_get_stream(self.h)
+
+    def sync(self):
+        self._check(self.lib.qfd_sync(self.h))

@@ -1,0 +1,74 @@
+"""Full-size checks (the 512^3 softened-Coulomb lattice the benchmark times, and
+the 256^3 Cornell lattice of the excited-state workload), through the C ABI.
+
+At these sizes the naive oracle is too slow for a whole lattice, so:
+  * plane-wave superpositions are exact eigenvectors of every FFT kinetic
+    term, so one step maps psi = sum_j c_j e^{i k_j.x} to
+    A psi - B dtau sum_j c_j T(k_j) e^{i k_j.x}; the oracle's T and V give
+    that value site by site at sampled sites;
+  * at 256^3 a random psi is stepped by the oracle with its library FFT.
+"""
+import numpy as np
+import pytest
+
+from oracle import qfd_oracle as O
+from paper_2006_16935_gb300 import inputs
+from paper_2006_16935_gb300 import qfd as Q
+
+pytestmark = pytest.mark.gpu
+
+
+def plane_wave_lattice(n, idx, amp):
+    x = np.arange(n)
+    out = np.zeros((n, n, n), np.complex128)
+    for (i1, i2, i3), c in zip(idx, amp):
+        e1 = np.exp(2j * np.pi * i1 * x / n)
+        e2 = np.exp(2j * np.pi * i2 * x / n)
+        e3 = np.exp(2j * np.pi * i3 * x / n)
+        out += c * (e1[:, None, None] * (e2[:, None] * e3[None, :])[None, :, :])
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", 3e-6)])
+def test_plane_wave_step_512(qfdlib, prec, tol):
+    n, a, m, kin, dt = 512, 0.05, 1.0, 2, 5e-4
+    idx, amp = inputs.plane_wave_mix(n, 5, modes=4)
+    psi = plane_wave_lattice(n, idx, amp)
+    with Q.Plan(n, a, m, dt, kin, precision=prec, ortho_every=1000) as p:
+        p.fill_potential("softcoul", (0.01,))
+        p.set_psi(0, psi)
+        p.step(0, 1)
+        got = p.get_psi(0)
+    rng = np.random.default_rng(0)
+    sites = rng.integers(0, n, size=(4096, 3))
+    sites[0] = [0, 0, 0]
+    sites[1] = [n - 1, n - 1, n - 1]
+    sites[2] = [n // 2, n // 2, n // 2]
+    V = O.potential(n, a, "softcoul", (0.01,))[sites[:, 0], sites[:, 1], sites[:, 2]]
+    T = O.kinetic_symbol(n, a, m, kin)[idx[:, 0], idx[:, 1], idx[:, 2]]
+    phase = np.exp(2j * np.pi * (sites @ idx.T) / n)  # [site, mode]
+    psi_s = phase @ amp
+    hk_s = phase @ (amp * T)
+    A, B = O.update_coefficients(V, dt)
+    expect = A * psi_s - B * dt * hk_s
+    err = np.max(np.abs(got[sites[:, 0], sites[:, 1], sites[:, 2]] - expect)) / np.max(np.abs(expect))
+    assert err < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", 2e-6)])
+def test_random_state_steps_256_against_library_fft_oracle(qfdlib, prec, tol):
+    n, a, m, kin = 256, 0.05, 1.5, 3
+    dt = 0.001
+    V = O.potential(n, a, "cornell", (0.3, 0.2))
+    psi0 = inputs.uniform_psi(n, 2)
+    if prec == "c64":
+        psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    with Q.Plan(n, a, m, dt, kin, precision=prec, ortho_every=2) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        p.set_psi(0, psi0)
+        p.set_parity(0, 1)
+        p.step(0, 3)
+        got = p.get_psi(0)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=2, method="library")
+    ref, _ = O.evolve(psi0, prob, 3, parity=1)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (the benchmark spec of the method, derived in the design doc for complex64):
+  complex128: relative L2 on psi <= 1e-10, relative energy <= 1e-9
+  complex64:  relative L2 on psi <= 2e-6 per 10 steps (FP32 FFT rounding,
+              eps32 * log2(N) per transform, entering the update times dtau T <= 2)
+"""
+import numpy as np
+import pytest
+
+from oracle import qfd_oracle as O
+from paper_2006_16935_gb300 import inputs
+from paper_2006_16935_gb300 import qfd as Q
+
+pytestmark = pytest.mark.gpu
+
+TOL_PSI = 1e-10
+TOL_E = 1e-9
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def stable_dt(n, a, m, kin, frac=0.9, rest_mass=0):
+    return frac / O.kinetic_max(n, a, m, kin, rest_mass)
+
+
+def test_uniform_fill_is_bit_exact(qfdlib):
+    for prec in ("c128", "c64"):
+        with Q.Plan(16, 0.1, 1.0, 1e-4, 2, precision=prec) as p:
+            p.fill_psi_uniform(0, 7)
+            got = p.get_psi(0)
+        ref = inputs.uniform_psi(16, 7)
+        if prec == "c64":
+            ref = ref.astype(np.complex64).astype(np.complex128)
+        assert np.array_equal(got, ref)
+
+
+def test_set_get_roundtrip_and_energy_of_plane_wave(qfdlib):
+    n, a, m = 16, 0.2, 1.1
+    j = np.arange(n)
+    j1, j2, j3 = np.meshgrid(j, j, j, indexing="ij")
+    pw = np.exp(2j * np.pi * (3 * j1 + 8 * j2 + 13 * j3) / n)
+    with Q.Plan(n, a, m, stable_dt(n, a, m, 3), 3) as p:
+        p.fill_potential("zero")
+        p.set_psi(0, pw)
+        assert np.array_equal(p.get_psi(0), pw)
+        e, n2 = p.energy(0)
+    T = O.kinetic_symbol(n, a, m, 3)
+    assert e == pytest.approx(T[3, 8, 13], rel=1e-13)
+    assert n2 == pytest.approx(n ** 3, rel=1e-14)
+
+
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+@pytest.mark.parametrize("kind,coeffs", [("ho", (1.0,)), ("cornell", (0.3, 0.2)), ("coulomb", ()),
+                                         ("softcoul", (0.01,)), ("zero", ())])
+def test_potential_fill_matches_oracle(qfdlib, kind, coeffs, centre):
+    n, a = 32, 0.05
+    with Q.Plan(n, a, 1.0, 1e-4, 2, centre=centre) as p:
+        p.fill_potential(kind, coeffs)
+        V = p.get_potential()
+    ref = O.potential(n, a, kind, coeffs, centre)
+    assert np.max(np.abs(V - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("nsteps", [10, 12])
+@pytest.mark.parametrize("kin", [1, 2, 3])
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+def test_step_parity_c128(qfdlib, n, kin, nsteps):
+    a, m = 0.1, 1.3
+    dt = stable_dt(n, a, m, kin)
+    V = O.potential(n, a, "cornell", (0.3, 0.2))
+    psi0 = inputs.uniform_psi(n, 11)
+    with Q.Plan(n, a, m, dt, kin, ortho_every=5) as p:
+        p.set_potential(V)
+        p.set_psi(0, psi0)
+        p.step(0, nsteps)
+        got = p.get_psi(0)
+    ref, _ = O.evolve(psi0, O.Problem(n, a, m, dt, kin, V, ortho_every=5), nsteps)
+    assert rel_l2(got, ref) < TOL_PSI
+
+
+@pytest.mark.parametrize("kin", [1, 3])
+def test_step_parity_c128_split_calls_and_rest_mass(qfdlib, kin):
+    # steps issued in several calls continue the same cadence counter
+    n, a, m = 32, 0.12, 2.0
+    dt = stable_dt(n, a, m, kin, 0.5, rest_mass=1)
+    V = O.potential(n, a, "ho", (0.7,))
+    psi0 = inputs.uniform_psi(n, 12)
+    with Q.Plan(n, a, m, dt, kin, rest_mass=1, ortho_every=4) as p:
+        p.set_potential(V)
+        p.set_psi(0, psi0)
+        for k in (3, 1, 5, 2):
+            p.step(0, k)
+        got = p.get_psi(0)
+    ref, _ = O.evolve(psi0, O.Problem(n, a, m, dt, kin, V, rest_mass=1, ortho_every=4), 11)
+    assert rel_l2(got, ref) < TOL_PSI
+
+
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+@pytest.mark.parametrize("parity", [1, -1])
+def test_step_parity_with_projection_and_gram_schmidt(qfdlib, centre, parity):
+    n, a, m, kin = 16, 0.2, 1.5, 3
+    dt = stable_dt(n, a, m, kin)
+    V = O.potential(n, a, "cornell", (0.3, 0.2), centre)
+    phi0 = O.normalize(inputs.uniform_psi(n, 1))
+    phi1 = O.normalize(O.gram_schmidt(inputs.uniform_psi(n, 2), [phi0]))
+    psi = inputs.uniform_psi(n, 3)
+    with Q.Plan(n, a, m, dt, kin, nstates=3, ortho_every=3, centre=centre) as p:
+        p.set_potential(V)
+        p.set_psi(0, phi0)
+        p.set_psi(1, phi1)
+        p.set_psi(2, psi)
+        p.set_parity(2, parity)
+        p.step(2, 9)
+        got = p.get_psi(2)
+        # the lower states are untouched
+        assert np.array_equal(p.get_psi(0), phi0)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=3, centre=centre)
+    ref, _ = O.evolve(psi, prob, 9, parity=parity, lower=(phi0, phi1))
+    assert rel_l2(got, ref) < TOL_PSI
+    assert abs(O.inner(phi0, got)) < 1e-12 and abs(O.inner(phi1, got)) < 1e-12
+    assert np.linalg.norm(O.parity_project(got, -parity, centre)) < 1e-12
+
+
+@pytest.mark.parametrize("kin", [1, 2, 3])
+@pytest.mark.parametrize("n", [16, 64])
+def test_energy_parity(qfdlib, n, kin):
+    a, m = 0.1, 1.0
+    V = O.potential(n, a, "softcoul", (0.01,))
+    psi = inputs.uniform_psi(n, 21)
+    with Q.Plan(n, a, m, stable_dt(n, a, m, kin), kin) as p:
+        p.set_potential(V)
+        p.set_psi(0, psi)
+        e, n2 = p.energy(0)
+    T = O.kinetic_symbol(n, a, m, kin)
+    assert e == pytest.approx(O.energy(psi, V, T), rel=1e-12)
+    assert n2 == pytest.approx(O.norm2(psi), rel=1e-13)
+
+
+@pytest.mark.parametrize("kin,dt", [(1, 0.001), (2, 0.002), (3, 0.002)])
+def test_solve_parity_oscillator_32(qfdlib, kin, dt):
+    # 32^3, A = 0.1, M = 1, V = r^2/2 from the box centre, uniform start (seed 1),
+    # 2000 steps, energy and normalisation every 100 steps
+    n, a, m = 32, 0.1, 1.0
+    with Q.Plan(n, a, m, dt, kin, ortho_every=100, check_every=100, max_steps=2000, tol=-1) as p:
+        p.fill_potential("ho", (1.0,))
+        p.fill_psi_uniform(0, 1)
+        es, steps, _ = p.solve_states(1)
+        psi = p.get_psi(0)
+    V = O.potential(n, a, "ho", (1.0,))
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=100, check_every=100)
+    res = O.solve_state(inputs.uniform_psi(n, 1), prob, 2000, -1)
+    assert steps[0] == res.steps == 2000
+    assert abs(es[0] - res.energy) <= TOL_E * abs(res.energy)
+    assert rel_l2(psi, res.psi) < TOL_PSI
+
+
+def test_solve_states_excited_with_parity(qfdlib):
+    # Cornell -0.3/r + 0.2 r, relativistic sqrt(p^2+m^2)-m with m = 1.5, states {even, odd, even}
+    n, a, m, kin = 16, 0.4, 1.5, 3
+    dt = stable_dt(n, a, m, kin, 0.5)
+    par = [1, -1, 1]
+    with Q.Plan(n, a, m, dt, kin, nstates=3, ortho_every=10, check_every=50, max_steps=20000, tol=1e-10) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        for s in range(3):
+            p.fill_psi_uniform(s, 100 + s)
+        es, steps, conv = p.solve_states(3, par)
+        psis = [p.get_psi(s) for s in range(3)]
+    assert conv
+    V = O.potential(n, a, "cornell", (0.3, 0.2))
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=10, check_every=50)
+    res = O.solve_states([inputs.uniform_psi(n, 100 + s) for s in range(3)], prob, 20000, 1e-10, par)
+    for s in range(3):
+        assert steps[s] == res[s].steps
+        assert abs(es[s] - res[s].energy) <= TOL_E * abs(res[s].energy)
+        assert rel_l2(psis[s], res[s].psi) < 1e-9
+    assert es[0] < es[1] < es[2]
+
+
+# ------------------------------------------------------------- complex64 ----
+
+@pytest.mark.parametrize("kin", [1, 2, 3])
+@pytest.mark.parametrize("n", [16, 64])
+def test_step_parity_c64(qfdlib, n, kin):
+    a, m = 0.1, 1.3
+    dt = stable_dt(n, a, m, kin)
+    V = O.potential(n, a, "cornell", (0.3, 0.2))
+    psi0 = inputs.uniform_psi(n, 31).astype(np.complex64).astype(np.complex128)
+    with Q.Plan(n, a, m, dt, kin, precision="c64", ortho_every=5) as p:
+        p.set_potential(V)
+        p.set_psi(0, psi0)
+        p.step(0, 10)
+        got = p.get_psi(0)
+        e, _ = p.energy(0)
+    ref, _ = O.evolve(psi0, O.Problem(n, a, m, dt, kin, V, ortho_every=5), 10)
+    assert rel_l2(got, ref) < 2e-6
+    assert e == pytest.approx(O.energy(ref, V, O.kinetic_symbol(n, a, m, kin)), rel=1e-5)
+
+
+def test_mixed_precision_solve_reaches_fp64_energy(qfdlib):
+    n, a, m, kin = 16, 0.25, 1.0, 2
+    dt = 0.01
+    kw = dict(ortho_every=20, check_every=100, max_steps=40000, tol=1e-10)
+    with Q.Plan(n, a, m, dt, kin, precision="c64_refine", tol_bulk=1e-6, **kw) as p:
+        p.fill_potential("ho", (1.0,))
+        p.fill_psi_uniform(0, 1)
+        es, steps, conv = p.solve_states(1)
+        st = p.stats(0)
+        psi = p.get_psi(0)
+    assert conv and st["steps_c64"] > 0 and st["steps_c128"] > 0
+    V = O.potential(n, a, "ho", (1.0,))
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=20, check_every=100)
+    res = O.solve_state(inputs.uniform_psi(n, 1), prob, 40000, 1e-10)
+    assert abs(es[0] - res.energy) <= TOL_E * abs(res.energy)
+    assert abs(abs(O.inner(psi, res.psi)) - 1) < 1e-8
+
+
+def test_timing_and_launch_counters(qfdlib):
+    n = 32
+    with Q.Plan(n, 0.1, 1.0, 0.001, 2, ortho_every=10) as p:
+        p.fill_potential("ho", (1.0,))
+        p.fill_psi_uniform(0, 1)
+        p.step(0, 1)
+        p.timing(True)
+        p.timing_reset()
+        p.step(0, 20)
+        cnt, ms = p.timing_query("update_x")
+        assert cnt == 20 and ms > 0
+        assert p.timing_query("z_kinetic")[0] == 20
+        assert p.launch_count() >= 80
