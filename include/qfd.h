@@ -56,9 +56,18 @@ typedef enum {
 
 /* Kinetic terms, numbered as the paper's KINTERM (Sec. 5.1). */
 enum { QFD_KIN_P2 = 1, QFD_KIN_SIN2 = 2, QFD_KIN_REL = 3 };
-/* Arithmetic of the steps: complex128; complex64; complex64 bulk followed by a
- * complex128 refinement of the same iteration (reductions are FP64 in all). */
-enum { QFD_C128 = 0, QFD_C64 = 1, QFD_C64_REFINE = 2 };
+/* Arithmetic of the steps (reductions end in FP64 in all of them):
+ *  QFD_C128          complex128 storage, native FP64 arithmetic;
+ *  QFD_C64           complex64 storage and FP32 arithmetic;
+ *  QFD_C64_REFINE    complex64 bulk to tol_bulk, then QFD_C128 steps of the
+ *                    same iteration to tol;
+ *  QFD_DF64          16 bytes per site like complex128, each real held as an
+ *                    unevaluated sum hi + lo of two FP32 numbers and all
+ *                    arithmetic done on the FP32 pipe with error-free
+ *                    transformations (relative rounding about 2^-46 per
+ *                    operation, about 2^-48 for stored values);
+ *  QFD_C64_REFINE_DF complex64 bulk, then QFD_DF64 refinement. */
+enum { QFD_C128 = 0, QFD_C64 = 1, QFD_C64_REFINE = 2, QFD_DF64 = 3, QFD_C64_REFINE_DF = 4 };
 /* Parity projection of a state (Eq. (parity)): none, P+, P-. */
 enum { QFD_PAR_NONE = 0, QFD_PAR_EVEN = 1, QFD_PAR_ODD = -1 };
 /* Potential centre (Sec. 1.3 / 5.3): the grid site (N/2, N/2, N/2) with the
@@ -81,7 +90,7 @@ typedef struct {
   int32_t kinetic;      /* QFD_KIN_* */
   int32_t rest_mass;    /* HK3 only: 1 keeps sqrt(p^2 + M^2) of Eq. (HK3); 0 subtracts M */
   int32_t nstates;      /* capacity of the state stack (1..8) */
-  int32_t precision;    /* QFD_C128, QFD_C64 or QFD_C64_REFINE */
+  int32_t precision;    /* QFD_C128, QFD_C64, QFD_C64_REFINE, QFD_DF64 or QFD_C64_REFINE_DF */
   int32_t ortho_every;  /* steps between parity / Gram-Schmidt / normalisation (>= 1) */
   int32_t check_every;  /* steps between energy checks in qfd_solve_states (>= 1) */
   int32_t centre;       /* QFD_CENTRE_* */
@@ -120,7 +129,8 @@ qfd_status qfd_fill_potential(qfd_plan_t plan, int kind, const double* coeffs, i
 qfd_status qfd_get_potential(qfd_plan_t plan, double* V, int on_device);
 
 /* Copies state `state` in (interleaved complex128, N^3 sites) and resets its
- * step counter.  In complex64 plans the values are rounded to complex64. */
+ * step counter.  Complex64 and double-float plans round the values to their
+ * representation. */
 qfd_status qfd_set_psi(qfd_plan_t plan, int state, const double* psi, int on_device);
 
 /* Fills state `state` on the device with Re, Im i.i.d. U[-1, 1) from the

@@ -1,8 +1,9 @@
 """Builds libqfd.so (the CUDA kernels and the C ABI of include/qfd.h) in-tree for sm_103a.
 
-Each translation unit is compiled by its own nvcc process in parallel, then
-linked into paper_2006_16935_gb300/libqfd.so with the CUDA runtime linked
-statically.  Rebuilds only when a source is newer than the library.
+qfd_inst.cu is compiled once per (arithmetic policy, lattice size) pair and
+every object by its own nvcc process in parallel; the objects are linked into
+paper_2006_16935_gb300/libqfd.so with the CUDA runtime linked statically.
+Rebuilds only when a source is newer than the library.
 """
 from __future__ import annotations
 
@@ -17,7 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqfd.so")
-SOURCES = ["qfd_api.cu", "qfd_k64.cu", "qfd_k32.cu"]
+POLICIES = ["DF", "F64", "F32"]  # slowest first
+SIZES = [1024, 512, 256, 128, 64, 32, 16, 8]
+UNITS = ([("qfd_inst.cu", f"inst_{p}_{n}", ["-DQFD_POLICY=" + p, f"-DQFD_N={n}"]) for p in POLICIES for n in SIZES]
+         + [("qfd_api.cu", "api", []), ("qfd_gs.cu", "gs", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -49,18 +53,20 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *FLAGS, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, name, defs = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc, *FLAGS, *ARCH, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")
         if verbose:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    workers = max(2, min(len(UNITS), os.cpu_count() or 4))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

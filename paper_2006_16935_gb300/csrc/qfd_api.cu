@@ -37,6 +37,7 @@ constexpr int FIN_THREADS = 1024;
 // ============================================================ small kernels
 namespace qfd {
 
+// Fixed-order sums of per-CTA partials, then the derived scalars of `op`.
 __global__ void __launch_bounds__(FIN_THREADS)
 k_finalize_op(const double* __restrict__ part, int nq, int count, double* __restrict__ scal, int op) {
   __shared__ double red[32];
@@ -94,18 +95,20 @@ __global__ void k_potential(double* __restrict__ V, int64_t n, double a, int kin
   }
 }
 
-// Update coefficients of Sec. 2.2 from V: complex128 {A, B dtau}, complex64
-// {B dtau, 1 - A} (1 - A = dtau V B formed in FP64 before rounding).
+// Update coefficients of Sec. 2.2 from V, per arithmetic: FP64 {A, B dtau};
+// FP32 and double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64.
 __global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double2* __restrict__ c64,
-                       float2* __restrict__ c32, int* __restrict__ bad) {
+                       dfc* __restrict__ cdf, float2* __restrict__ c32, int* __restrict__ bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i];
     const double h = 0.5 * dtau * v;
     const double den = 1.0 + h;
     if (!(den > 0.0) || !isfinite(v)) atomicOr(bad, 1);
     const double A = (1.0 - h) / den, B = 1.0 / den;
-    if (c64) c64[i] = double2{A, B * dtau};
-    if (c32) c32[i] = float2{(float)(B * dtau), (float)(dtau * v * B)};
+    const double g1 = B * dtau, g2 = dtau * v * B;
+    if (c64) c64[i] = double2{A, g1};
+    if (cdf) cdf[i] = dfc{dsplit(g1), dsplit(g2)};
+    if (c32) c32[i] = float2{(float)g1, (float)g2};
   }
 }
 
@@ -116,33 +119,29 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-template <typename C>
-__global__ void k_fill_uniform(C* __restrict__ psi, int64_t n3, uint64_t seed) {
+template <class A>
+__global__ void k_fill_uniform(typename A::C* __restrict__ psi, int64_t n3, uint64_t seed) {
   const uint64_t base = seed * 0x9E3779B97F4A7C15ull;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t z0 = splitmix64(base ^ (uint64_t)(2 * i)), z1 = splitmix64(base ^ (uint64_t)(2 * i + 1));
     const double u0 = (double)(z0 >> 11) * 0x1.0p-53, u1 = (double)(z1 >> 11) * 0x1.0p-53;
-    psi[i] = C{(decltype(C().x))(2.0 * u0 - 1.0), (decltype(C().x))(2.0 * u1 - 1.0)};
+    psi[i] = A::from_d2(double2{2.0 * u0 - 1.0, 2.0 * u1 - 1.0});
   }
 }
 
-template <typename CI, typename CO>
-__global__ void k_convert(const CI* __restrict__ in, CO* __restrict__ out, int64_t n3) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const CI v = in[i];
-    out[i] = CO{(decltype(CO().x))v.x, (decltype(CO().x))v.y};
-  }
+template <class AI, class AO>
+__global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C* __restrict__ out, int64_t n3) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = AO::from_d2(AI::to_d2(in[i]));
 }
 
 // psi *= scal[SC_SCALE] (mode 0) or 1 / sqrt(scal[SC_N2]) (mode 1).
-template <typename C>
-__global__ void k_scale(C* __restrict__ psi, int64_t n3, const double* __restrict__ scal, int mode) {
+template <class A>
+__global__ void k_scale(typename A::C* __restrict__ psi, int64_t n3, const double* __restrict__ scal, int mode) {
   const double f = mode == 0 ? scal[SC_SCALE] : 1.0 / sqrt(scal[SC_N2]);
-  using R = decltype(C().x);
-  const R fr = (R)f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    C v = psi[i];
-    psi[i] = C{v.x * fr, v.y * fr};
+    const double2 v = A::to_d2(psi[i]);
+    psi[i] = A::from_d2(double2{v.x * f, v.y * f});
   }
 }
 
@@ -156,34 +155,34 @@ struct qfd_plan_s {
   bool own_stream = false;
   std::string err;
   // device memory
-  double2* psi64 = nullptr;
-  float2* psi32 = nullptr;
-  double2* W = nullptr;
-  double2* coef64 = nullptr;
+  void* psi16 = nullptr;    // state stack, 16 bytes per site (F64 or DF)
+  float2* psi32 = nullptr;  // state stack, complex64
+  double2* W = nullptr;     // work lattice (16 bytes per site; complex64 uses half)
+  void* coef16 = nullptr;   // F64 {A, B dtau} or DF {B dtau, 1 - A}
   float2* coef32 = nullptr;
   double* V = nullptr;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
+  dfc* twdf = nullptr;
   double* ktab64 = nullptr;
   float* ktab32 = nullptr;
-  KinParams* kin_host = nullptr;
+  df* ktabdf = nullptr;
   double* partA = nullptr;
   double* partC = nullptr;
   double* partG = nullptr;
-  int npart = 0;
   int nA = 0, nC = 0;
   double* scal = nullptr;
   int* flag = nullptr;
   // host-side state
   KinParams kin{};
-  double tmax = 0.0;
+  int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
   std::vector<int64_t> t;
   std::vector<int> parity;
-  std::vector<int64_t> steps64, steps32;
+  std::vector<int64_t> steps16, steps32;
   std::vector<double> ebulk;
   int w_state = -1, w_stage = ST_NONE, w_phase = -1;
   bool pending = false;
-  int phase = 0;  // 0: complex128 buffers, 1: complex64 buffers
+  int phase = 0;  // policy id of the current arithmetic
   bool has_pot = false;
   // instrumentation
   bool timing = false;
@@ -208,25 +207,22 @@ qfd_status fail(qfd_plan_t pl, qfd_status s, const std::string& msg) {
 // Launch f() (which returns cudaError_t), bracketed by timing events when enabled.
 template <class F>
 cudaError_t run(qfd_plan_t pl, int kind, F&& f) {
-  if (pl->timing) {
-    size_t& u = pl->evused[kind];
-    auto& v = pl->ev[kind];
-    if (u + 2 > v.size()) {
-      cudaEvent_t a, b;
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      v.push_back(a);
-      v.push_back(b);
-    }
-    cudaEventRecord(v[u], pl->st);
-    cudaError_t e = f();
-    cudaEventRecord(v[u + 1], pl->st);
-    u += 2;
-    ++pl->launches;
-    return e;
-  }
   ++pl->launches;
-  return f();
+  if (!pl->timing) return f();
+  size_t& u = pl->evused[kind];
+  auto& v = pl->ev[kind];
+  if (u + 2 > v.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return cudaErrorMemoryAllocation;
+    if (cudaEventCreate(&b) != cudaSuccess) return cudaErrorMemoryAllocation;
+    v.push_back(a);
+    v.push_back(b);
+  }
+  cudaEventRecord(v[u], pl->st);
+  cudaError_t e = f();
+  cudaEventRecord(v[u + 1], pl->st);
+  u += 2;
+  return e;
 }
 
 #define QFD_RUN(kind, expr)                                                                      \
@@ -267,119 +263,134 @@ void unit_root(int64_t e, int64_t n, double* c, double* s) {
   *s = -st;
 }
 
-template <typename R> struct PhaseOf;
-template <> struct PhaseOf<double> { static constexpr int id = 0; };
-template <> struct PhaseOf<float> { static constexpr int id = 1; };
-
-template <typename R> typename CxT<R>::T* psi_of(qfd_plan_t pl, int s);
-template <> double2* psi_of<double>(qfd_plan_t pl, int s) { return pl->psi64 + (int64_t)s * pl->n3; }
-template <> float2* psi_of<float>(qfd_plan_t pl, int s) { return pl->psi32 + (int64_t)s * pl->n3; }
-template <typename R> const void* coef_of(qfd_plan_t pl) {
-  return PhaseOf<R>::id == 0 ? (const void*)pl->coef64 : (const void*)pl->coef32;
-}
-template <typename R> const void* tw_of(qfd_plan_t pl) {
-  return PhaseOf<R>::id == 0 ? (const void*)pl->tw64 : (const void*)pl->tw32;
-}
-template <typename R> const void* ktab_of(qfd_plan_t pl) {
-  return PhaseOf<R>::id == 0 ? (const void*)pl->ktab64 : (const void*)pl->ktab32;
+df host_split(double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (double)h)};
 }
 
-template <typename R>
+// ---------------------------------------------------------- policy access
+template <class A> typename A::C* psi_of(qfd_plan_t pl, int s);
+template <> double2* psi_of<F64>(qfd_plan_t pl, int s) { return (double2*)pl->psi16 + (int64_t)s * pl->n3; }
+template <> dfc* psi_of<DF>(qfd_plan_t pl, int s) { return (dfc*)pl->psi16 + (int64_t)s * pl->n3; }
+template <> float2* psi_of<F32>(qfd_plan_t pl, int s) { return pl->psi32 + (int64_t)s * pl->n3; }
+template <class A> const void* coef_of(qfd_plan_t pl) { return A::id == 1 ? (const void*)pl->coef32 : pl->coef16; }
+template <class A> const void* tw_of(qfd_plan_t pl) {
+  return A::id == 0 ? (const void*)pl->tw64 : A::id == 1 ? (const void*)pl->tw32 : (const void*)pl->twdf;
+}
+template <class A> const void* ktab_of(qfd_plan_t pl) {
+  return A::id == 0 ? (const void*)pl->ktab64 : A::id == 1 ? (const void*)pl->ktab32 : (const void*)pl->ktabdf;
+}
+
+// Runs f(policy) for the policy with id `phase`.
+template <class F>
+qfd_status with_policy(int phase, F&& f) {
+  if (phase == 0) return f(F64{});
+  if (phase == 1) return f(F32{});
+  return f(DF{});
+}
+
+template <class A>
 LaunchArgs base_args(qfd_plan_t pl) {
   LaunchArgs a;
   a.n = pl->p.n;
   a.W = pl->W;
-  a.tw = tw_of<R>(pl);
-  a.ktab = ktab_of<R>(pl);
+  a.tw = tw_of<A>(pl);
+  a.ktab = ktab_of<A>(pl);
   a.kin = &pl->kin;
-  a.coef = coef_of<R>(pl);
+  a.coef = coef_of<A>(pl);
   a.V = pl->V;
   a.stream = pl->st;
   return a;
 }
 
 qfd_status finalize(qfd_plan_t pl, const double* part, int nq, int count, int op) {
-  QFD_RUN(PASS_FINALIZE, (k_finalize_op<<<1, FIN_THREADS, 0, pl->st>>>(part, nq, count, pl->scal, op), cudaGetLastError()));
+  QFD_RUN(PASS_FINALIZE,
+          (k_finalize_op<<<1, FIN_THREADS, 0, pl->st>>>(part, nq, count, pl->scal, op), cudaGetLastError()));
   return QFD_OK;
 }
 
-// forward DFT_x of src (times the pending scale if use_scale) into W; psi_out
-// optionally receives the scaled input.  Partials of |.|^2, V|.|^2 -> partA.
-template <typename R>
-qfd_status pass_forward_x(qfd_plan_t pl, const void* src, void* psi_out, bool use_scale, int check) {
-  LaunchArgs a = base_args<R>(pl);
+// forward DFT_x of src (times the pending factor if use_scale) into W; psi_out
+// optionally receives the scaled input.  Partials per `stats` -> partA.
+template <class A>
+qfd_status pass_forward_x(qfd_plan_t pl, const void* src, void* psi_out, bool use_scale, int stats) {
+  LaunchArgs a = base_args<A>(pl);
   a.src = src;
   a.psi_out = psi_out;
   a.scale = use_scale ? pl->scal + SC_SCALE : nullptr;
   a.part = pl->partA;
-  a.check = check;
+  a.stats = stats;
   int nb = 0;
-  QFD_RUN(PASS_FWD_X, launch_forward_x<R>(a, &nb));
+  QFD_RUN(PASS_FWD_X, launch_forward_x<A>(a, &nb));
   pl->nA = nb;
   return QFD_OK;
 }
 
-template <typename R>
+template <class A>
 qfd_status advance_to_d(qfd_plan_t pl, int parseval_at_c) {
-  LaunchArgs a = base_args<R>(pl);
+  LaunchArgs a = base_args<A>(pl);
   if (pl->w_stage == ST_X) {
-    QFD_RUN(PASS_FWD_Y, launch_fft_y<R>(a, -1));
+    QFD_RUN(PASS_FWD_Y, launch_fft_y<A>(a, -1));
     pl->w_stage = ST_XY;
   }
   if (pl->w_stage == ST_XY) {
     a.part = pl->partC;
-    a.check = parseval_at_c;
+    a.stats = parseval_at_c;
     int nb = 0;
-    QFD_RUN(PASS_ZKIN, launch_zpass<R>(a, &nb));
+    QFD_RUN(PASS_ZKIN, launch_zpass<A>(a, &nb));
     pl->nC = nb;
     pl->w_stage = ST_C;
     if (parseval_at_c) return QFD_OK;  // caller reads the Parseval partials before pass D
   }
   if (pl->w_stage == ST_C) {
-    QFD_RUN(PASS_INV_Y, launch_fft_y<R>(a, +1));
+    QFD_RUN(PASS_INV_Y, launch_fft_y<A>(a, +1));
     pl->w_stage = ST_D;
   }
   return QFD_OK;
 }
 
-template <typename R>
+template <class A>
+void mark_w(qfd_plan_t pl, int s, int stage) {
+  pl->w_state = s;
+  pl->w_phase = A::id;
+  pl->w_stage = stage;
+}
+
+template <class A>
 qfd_status ensure_w(qfd_plan_t pl, int s) {
-  if (pl->w_state != s || pl->w_phase != PhaseOf<R>::id || pl->w_stage == ST_NONE) {
+  if (pl->w_state != s || pl->w_phase != A::id || pl->w_stage == ST_NONE) {
     pl->pending = false;
-    qfd_status r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 0);
+    qfd_status r = pass_forward_x<A>(pl, psi_of<A>(pl, s), nullptr, false, STATS_NONE);
     if (r != QFD_OK) return r;
-    pl->w_state = s;
-    pl->w_phase = PhaseOf<R>::id;
-    pl->w_stage = ST_X;
+    mark_w<A>(pl, s, ST_X);
   }
   return QFD_OK;
 }
 
+bool projects(qfd_plan_t pl, int s) { return s > 0 || pl->parity[s] != 0; }
+
 // Parity projection, Gram-Schmidt against states 0..s-1, normalisation.
 // With neither projection nor lower states the normalisation factor is only
 // computed here and applied by the next pass A (the update is linear).
-template <typename R>
+template <class A>
 qfd_status cadence(qfd_plan_t pl, int s, int check) {
   const int k = s;
   const int par = pl->parity[s];
   const int offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
   qfd_status r;
-  if (k > 0 || par != 0) {
+  if (projects(pl, s)) {
     if (pl->pending) return fail(pl, QFD_ERR_STATE, "internal: pending scale at projection");
-    auto* psi = psi_of<R>(pl, s);
-    auto* lower = psi_of<R>(pl, 0);
+    auto* psi = psi_of<A>(pl, s);
+    auto* lower = psi_of<A>(pl, 0);
     if (k > 0) {
-      QFD_RUN(PASS_GS_DOTS, launch_gs_dots<R>(psi, lower, k, par, offgrid, pl->p.n, pl->partG, GS_BLOCKS, pl->st));
+      QFD_RUN(PASS_GS_DOTS, launch_gs_dots<A>(psi, lower, k, par, offgrid, pl->p.n, pl->partG, GS_BLOCKS, pl->st));
       if ((r = finalize(pl, pl->partG, 2 * k, GS_BLOCKS, OP_SUMS)) != QFD_OK) return r;
     }
-    QFD_RUN(PASS_GS_APPLY, launch_gs_apply<R>(psi, lower, pl->scal + SC_SUMS, k, par, offgrid, pl->p.n, pl->W, pl->V,
+    QFD_RUN(PASS_GS_APPLY, launch_gs_apply<A>(psi, lower, pl->scal + SC_SUMS, k, par, offgrid, pl->p.n, pl->W, pl->V,
                                               pl->partG, 0, GS_BLOCKS, pl->st));
     if ((r = finalize(pl, pl->partG, 2, GS_BLOCKS, OP_NORM)) != QFD_OK) return r;
-    if ((r = pass_forward_x<R>(pl, pl->W, psi, true, check)) != QFD_OK) return r;
+    if ((r = pass_forward_x<A>(pl, pl->W, psi, true, check ? STATS_FULL : STATS_NONE)) != QFD_OK) return r;
     if (check && (r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
-    pl->w_state = s;
-    pl->w_phase = PhaseOf<R>::id;
-    pl->w_stage = ST_X;
+    mark_w<A>(pl, s, ST_X);
     pl->pending = false;
     return QFD_OK;
   }
@@ -388,24 +399,29 @@ qfd_status cadence(qfd_plan_t pl, int s, int check) {
   return QFD_OK;
 }
 
-template <typename R>
+template <class A>
 qfd_status step_once(qfd_plan_t pl, int s, int check) {
   qfd_status r;
-  if ((r = ensure_w<R>(pl, s)) != QFD_OK) return r;
-  if ((r = advance_to_d<R>(pl, 0)) != QFD_OK) return r;
-  LaunchArgs a = base_args<R>(pl);
-  a.psi = psi_of<R>(pl, s);
+  if ((r = ensure_w<A>(pl, s)) != QFD_OK) return r;
+  if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) return r;
+  const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
+  const bool proj = projects(pl, s);
+  int stats = STATS_NONE;
+  if (ortho_next && !proj) stats = check ? STATS_FULL : STATS_NORM;
+  else if (check && !(ortho_next && proj)) stats = STATS_FULL;
+  LaunchArgs a = base_args<A>(pl);
+  a.psi = psi_of<A>(pl, s);
   a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
   a.part = pl->partA;
-  a.check = check;
+  a.stats = stats;
   int nb = 0;
-  QFD_RUN(PASS_UPDATE_X, launch_update_x<R>(a, &nb));
+  QFD_RUN(PASS_UPDATE_X, launch_update_x<A>(a, &nb));
   pl->nA = nb;
   pl->pending = false;
   pl->w_stage = ST_X;
   pl->t[s] += 1;
   if (pl->t[s] % pl->p.ortho_every == 0) {
-    if ((r = cadence<R>(pl, s, check)) != QFD_OK) return r;
+    if ((r = cadence<A>(pl, s, check)) != QFD_OK) return r;
   } else if (check) {
     if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
   }
@@ -413,10 +429,10 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
 }
 
 // Applies a pending normalisation factor to the stored state (W is dropped).
-template <typename R>
+template <class A>
 qfd_status materialize(qfd_plan_t pl, int s) {
   if (pl->pending) {
-    QFD_RUN(PASS_OTHER, (k_scale<<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<R>(pl, s), pl->n3, pl->scal, 0),
+    QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal, 0),
                          cudaGetLastError()));
     pl->pending = false;
     pl->w_stage = ST_NONE;
@@ -426,11 +442,11 @@ qfd_status materialize(qfd_plan_t pl, int s) {
 
 // Energy of the state whose partials (N2, PV) were just finalised and whose
 // x-transform sits in W: passes B and C (with the Parseval sum), then E.
-template <typename R>
+template <class A>
 qfd_status energy_tail(qfd_plan_t pl, double* E, double* n2) {
   qfd_status r;
   if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
-  if ((r = advance_to_d<R>(pl, 1)) != QFD_OK) return r;
+  if ((r = advance_to_d<A>(pl, 1)) != QFD_OK) return r;
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   double h[SC_COUNT];
   QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
@@ -440,44 +456,38 @@ qfd_status energy_tail(qfd_plan_t pl, double* E, double* n2) {
   return QFD_OK;
 }
 
-template <typename R>
+template <class A>
 qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
   qfd_status r;
-  if ((r = materialize<R>(pl, s)) != QFD_OK) return r;
-  if ((r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 1)) != QFD_OK) return r;
-  pl->w_state = s;
-  pl->w_phase = PhaseOf<R>::id;
-  pl->w_stage = ST_X;
+  if ((r = materialize<A>(pl, s)) != QFD_OK) return r;
+  if ((r = pass_forward_x<A>(pl, psi_of<A>(pl, s), nullptr, false, STATS_FULL)) != QFD_OK) return r;
+  mark_w<A>(pl, s, ST_X);
   if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
-  return energy_tail<R>(pl, E, n2);
+  return energy_tail<A>(pl, E, n2);
 }
 
 // One state in one arithmetic: cadence at t = 0, then blocks of check_every
 // steps, each followed by the energy and the relative-change test.
-template <typename R>
+template <class A>
 qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, double* E_out, int64_t* steps,
                        bool* converged) {
   qfd_status r;
   pl->t[s] = 0;
   pl->pending = false;
   pl->w_stage = ST_NONE;
-  if (s > 0 || pl->parity[s] != 0) {
-    if ((r = cadence<R>(pl, s, 0)) != QFD_OK) return r;
-  } else {
-    if ((r = pass_forward_x<R>(pl, psi_of<R>(pl, s), nullptr, false, 0)) != QFD_OK) return r;
-    pl->w_state = s;
-    pl->w_phase = PhaseOf<R>::id;
-    pl->w_stage = ST_X;
-    if ((r = cadence<R>(pl, s, 0)) != QFD_OK) return r;
+  if (!projects(pl, s)) {
+    if ((r = pass_forward_x<A>(pl, psi_of<A>(pl, s), nullptr, false, STATS_NORM)) != QFD_OK) return r;
+    mark_w<A>(pl, s, ST_X);
   }
+  if ((r = cadence<A>(pl, s, 0)) != QFD_OK) return r;
   double e = NAN, e_prev = NAN, n2 = NAN;
   bool have_prev = false;
   *converged = false;
   const int ce = pl->p.check_every;
   while (pl->t[s] < max_steps) {
     for (int j = 0; j < ce; ++j)
-      if ((r = step_once<R>(pl, s, j == ce - 1)) != QFD_OK) return r;
-    if ((r = energy_tail<R>(pl, &e, &n2)) != QFD_OK) return r;
+      if ((r = step_once<A>(pl, s, j == ce - 1)) != QFD_OK) return r;
+    if ((r = energy_tail<A>(pl, &e, &n2)) != QFD_OK) return r;
     if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
       return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
     if (tol >= 0 && have_prev && std::fabs(e - e_prev) <= tol * std::fabs(e)) {
@@ -487,9 +497,8 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
     e_prev = e;
     have_prev = true;
   }
-  // leave the state normalised (its last finalised N2 is of the stored values
-  // times the pending factor, which equals 1 / sqrt(N2) when pending)
-  QFD_RUN(PASS_OTHER, (k_scale<<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<R>(pl, s), pl->n3, pl->scal, 1),
+  // leave the state normalised (its last finalised N2 is of the stored values)
+  QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal, 1),
                        cudaGetLastError()));
   pl->pending = false;
   pl->w_stage = ST_NONE;
@@ -498,17 +507,21 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
   return QFD_OK;
 }
 
-qfd_status convert_state(qfd_plan_t pl, int s, int to_phase) {
+// Copies state s between the 16-byte representation and complex64.
+qfd_status convert_state(qfd_plan_t pl, int s, int to_f32) {
   const int g = grid_for(pl->n3);
-  if (to_phase == 1) {
-    QFD_RUN(PASS_OTHER, (k_convert<<<g, 256, 0, pl->st>>>(pl->psi64 + s * pl->n3, pl->psi32 + s * pl->n3, pl->n3),
-                         cudaGetLastError()));
-  } else {
-    QFD_RUN(PASS_OTHER, (k_convert<<<g, 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->psi64 + s * pl->n3, pl->n3),
-                         cudaGetLastError()));
-  }
-  if (pl->w_state == s) pl->w_stage = ST_NONE;
-  return QFD_OK;
+  return with_policy(pl->arith16, [&](auto pol) -> qfd_status {
+    using A = decltype(pol);
+    if (to_f32) {
+      QFD_RUN(PASS_OTHER, (k_convert<A, F32><<<g, 256, 0, pl->st>>>(psi_of<A>(pl, s), psi_of<F32>(pl, s), pl->n3),
+                           cudaGetLastError()));
+    } else {
+      QFD_RUN(PASS_OTHER, (k_convert<F32, A><<<g, 256, 0, pl->st>>>(psi_of<F32>(pl, s), psi_of<A>(pl, s), pl->n3),
+                           cudaGetLastError()));
+    }
+    if (pl->w_state == s) pl->w_stage = ST_NONE;
+    return QFD_OK;
+  });
 }
 
 qfd_status check_state(qfd_plan_t pl, int s) {
@@ -519,7 +532,9 @@ qfd_status check_state(qfd_plan_t pl, int s) {
 
 qfd_status derive_coefficients(qfd_plan_t pl) {
   QFD_CK(cudaMemsetAsync(pl->flag, 0, sizeof(int), pl->st));
-  QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau, pl->coef64, pl->coef32,
+  double2* c64 = (pl->coef16 && pl->arith16 == 0) ? (double2*)pl->coef16 : nullptr;
+  dfc* cdf = (pl->coef16 && pl->arith16 == 2) ? (dfc*)pl->coef16 : nullptr;
+  QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau, c64, cdf, pl->coef32,
                                                                      pl->flag),
                        cudaGetLastError()));
   int bad = 0;
@@ -532,6 +547,12 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
   pl->has_pot = true;
   return QFD_OK;
 }
+
+bool uses16(int precision) { return precision != QFD_C64; }
+bool uses32(int precision) {
+  return precision == QFD_C64 || precision == QFD_C64_REFINE || precision == QFD_C64_REFINE_DF;
+}
+bool refines(int precision) { return precision == QFD_C64_REFINE || precision == QFD_C64_REFINE_DF; }
 
 }  // namespace
 
@@ -550,10 +571,10 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
     return QFD_ERR_ARG;
   }
   if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 1 || p.kinetic > 3 || p.nstates < 1 ||
-      p.nstates > MAX_LOWER || p.precision < 0 || p.precision > 2 || p.ortho_every < 1 || p.check_every < 1 ||
-      (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || p.reserved != 0 || p.max_steps < 0 ||
-      (p.rest_mass != 0 && p.rest_mass != 1)) {
-    g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 1..3; nstates 1..8; cadences >= 1)";
+      p.nstates > MAX_LOWER || p.precision < 0 || p.precision > QFD_C64_REFINE_DF || p.ortho_every < 1 ||
+      p.check_every < 1 || (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || p.reserved != 0 ||
+      p.max_steps < 0 || (p.rest_mass != 0 && p.rest_mass != 1)) {
+    g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 1..3; nstates 1..8; precision 0..4; cadences >= 1)";
     return QFD_ERR_ARG;
   }
   const int64_t n = p.n;
@@ -578,6 +599,14 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   kin.am2 = (p.a * p.mass) * (p.a * p.mass);
   kin.inv_a_n3 = 1.0 / (p.a * n3d);
   kin.m0_n3 = p.rest_mass ? 0.0 : p.mass / n3d;
+  kin.f_pref = (float)kin.pref;
+  kin.f_am2 = (float)kin.am2;
+  kin.f_ia = (float)kin.inv_a_n3;
+  kin.f_m0 = (float)kin.m0_n3;
+  kin.d_pref = host_split(kin.pref);
+  kin.d_am2 = host_split(kin.am2);
+  kin.d_ia = host_split(kin.inv_a_n3);
+  kin.d_m0 = host_split(kin.m0_n3);
   const double smax = 3.0 * kmax;
   const double tmax = p.kinetic == 3 ? std::sqrt(smax + kin.am2) / p.a - (p.rest_mass ? 0.0 : p.mass)
                                      : smax / (2.0 * p.a * p.a * p.mass);
@@ -592,13 +621,13 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->p = p;
   pl->n3 = n * n * n;
   pl->kin = kin;
-  pl->tmax = tmax;
   pl->t.assign(p.nstates, 0);
   pl->parity.assign(p.nstates, 0);
-  pl->steps64.assign(p.nstates, 0);
+  pl->steps16.assign(p.nstates, 0);
   pl->steps32.assign(p.nstates, 0);
   pl->ebulk.assign(p.nstates, NAN);
-  pl->phase = p.precision == QFD_C128 ? 0 : 1;
+  pl->arith16 = (p.precision == QFD_DF64 || p.precision == QFD_C64_REFINE_DF) ? 2 : 0;
+  pl->phase = uses32(p.precision) ? 1 : pl->arith16;
 
   auto cleanup_fail = [&](qfd_status s, const std::string& msg) {
     g_create_error = msg;
@@ -612,29 +641,33 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       return cleanup_fail(QFD_ERR_CUDA, "cudaStreamCreate failed");
     pl->own_stream = true;
   }
-  const bool need64 = p.precision != QFD_C64, need32 = p.precision != QFD_C128;
   const int64_t n3 = pl->n3;
-  const int npart = std::max(std::max(max_partials<double>(n), max_partials<float>(n)), GS_BLOCKS);
-  pl->npart = npart;
-  struct Alloc { void** ptr; size_t bytes; };
+  const int npart =
+      std::max(std::max(std::max(max_partials<F64>(n), max_partials<F32>(n)), max_partials<DF>(n)), GS_BLOCKS);
+  struct Alloc {
+    void** ptr;
+    size_t bytes;
+  };
   std::vector<Alloc> allocs = {
-      {(void**)&pl->W, (size_t)n3 * sizeof(double2)},
+      {(void**)&pl->W, (size_t)n3 * 16},
       {(void**)&pl->V, (size_t)n3 * sizeof(double)},
       {(void**)&pl->tw64, (size_t)n * sizeof(double2)},
       {(void**)&pl->tw32, (size_t)n * sizeof(float2)},
+      {(void**)&pl->twdf, (size_t)n * sizeof(dfc)},
       {(void**)&pl->ktab64, (size_t)n * sizeof(double)},
       {(void**)&pl->ktab32, (size_t)n * sizeof(float)},
+      {(void**)&pl->ktabdf, (size_t)n * sizeof(df)},
       {(void**)&pl->partA, (size_t)2 * npart * sizeof(double)},
       {(void**)&pl->partC, (size_t)npart * sizeof(double)},
       {(void**)&pl->partG, (size_t)2 * MAX_LOWER * npart * sizeof(double)},
       {(void**)&pl->scal, SC_COUNT * sizeof(double)},
       {(void**)&pl->flag, sizeof(int)},
   };
-  if (need64) {
-    allocs.push_back({(void**)&pl->psi64, (size_t)p.nstates * n3 * sizeof(double2)});
-    allocs.push_back({(void**)&pl->coef64, (size_t)n3 * sizeof(double2)});
+  if (uses16(p.precision)) {
+    allocs.push_back({(void**)&pl->psi16, (size_t)p.nstates * n3 * 16});
+    allocs.push_back({(void**)&pl->coef16, (size_t)n3 * 16});
   }
-  if (need32) {
+  if (uses32(p.precision)) {
     allocs.push_back({(void**)&pl->psi32, (size_t)p.nstates * n3 * sizeof(float2)});
     allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
   }
@@ -648,18 +681,24 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   }
   std::vector<double2> tw(n);
   std::vector<float2> tw32(n);
+  std::vector<dfc> twdf(n);
   std::vector<float> kt32(n);
+  std::vector<df> ktdf(n);
   for (int64_t e = 0; e < n; ++e) {
     double c, s;
     unit_root(e, n, &c, &s);
     tw[e] = double2{c, s};
     tw32[e] = float2{(float)c, (float)s};
+    twdf[e] = dfc{host_split(c), host_split(s)};
     kt32[e] = (float)ktab[e];
+    ktdf[e] = host_split(ktab[e]);
   }
   bool ok = cudaMemcpy(pl->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->tw32, tw32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->twdf, twdf.data(), n * sizeof(dfc), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktab64, ktab.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktab32, kt32.data(), n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(pl->ktabdf, ktdf.data(), n * sizeof(df), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess;
   if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
   *out = pl;
@@ -669,8 +708,9 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
 void qfd_destroy(qfd_plan_t pl) {
   if (!pl) return;
   if (pl->st) cudaStreamSynchronize(pl->st);
-  void* bufs[] = {pl->psi64, pl->psi32, pl->W,     pl->coef64, pl->coef32, pl->V,    pl->tw64, pl->tw32,
-                  pl->ktab64, pl->ktab32, pl->partA, pl->partC, pl->partG, pl->scal, pl->flag};
+  void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
+                  pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
+                  pl->partG, pl->scal,  pl->flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : pl->ev)
@@ -683,8 +723,8 @@ const char* qfd_last_error(qfd_plan_t pl) { return pl ? pl->err.c_str() : g_crea
 
 qfd_status qfd_set_potential(qfd_plan_t pl, const double* V, int on_device) {
   if (!pl || !V) return fail(pl, QFD_ERR_ARG, "null argument");
-  QFD_CK(cudaMemcpyAsync(pl->V, V, pl->n3 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                         pl->st));
+  QFD_CK(cudaMemcpyAsync(pl->V, V, pl->n3 * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pl->st));
   return derive_coefficients(pl);
 }
 
@@ -704,8 +744,8 @@ qfd_status qfd_fill_potential(qfd_plan_t pl, int kind, const double* coeffs, int
 qfd_status qfd_get_potential(qfd_plan_t pl, double* V, int on_device) {
   if (!pl || !V) return fail(pl, QFD_ERR_ARG, "null argument");
   if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "no potential set");
-  QFD_CK(cudaMemcpyAsync(V, pl->V, pl->n3 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                         pl->st));
+  QFD_CK(cudaMemcpyAsync(V, pl->V, pl->n3 * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pl->st));
   QFD_CK(cudaStreamSynchronize(pl->st));
   return QFD_OK;
 }
@@ -716,17 +756,21 @@ qfd_status qfd_set_psi(qfd_plan_t pl, int s, const double* psi, int on_device) {
   if (!psi) return fail(pl, QFD_ERR_ARG, "null psi");
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t bytes = pl->n3 * sizeof(double2);
-  if (pl->psi64) {
-    QFD_CK(cudaMemcpyAsync(pl->psi64 + s * pl->n3, psi, bytes, kind, pl->st));
-    if (pl->psi32) {
-      if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
-    }
+  const int g = grid_for(pl->n3);
+  if (pl->psi16 && pl->arith16 == 0) {
+    QFD_CK(cudaMemcpyAsync(psi_of<F64>(pl, s), psi, bytes, kind, pl->st));
   } else {
+    // stage the complex128 values in W, then round into the plan's representation
     QFD_CK(cudaMemcpyAsync(pl->W, psi, bytes, kind, pl->st));
-    QFD_RUN(PASS_OTHER, (k_convert<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->W, pl->psi32 + s * pl->n3, pl->n3),
-                         cudaGetLastError()));
+    if (pl->psi16)
+      QFD_RUN(PASS_OTHER,
+              (k_convert<F64, DF><<<g, 256, 0, pl->st>>>(pl->W, psi_of<DF>(pl, s), pl->n3), cudaGetLastError()));
+    else
+      QFD_RUN(PASS_OTHER,
+              (k_convert<F64, F32><<<g, 256, 0, pl->st>>>(pl->W, psi_of<F32>(pl, s), pl->n3), cudaGetLastError()));
     pl->w_stage = ST_NONE;
   }
+  if (pl->psi16 && pl->psi32 && (r = convert_state(pl, s, 1)) != QFD_OK) return r;
   pl->t[s] = 0;
   if (pl->w_state == s) pl->w_stage = ST_NONE;
   if (!on_device) QFD_CK(cudaStreamSynchronize(pl->st));  // caller may reuse its host buffer
@@ -737,10 +781,15 @@ qfd_status qfd_fill_psi_uniform(qfd_plan_t pl, int s, uint64_t seed) {
   qfd_status r = check_state(pl, s);
   if (r != QFD_OK) return r;
   const int g = grid_for(pl->n3);
-  if (pl->psi64)
-    QFD_RUN(PASS_OTHER, (k_fill_uniform<<<g, 256, 0, pl->st>>>(pl->psi64 + s * pl->n3, pl->n3, seed), cudaGetLastError()));
+  if (pl->psi16 && pl->arith16 == 0)
+    QFD_RUN(PASS_OTHER,
+            (k_fill_uniform<F64><<<g, 256, 0, pl->st>>>(psi_of<F64>(pl, s), pl->n3, seed), cudaGetLastError()));
+  if (pl->psi16 && pl->arith16 == 2)
+    QFD_RUN(PASS_OTHER,
+            (k_fill_uniform<DF><<<g, 256, 0, pl->st>>>(psi_of<DF>(pl, s), pl->n3, seed), cudaGetLastError()));
   if (pl->psi32)
-    QFD_RUN(PASS_OTHER, (k_fill_uniform<<<g, 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->n3, seed), cudaGetLastError()));
+    QFD_RUN(PASS_OTHER,
+            (k_fill_uniform<F32><<<g, 256, 0, pl->st>>>(psi_of<F32>(pl, s), pl->n3, seed), cudaGetLastError()));
   pl->t[s] = 0;
   if (pl->w_state == s) pl->w_stage = ST_NONE;
   return QFD_OK;
@@ -752,16 +801,21 @@ qfd_status qfd_get_psi(qfd_plan_t pl, int s, double* out, int on_device) {
   if (!out) return fail(pl, QFD_ERR_ARG, "null output");
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t bytes = pl->n3 * sizeof(double2);
-  if (pl->phase == 0) {
-    if ((r = materialize<double>(pl, s)) != QFD_OK) return r;
-    QFD_CK(cudaMemcpyAsync(out, pl->psi64 + s * pl->n3, bytes, kind, pl->st));
-  } else {
-    if ((r = materialize<float>(pl, s)) != QFD_OK) return r;
-    QFD_RUN(PASS_OTHER, (k_convert<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->psi32 + s * pl->n3, pl->W, pl->n3),
-                         cudaGetLastError()));
-    pl->w_stage = ST_NONE;
-    QFD_CK(cudaMemcpyAsync(out, pl->W, bytes, kind, pl->st));
-  }
+  r = with_policy(pl->phase, [&](auto pol) -> qfd_status {
+    using A = decltype(pol);
+    qfd_status q = materialize<A>(pl, s);
+    if (q != QFD_OK) return q;
+    if (A::id == 0) {
+      QFD_CK(cudaMemcpyAsync(out, psi_of<A>(pl, s), bytes, kind, pl->st));
+    } else {
+      QFD_RUN(PASS_OTHER, (k_convert<A, F64><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->W, pl->n3),
+                           cudaGetLastError()));
+      pl->w_stage = ST_NONE;
+      QFD_CK(cudaMemcpyAsync(out, pl->W, bytes, kind, pl->st));
+    }
+    return QFD_OK;
+  });
+  if (r != QFD_OK) return r;
   QFD_CK(cudaStreamSynchronize(pl->st));
   return QFD_OK;
 }
@@ -779,61 +833,60 @@ qfd_status qfd_step(qfd_plan_t pl, int s, int64_t nsteps) {
   if (r != QFD_OK) return r;
   if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before stepping");
   if (nsteps < 0) return fail(pl, QFD_ERR_ARG, "nsteps < 0");
-  for (int64_t i = 0; i < nsteps; ++i) {
-    r = pl->phase == 0 ? step_once<double>(pl, s, 0) : step_once<float>(pl, s, 0);
-    if (r != QFD_OK) return r;
-  }
-  return pl->phase == 0 ? materialize<double>(pl, s) : materialize<float>(pl, s);
+  return with_policy(pl->phase, [&](auto pol) -> qfd_status {
+    using A = decltype(pol);
+    for (int64_t i = 0; i < nsteps; ++i) {
+      qfd_status q = step_once<A>(pl, s, 0);
+      if (q != QFD_OK) return q;
+    }
+    return materialize<A>(pl, s);
+  });
 }
 
 qfd_status qfd_energy(qfd_plan_t pl, int s, double* E, double* norm2) {
   qfd_status r = check_state(pl, s);
   if (r != QFD_OK) return r;
   if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before taking the energy");
-  return pl->phase == 0 ? energy_full<double>(pl, s, E, norm2) : energy_full<float>(pl, s, E, norm2);
+  return with_policy(pl->phase, [&](auto pol) -> qfd_status { return energy_full<decltype(pol)>(pl, s, E, norm2); });
 }
 
 qfd_status qfd_solve_states(qfd_plan_t pl, int nstates, const int* parity, double* E_out, int64_t* steps_out) {
   if (!pl) return QFD_ERR_ARG;
   if (nstates < 1 || nstates > pl->p.nstates) return fail(pl, QFD_ERR_ARG, "nstates out of range");
   if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before solving");
+  for (int s = 0; s < nstates; ++s)
+    if (parity && (parity[s] < -1 || parity[s] > 1)) return fail(pl, QFD_ERR_ARG, "parity must be -1, 0 or 1");
+  const bool refine = refines(pl->p.precision);
   bool all_conv = true;
   for (int s = 0; s < nstates; ++s) {
-    const int par = parity ? parity[s] : 0;
-    if (par < -1 || par > 1) return fail(pl, QFD_ERR_ARG, "parity must be -1, 0 or 1");
-    pl->parity[s] = par;
+    pl->parity[s] = parity ? parity[s] : 0;
     double e = NAN;
     int64_t steps = 0;
     bool conv = false;
-    qfd_status r = QFD_OK;
-    pl->steps32[s] = pl->steps64[s] = 0;
+    qfd_status r;
+    pl->steps32[s] = pl->steps16[s] = 0;
     pl->ebulk[s] = NAN;
-    if (pl->p.precision == QFD_C128) {
-      pl->phase = 0;
-      r = solve_phase<double>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
-      pl->steps64[s] = steps;
-    } else if (pl->p.precision == QFD_C64) {
-      pl->phase = 1;
-      r = solve_phase<float>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
-      pl->steps32[s] = steps;
-    } else {
+    if (refine) {
+      // complex64 bulk to tol_bulk, then the 16-byte arithmetic to tol
       pl->phase = 1;
       if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
-      r = solve_phase<float>(pl, s, pl->p.tol_bulk, pl->p.max_steps, &e, &steps, &conv);
-      if (r != QFD_OK) return r;
+      if ((r = solve_phase<F32>(pl, s, pl->p.tol_bulk, pl->p.max_steps, &e, &steps, &conv)) != QFD_OK) return r;
       pl->steps32[s] = steps;
       pl->ebulk[s] = e;
       if ((r = convert_state(pl, s, 0)) != QFD_OK) return r;
-      pl->phase = 0;
-      r = solve_phase<double>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
-      if (r != QFD_OK) return r;
-      pl->steps64[s] = steps;
-      if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;  // lower state for later complex64 phases
-      steps = pl->steps32[s] + pl->steps64[s];
+      pl->phase = pl->arith16;
+    } else {
+      pl->phase = uses32(pl->p.precision) ? 1 : pl->arith16;
     }
+    r = with_policy(pl->phase, [&](auto pol) -> qfd_status {
+      return solve_phase<decltype(pol)>(pl, s, pl->p.tol, pl->p.max_steps, &e, &steps, &conv);
+    });
     if (r != QFD_OK) return r;
+    if (pl->phase == 1) pl->steps32[s] = steps;
+    else pl->steps16[s] = steps;
+    if (refine && (r = convert_state(pl, s, 1)) != QFD_OK) return r;  // lower state for later bulk phases
     if (E_out) E_out[s] = e;
-    if (steps_out) steps_out[s] = steps;
+    if (steps_out) steps_out[s] = pl->steps32[s] + pl->steps16[s];
     if (pl->p.tol >= 0 && !conv) all_conv = false;
   }
   QFD_CK(cudaStreamSynchronize(pl->st));
@@ -854,7 +907,7 @@ qfd_status qfd_get_stats(qfd_plan_t pl, int s, int64_t* steps_c64, int64_t* step
   qfd_status r = check_state(pl, s);
   if (r != QFD_OK) return r;
   if (steps_c64) *steps_c64 = pl->steps32[s];
-  if (steps_c128) *steps_c128 = pl->steps64[s];
+  if (steps_c128) *steps_c128 = pl->steps16[s];
   if (e_bulk) *e_bulk = pl->ebulk[s];
   return QFD_OK;
 }

@@ -13,9 +13,18 @@
 //
 // Every line transform is a radix-8/4/2 Stockham FFT held in registers:
 // thread t of a line owns the 8 elements t + m*N/8 (m = 0..7) before and after
-// the transform, stages exchange through shared memory.  Complex data is
-// double2 (complex128) or float2 (complex64); every reduction accumulates in
-// FP64 and combines per-CTA partials in a fixed order (deterministic).
+// the transform, stages exchange through shared memory.
+//
+// Three arithmetic policies share the code:
+//   F64  complex128 (double2), native FP64 arithmetic;
+//   F32  complex64 (float2), FP32 arithmetic;
+//   DF   complex stored as double-float pairs (hi + lo FP32, 16 bytes like
+//        complex128), arithmetic on the FP32 pipe with error-free
+//        transformations (two-sum, FMA two-product): about 2^-46 relative
+//        rounding per operation.  GB300 issues FP32 ~58x faster than FP64.
+// Reductions always end in FP64: per-thread partials of |psi|^2 are exact
+// double-float sums (F32/DF) or FP64 (F64), converted to double once per
+// thread, then combined per CTA and across CTAs in a fixed order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,11 +32,7 @@
 
 namespace qfd {
 
-// ------------------------------------------------------------------ complex
-template <typename R> struct CxT;
-template <> struct CxT<double> { using T = double2; };
-template <> struct CxT<float> { using T = float2; };
-
+// ============================================================ float/double
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
 template <typename C> __device__ __forceinline__ C cmul(C a, C w) {
@@ -37,7 +42,6 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C w) {  // a * con
   return C{fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y)};
 }
 template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return C{a.x * s, a.y * s}; }
-
 // multiply by -i (DIR = -1, forward) or +i (DIR = +1, inverse)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   return DIR > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
@@ -48,6 +52,211 @@ template <int DIR, typename C> __device__ __forceinline__ C mul_w8(C a) {
   const R h = R(0.70710678118654752440084436210485);
   return DIR > 0 ? C{(a.x - a.y) * h, (a.x + a.y) * h} : C{(a.x + a.y) * h, (a.y - a.x) * h};
 }
+
+// ============================================================ double-float
+// Error-free transformations (Knuth two-sum, Dekker fast-two-sum, FMA
+// two-product) with round-to-nearest intrinsics so that nothing is contracted
+// or reassociated.
+struct df {
+  float h, l;
+};
+struct __align__(16) dfc {
+  df x, y;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return df{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df dneg(df a) { return df{-a.h, -a.l}; }
+// a + b with error below ~2^-45 (|a| + |b|)
+__device__ __forceinline__ df dadd(df a, df b) {
+  const df s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ df dsub(df a, df b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ df dmul(df a, df b) {
+  const df p = two_prod(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.l, p.l);
+  e = __fmaf_rn(a.l, b.h, e);
+  return fast_two_sum(p.h, e);
+}
+// a*b - c*d and a*b + c*d with one renormalisation
+__device__ __forceinline__ df dmul_sub(df a, df b, df c, df d) {
+  const df p = two_prod(a.h, b.h), q = two_prod(c.h, d.h);
+  const df s = two_sum(p.h, -q.h);
+  float e = __fadd_rn(s.l, __fsub_rn(p.l, q.l));
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  e = __fmaf_rn(-c.h, d.l, e);
+  e = __fmaf_rn(-c.l, d.h, e);
+  return fast_two_sum(s.h, e);
+}
+__device__ __forceinline__ df dmul_add(df a, df b, df c, df d) { return dmul_sub(a, b, dneg(c), d); }
+__device__ __forceinline__ df dsqrt(df a) {
+  if (!(a.h > 0.f)) return df{0.f, 0.f};
+  const float s = sqrtf(a.h);
+  const df s2 = two_prod(s, s);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, s2.h), s2.l), a.l);
+  return fast_two_sum(s, __fmul_rn(r, __fdiv_rn(0.5f, s)));
+}
+__device__ __forceinline__ df dsplit(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dval(df a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc{dadd(a.x, b.x), dadd(a.y, b.y)}; }
+__device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc{dsub(a.x, b.x), dsub(a.y, b.y)}; }
+__device__ __forceinline__ dfc cmul(dfc a, dfc w) {
+  return dfc{dmul_sub(a.x, w.x, a.y, w.y), dmul_add(a.x, w.y, a.y, w.x)};
+}
+__device__ __forceinline__ dfc cmulc(dfc a, dfc w) {
+  return dfc{dmul_add(a.x, w.x, a.y, w.y), dmul_sub(a.y, w.x, a.x, w.y)};
+}
+__device__ __forceinline__ dfc cscale(dfc a, df s) { return dfc{dmul(a.x, s), dmul(a.y, s)}; }
+template <int DIR> __device__ __forceinline__ dfc mul_i(dfc a) {
+  return DIR > 0 ? dfc{dneg(a.y), a.x} : dfc{a.y, dneg(a.x)};
+}
+template <int DIR> __device__ __forceinline__ dfc mul_w8(dfc a) {
+  const df h{0.70710677f, 1.2101617486e-08f};  // sqrt(1/2) = h.h + h.l to 2^-51
+  return DIR > 0 ? dfc{dmul(dsub(a.x, a.y), h), dmul(dadd(a.x, a.y), h)}
+                 : dfc{dmul(dadd(a.x, a.y), h), dmul(dsub(a.y, a.x), h)};
+}
+
+// ================================================================ policies
+struct KinParams {
+  int kinterm;      // 1, 2, 3 (Eqs. HK1-HK3)
+  double pref;      // HK1/HK2: 1 / (2 A^2 M N^3)
+  double am2;       // (A M)^2 (HK3)
+  double inv_a_n3;  // 1 / (A N^3) (HK3)
+  double m0_n3;     // M / N^3 subtracted when the rest mass is removed (HK3)
+  float f_pref, f_am2, f_ia, f_m0;      // the same rounded to FP32
+  df d_pref, d_am2, d_ia, d_m0;         // the same as double-float pairs
+};
+
+struct F64 {
+  using C = double2;  // lattice element
+  using K = double2;  // update coefficients {A, B dtau}
+  using T = double;   // per-axis kinetic table entry
+  using S = double;   // scalar
+  static constexpr int id = 0;
+  static __device__ __forceinline__ C ldtw(const C* p) { return __ldg(p); }
+  static __device__ __forceinline__ T kadd(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T kin(T s, const KinParams& kp) {
+    return kp.kinterm == 3 ? sqrt(s + kp.am2) * kp.inv_a_n3 - kp.m0_n3 : s * kp.pref;
+  }
+  static __device__ __forceinline__ S scalar(double s) { return s; }
+  // Eq. (iter_proced) as printed: A psi - (B dtau) H_K psi
+  static __device__ __forceinline__ C update(C ps, C hk, K cf) {
+    return C{cf.x * ps.x - cf.y * hk.x, cf.x * ps.y - cf.y * hk.y};
+  }
+  static __device__ __forceinline__ double2 to_d2(C v) { return v; }
+  static __device__ __forceinline__ C from_d2(double2 v) { return v; }
+  static __device__ __forceinline__ double norm2_d(C v) { return v.x * v.x + v.y * v.y; }
+  static __device__ __forceinline__ double tval(T t) { return t; }
+  struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add_norm(C v) { s += v.x * v.x + v.y * v.y; }
+    __device__ __forceinline__ double value() const { return s; }
+  };
+};
+
+struct F32 {
+  using C = float2;
+  using K = float2;  // {B dtau, 1 - A}
+  using T = float;
+  using S = float;
+  static constexpr int id = 1;
+  static __device__ __forceinline__ C ldtw(const C* p) { return __ldg(p); }
+  static __device__ __forceinline__ T kadd(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T kin(T s, const KinParams& kp) {
+    return kp.kinterm == 3 ? sqrtf(s + kp.f_am2) * kp.f_ia - kp.f_m0 : s * kp.f_pref;
+  }
+  static __device__ __forceinline__ S scalar(double s) { return (float)s; }
+  // psi - ((1 - A) psi + (B dtau) H_K psi): the O(dtau) increment keeps FP32 relative precision
+  static __device__ __forceinline__ C update(C ps, C hk, K cf) {
+    return C{ps.x - (cf.y * ps.x + cf.x * hk.x), ps.y - (cf.y * ps.y + cf.x * hk.y)};
+  }
+  static __device__ __forceinline__ double2 to_d2(C v) { return double2{(double)v.x, (double)v.y}; }
+  static __device__ __forceinline__ C from_d2(double2 v) { return C{(float)v.x, (float)v.y}; }
+  static __device__ __forceinline__ double norm2_d(C v) {
+    return (double)v.x * v.x + (double)v.y * v.y;
+  }
+  static __device__ __forceinline__ double tval(T t) { return t; }
+  struct Acc {  // exact double-float accumulation of the squares
+    df s{0.f, 0.f};
+    __device__ __forceinline__ void add_norm(C v) {
+      const df a = two_prod(v.x, v.x), b = two_prod(v.y, v.y);
+      s = dadd(s, dadd(a, b));
+    }
+    __device__ __forceinline__ double value() const { return dval(s); }
+  };
+};
+
+struct DF {
+  using C = dfc;
+  using K = dfc;  // {B dtau, 1 - A} as double-float pairs
+  using T = df;
+  using S = df;
+  static constexpr int id = 2;
+  static __device__ __forceinline__ C ldtw(const C* p) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    return dfc{df{q.x, q.y}, df{q.z, q.w}};
+  }
+  static __device__ __forceinline__ T kadd(T a, T b) { return dadd(a, b); }
+  static __device__ __forceinline__ T kin(T s, const KinParams& kp) {
+    return kp.kinterm == 3 ? dsub(dmul(dsqrt(dadd(s, kp.d_am2)), kp.d_ia), kp.d_m0) : dmul(s, kp.d_pref);
+  }
+  static __device__ __forceinline__ S scalar(double s) { return dsplit(s); }
+  static __device__ __forceinline__ C update(C ps, C hk, K cf) {
+    const df dx = dmul_add(cf.y, ps.x, cf.x, hk.x), dy = dmul_add(cf.y, ps.y, cf.x, hk.y);
+    return dfc{dsub(ps.x, dx), dsub(ps.y, dy)};
+  }
+  static __device__ __forceinline__ double2 to_d2(C v) { return double2{dval(v.x), dval(v.y)}; }
+  static __device__ __forceinline__ C from_d2(double2 v) { return dfc{dsplit(v.x), dsplit(v.y)}; }
+  static __device__ __forceinline__ double norm2_d(C v) {
+    const double2 d = to_d2(v);
+    return d.x * d.x + d.y * d.y;
+  }
+  static __device__ __forceinline__ double tval(T t) { return dval(t); }
+  struct Acc {
+    df s{0.f, 0.f};
+    __device__ __forceinline__ void add_norm(C v) {
+      // |v|^2 = xh^2 + 2 xh xl + yh^2 + 2 yh yl (+ O(2^-48))
+      const df a = two_prod(v.x.h, v.x.h), b = two_prod(v.y.h, v.y.h);
+      df t = two_sum(a.h, b.h);
+      float e = __fadd_rn(t.l, __fadd_rn(a.l, b.l));
+      e = __fmaf_rn(2.f * v.x.h, v.x.l, e);
+      e = __fmaf_rn(2.f * v.y.h, v.y.l, e);
+      s = dadd(s, fast_two_sum(t.h, e));
+    }
+    __device__ __forceinline__ double value() const { return dval(s); }
+  };
+};
+
+// ============================================================ FFT planning
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// N = 2^p: floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
+template <int N> struct FftPlan {
+  static constexpr int P = ilog2c(N);
+  static constexpr int Q = P / 3;
+  static constexpr int REM = P % 3;
+  static constexpr int S = Q + (REM ? 1 : 0);
+  __host__ __device__ static constexpr int radix(int i) { return i < Q ? 8 : (REM == 1 ? 2 : 4); }
+  __host__ __device__ static constexpr int ns(int i) { return i == 0 ? 1 : ns(i - 1) * radix(i - 1); }
+};
 
 template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
   C t = a;
@@ -80,24 +289,12 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   x[7] = csub(e3, o3);
 }
 
-// ------------------------------------------------------------ FFT planning
-__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
-
-// N = 2^p: floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
-template <int N> struct FftPlan {
-  static constexpr int P = ilog2c(N);
-  static constexpr int Q = P / 3;
-  static constexpr int REM = P % 3;
-  static constexpr int S = Q + (REM ? 1 : 0);
-  __host__ __device__ static constexpr int radix(int i) { return i < Q ? 8 : (REM == 1 ? 2 : 4); }
-  __host__ __device__ static constexpr int ns(int i) { return i == 0 ? 1 : ns(i - 1) * radix(i - 1); }
-};
-
 // One Stockham stage on the register-resident canonical set v[m] = x[t + m N/8].
 // Butterfly b = t + u N/8 (u < 8/RAD) takes x[b + r N/RAD] = v[u + r (8/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
-template <typename C, int N, int RAD, int NS, int DIR>
-__device__ __forceinline__ void stage_compute(C (&v)[8], int t, const C* __restrict__ tw) {
+template <class A, int N, int RAD, int NS, int DIR>
+__device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw) {
+  using C = typename A::C;
   constexpr int NB = 8 / RAD;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
@@ -109,7 +306,7 @@ __device__ __forceinline__ void stage_compute(C (&v)[8], int t, const C* __restr
       const int e0 = (b % NS) * (N / (NS * RAD));
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        const C w = __ldg(&tw[e0 * r]);
+        const C w = A::ldtw(&tw[e0 * r]);
         x[r] = DIR < 0 ? cmul(x[r], w) : cmulc(x[r], w);
       }
     }
@@ -138,24 +335,26 @@ __device__ __forceinline__ void stage_exchange(C (&v)[8], int t, Acc& acc) {
   __syncthreads();
 }
 
-template <typename C, int N, int DIR, int I, class Acc>
-__device__ __forceinline__ void fft_stages(C (&v)[8], int t, const C* __restrict__ tw, Acc& acc) {
+template <class A, int N, int DIR, int I, class Acc>
+__device__ __forceinline__ void fft_stages(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
+                                           Acc& acc) {
   if constexpr (I < FftPlan<N>::S) {
     constexpr int RAD = FftPlan<N>::radix(I);
     constexpr int NS = FftPlan<N>::ns(I);
-    stage_compute<C, N, RAD, NS, DIR>(v, t, tw);
-    if constexpr (I + 1 < FftPlan<N>::S) stage_exchange<C, N, RAD, NS>(v, t, acc);
-    fft_stages<C, N, DIR, I + 1>(v, t, tw, acc);
+    stage_compute<A, N, RAD, NS, DIR>(v, t, tw);
+    if constexpr (I + 1 < FftPlan<N>::S) stage_exchange<typename A::C, N, RAD, NS>(v, t, acc);
+    fft_stages<A, N, DIR, I + 1>(v, t, tw, acc);
   }
 }
 
 // Unnormalised length-N DFT, sign DIR, canonical layout in and out.
-template <typename C, int N, int DIR, class Acc>
-__device__ __forceinline__ void fft_line(C (&v)[8], int t, const C* __restrict__ tw, Acc& acc) {
-  fft_stages<C, N, DIR, 0>(v, t, tw, acc);
+template <class A, int N, int DIR, class Acc>
+__device__ __forceinline__ void fft_line(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
+                                         Acc& acc) {
+  fft_stages<A, N, DIR, 0>(v, t, tw, acc);
 }
 
-// Shared-memory views. Tile of C_ columns of a strided axis: [pos][col].
+// Shared-memory views. Tile of CW columns of a strided axis: [pos][col].
 template <typename C, int CW> struct AccTile {
   C* sm;
   int col;
@@ -168,12 +367,12 @@ template <typename C> struct AccLine {
 };
 
 // ---------------------------------------------------------- launch shapes
-template <typename R, int N> struct Shape {
-  static constexpr int T = N / 8;                       // threads per line
-  static constexpr int CMIN = sizeof(R) == 8 ? 8 : 16;  // 128-byte row segments
+template <class A, int N> struct Shape {
+  static constexpr int T = N / 8;                                     // threads per line
+  static constexpr int CMIN = sizeof(typename A::C) >= 16 ? 8 : 16;   // 128-byte row segments
   static constexpr int C0 = (256 / T > CMIN) ? 256 / T : CMIN;
   static constexpr int C1 = C0 < 1024 / T ? C0 : 1024 / T;
-  static constexpr int COLS = C1 < N ? C1 : N;          // strided-tile columns
+  static constexpr int COLS = C1 < N ? C1 : N;  // strided-tile columns
   static constexpr int TILE_THREADS = T * COLS;
   static constexpr int LINES0 = (256 / T) > 1 ? 256 / T : 1;
   static constexpr int LINES = LINES0 < N * N ? LINES0 : N * N;  // z-pass lines per CTA
@@ -223,50 +422,23 @@ __device__ __forceinline__ void block_reduce_store(double (&val)[NQ], double* __
   }
 }
 
-// ------------------------------------------------------------ parameters
-struct KinParams {
-  int kinterm;       // 1, 2, 3 (Eqs. HK1-HK3)
-  double pref;       // HK1/HK2: 1 / (2 A^2 M N^3)
-  double am2;        // (A M)^2 (HK3)
-  double inv_a_n3;   // 1 / (A N^3) (HK3)
-  double m0_n3;      // M / N^3 subtracted when the rest mass is removed (HK3)
-};
-
-template <typename R>
-__device__ __forceinline__ R kin_value(R s, const KinParams& kp) {
-  if (kp.kinterm == 3) return sqrt(s + R(kp.am2)) * R(kp.inv_a_n3) - R(kp.m0_n3);
-  return s * R(kp.pref);
-}
-
-// Update coefficients: complex128 stores {A, B dtau} and forms A psi - (B dtau) H_K psi
-// as printed; complex64 stores {B dtau, 1 - A} and forms psi - (1-A) psi - (B dtau) H_K psi
-// so that the O(dtau) increment keeps full FP32 relative precision.
-template <typename R> struct Coef;
-template <> struct Coef<double> { using T = double2; };
-template <> struct Coef<float> { using T = float2; };
-
-template <typename C, typename K>
-__device__ __forceinline__ C update_site(C ps, C hk, K cf);
-template <>
-__device__ __forceinline__ double2 update_site<double2, double2>(double2 ps, double2 hk, double2 cf) {
-  return double2{cf.x * ps.x - cf.y * hk.x, cf.x * ps.y - cf.y * hk.y};
-}
-template <>
-__device__ __forceinline__ float2 update_site<float2, float2>(float2 ps, float2 hk, float2 cf) {
-  return float2{ps.x - (cf.y * ps.x + cf.x * hk.x), ps.y - (cf.y * ps.y + cf.x * hk.y)};
-}
+// Partial-sum modes of the passes that write psi (pass A and forward x):
+//   STATS_NONE  no reduction (the common step)
+//   STATS_NORM  sum |psi|^2 (steps that end in a normalisation)
+//   STATS_FULL  sum |psi|^2 and sum V |psi|^2 (energy checks; FP64 per site)
+enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 
 // ================================================================ kernels
 
-// Pass B / D (and the x-direction forward transform of a fresh psi when src
-// is given): in-place strided line FFT over tiles of COLS contiguous columns.
-// Tile id -> base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
-template <typename R, int N, int DIR>
-__global__ void __launch_bounds__(Shape<R, N>::TILE_THREADS)
-k_fft_strided(typename CxT<R>::T* W, const typename CxT<R>::T* __restrict__ tw, int64_t stride,
-              int tiles_inner, int64_t outer_stride) {
-  using C = typename CxT<R>::T;
-  using SH = Shape<R, N>;
+// Pass B / D (and the plain x transform): in-place strided line FFT over tiles
+// of COLS contiguous columns.  Tile id ->
+// base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
+template <class A, int N, int DIR>
+__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
+              int64_t outer_stride) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
@@ -276,20 +448,21 @@ k_fft_strided(typename CxT<R>::T* W, const typename CxT<R>::T* __restrict__ tw, 
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
   AccTile<C, SH::COLS> acc{sm, col};
-  fft_line<C, N, DIR>(v, t, tw, acc);
+  fft_line<A, N, DIR>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
 }
 
-// Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial), inverse DFT_z.
-// The canonical layout is the same before and after a transform, so the
-// multiply sits in registers between the two transforms.
-template <typename R, int N>
-__global__ void __launch_bounds__(Shape<R, N>::LINE_THREADS)
-k_zpass(typename CxT<R>::T* W, const typename CxT<R>::T* __restrict__ tw, const R* __restrict__ ktab,
-        KinParams kp, double* __restrict__ part, int parseval) {
-  using C = typename CxT<R>::T;
-  using SH = Shape<R, N>;
+// Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial when PARSEVAL),
+// inverse DFT_z.  The canonical layout is the same before and after a
+// transform, so the multiply sits in registers between the two transforms.
+template <class A, int N, bool PARSEVAL>
+__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
+k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
+        KinParams kp, double* __restrict__ part) {
+  using C = typename A::C;
+  using T = typename A::T;
+  using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int l = threadIdx.x / SH::T, t = threadIdx.x % SH::T;
@@ -299,19 +472,19 @@ k_zpass(typename CxT<R>::T* W, const typename CxT<R>::T* __restrict__ tw, const 
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = p[t + m * SH::T];
   AccLine<C> acc{sm + l * SH::LPAD};
-  fft_line<C, N, -1>(v, t, tw, acc);
-  const R sxy = ktab[line / N] + ktab[line % N];
+  fft_line<A, N, -1>(v, t, tw, acc);
+  const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
   double pt = 0.0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const R tk = kin_value<R>(sxy + ktab[t + m * SH::T], kp);
-    if (parseval) pt += (double)tk * ((double)v[m].x * v[m].x + (double)v[m].y * v[m].y);
+    const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
+    if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
     v[m] = cscale(v[m], tk);
   }
-  fft_line<C, N, +1>(v, t, tw, acc);
+  fft_line<A, N, +1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
-  if (parseval) {
+  if constexpr (PARSEVAL) {
     double q[1] = {pt};
     block_reduce_store<1>(q, part);
   }
@@ -319,16 +492,15 @@ k_zpass(typename CxT<R>::T* W, const typename CxT<R>::T* __restrict__ tw, const 
 
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
 // Eq. (iter_proced) with the coefficients of Sec. 2.2 (times an optional
-// normalisation factor *scale carried from the previous step); partials of
-// sum |psi|^2 and (check) sum V |psi|^2; forward DFT_x of the new psi into W.
-template <typename R, int N>
-__global__ void __launch_bounds__(Shape<R, N>::TILE_THREADS)
-k_update_x(typename CxT<R>::T* W, typename CxT<R>::T* __restrict__ psi,
-           const typename Coef<R>::T* __restrict__ coef, const double* __restrict__ V,
-           const double* __restrict__ scale, const typename CxT<R>::T* __restrict__ tw,
-           double* __restrict__ part, int check) {
-  using C = typename CxT<R>::T;
-  using SH = Shape<R, N>;
+// normalisation factor *scale carried from the previous step); partial sums
+// per STATS; forward DFT_x of the new psi into W.
+template <class A, int N, int STATS>
+__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
+           const double* __restrict__ V, const double* __restrict__ scale, const typename A::C* __restrict__ tw,
+           double* __restrict__ part) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
@@ -338,65 +510,80 @@ k_update_x(typename CxT<R>::T* W, typename CxT<R>::T* __restrict__ psi,
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (t + m * SH::T) * S];
   AccTile<C, SH::COLS> acc{sm, col};
-  fft_line<C, N, +1>(v, t, tw, acc);
-  const R s = scale ? R(*scale) : R(1);
+  fft_line<A, N, +1>(v, t, tw, acc);
+  const bool scaled = scale != nullptr;
+  const typename A::S s = A::scalar(scaled ? *scale : 1.0);
+  typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
-    C nw = update_site(psi[idx], v[m], coef[idx]);
-    if (scale) nw = cscale(nw, s);
+    C nw = A::update(psi[idx], v[m], coef[idx]);
+    if (scaled) nw = cscale(nw, s);
     psi[idx] = nw;
     v[m] = nw;
-    const double a2 = (double)nw.x * nw.x + (double)nw.y * nw.y;
-    n2 += a2;
-    if (check) pv += V[idx] * a2;
+    if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
+    if constexpr (STATS == STATS_FULL) {
+      const double a2 = A::norm2_d(nw);
+      n2 += a2;
+      pv += V[idx] * a2;
+    }
   }
-  fft_line<C, N, -1>(v, t, tw, acc);
+  fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
-  double q[2] = {n2, pv};
-  block_reduce_store<2>(q, part);
+  if constexpr (STATS != STATS_NONE) {
+    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+    double q[2] = {n2, pv};
+    block_reduce_store<2>(q, part);
+  }
 }
 
 // Forward DFT_x of src (optionally times *scale, optionally also written to
-// psi_out) into W; partials of sum |.|^2 and sum V |.|^2 of the scaled input.
-// src may alias W (each CTA reads its whole tile before writing it).
-template <typename R, int N>
-__global__ void __launch_bounds__(Shape<R, N>::TILE_THREADS)
-k_forward_x(const typename CxT<R>::T* src, typename CxT<R>::T* W, typename CxT<R>::T* psi_out,
-            const double* __restrict__ V, const double* __restrict__ scale,
-            const typename CxT<R>::T* __restrict__ tw, double* __restrict__ part, int check) {
-  using C = typename CxT<R>::T;
-  using SH = Shape<R, N>;
+// psi_out) into W; partials per STATS of the scaled input.  src may alias W
+// (each CTA reads its whole tile before writing it).
+template <class A, int N, int STATS>
+__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, const double* __restrict__ V,
+            const double* __restrict__ scale, const typename A::C* __restrict__ tw, double* __restrict__ part) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
   const int64_t base = (int64_t)blockIdx.x * SH::COLS + col;
   constexpr int64_t S = (int64_t)N * N;
-  const R s = scale ? R(*scale) : R(1);
+  const bool scaled = scale != nullptr;
+  const typename A::S s = A::scalar(scaled ? *scale : 1.0);
   C v[8];
+  typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
     C x = src[idx];
-    if (scale) x = cscale(x, s);
+    if (scaled) x = cscale(x, s);
     v[m] = x;
-    const double a2 = (double)x.x * x.x + (double)x.y * x.y;
-    n2 += a2;
-    if (check) pv += V[idx] * a2;
+    if constexpr (STATS == STATS_NORM) nacc.add_norm(x);
+    if constexpr (STATS == STATS_FULL) {
+      const double a2 = A::norm2_d(x);
+      n2 += a2;
+      pv += V[idx] * a2;
+    }
   }
   if (psi_out) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) psi_out[base + (t + m * SH::T) * S] = v[m];
   }
   AccTile<C, SH::COLS> acc{sm, col};
-  fft_line<C, N, -1>(v, t, tw, acc);
+  fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
-  double q[2] = {n2, pv};
-  block_reduce_store<2>(q, part);
+  if constexpr (STATS != STATS_NONE) {
+    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+    double q[2] = {n2, pv};
+    block_reduce_store<2>(q, part);
+  }
 }
 
 // ------------------------------------------------- elementwise site kernels
@@ -411,27 +598,25 @@ __host__ __device__ __forceinline__ int64_t reflect_index(int64_t i, int64_t n, 
 constexpr int MAX_LOWER = 8;
 
 // Overlaps <phi_j | P psi> (FP64) for j < k, P the parity projector (Eq. parity).
-template <typename R>
-__global__ void k_gs_dots(const typename CxT<R>::T* __restrict__ psi, const typename CxT<R>::T* __restrict__ lower,
-                          int k, int parity, int offgrid, int64_t n, double* __restrict__ part) {
+template <class A>
+__global__ void k_gs_dots(const typename A::C* __restrict__ psi, const typename A::C* __restrict__ lower, int k,
+                          int parity, int offgrid, int64_t n, double* __restrict__ part) {
   const int64_t n3 = n * n * n;
   double acc[2 * MAX_LOWER];
 #pragma unroll
   for (int j = 0; j < 2 * MAX_LOWER; ++j) acc[j] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    auto p = psi[i];
-    double px = p.x, py = p.y;
+    double2 p = A::to_d2(psi[i]);
     if (parity) {
-      auto q = psi[reflect_index(i, n, offgrid)];
-      px = 0.5 * (px + parity * (double)q.x);
-      py = 0.5 * (py + parity * (double)q.y);
+      const double2 q = A::to_d2(psi[reflect_index(i, n, offgrid)]);
+      p = double2{0.5 * (p.x + parity * q.x), 0.5 * (p.y + parity * q.y)};
     }
 #pragma unroll
     for (int j = 0; j < MAX_LOWER; ++j) {
       if (j < k) {
-        auto f = lower[j * n3 + i];
-        acc[2 * j] += (double)f.x * px + (double)f.y * py;
-        acc[2 * j + 1] += (double)f.x * py - (double)f.y * px;
+        const double2 f = A::to_d2(lower[j * n3 + i]);
+        acc[2 * j] += f.x * p.x + f.y * p.y;
+        acc[2 * j + 1] += f.x * p.y - f.y * p.x;
       }
     }
   }
@@ -439,29 +624,29 @@ __global__ void k_gs_dots(const typename CxT<R>::T* __restrict__ psi, const type
 }
 
 // out = P psi - sum_j c_j phi_j  (c_j = sums[2j] + i sums[2j+1]);
-// partials of sum |out|^2 and sum V |out|^2.
-template <typename R>
-__global__ void k_gs_apply(const typename CxT<R>::T* __restrict__ psi, const typename CxT<R>::T* __restrict__ lower,
+// partials of sum |out|^2 and sum V |out|^2 (FP64).
+template <class A>
+__global__ void k_gs_apply(const typename A::C* __restrict__ psi, const typename A::C* __restrict__ lower,
                            const double* __restrict__ sums, int k, int parity, int offgrid, int64_t n,
-                           typename CxT<R>::T* __restrict__ out, const double* __restrict__ V,
-                           double* __restrict__ part, int check) {
-  using C = typename CxT<R>::T;
+                           typename A::C* __restrict__ out, const double* __restrict__ V, double* __restrict__ part,
+                           int check) {
   const int64_t n3 = n * n * n;
   double n2 = 0.0, pv = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    C p = psi[i];
+    double2 p = A::to_d2(psi[i]);
     if (parity) {
-      const C q = psi[reflect_index(i, n, offgrid)];
-      p = C{R(0.5) * (p.x + R(parity) * q.x), R(0.5) * (p.y + R(parity) * q.y)};
+      const double2 q = A::to_d2(psi[reflect_index(i, n, offgrid)]);
+      p = double2{0.5 * (p.x + parity * q.x), 0.5 * (p.y + parity * q.y)};
     }
     for (int j = 0; j < k; ++j) {
-      const C f = lower[j * n3 + i];
-      const R cr = R(sums[2 * j]), ci = R(sums[2 * j + 1]);
+      const double2 f = A::to_d2(lower[j * n3 + i]);
+      const double cr = sums[2 * j], ci = sums[2 * j + 1];
       p.x -= cr * f.x - ci * f.y;
       p.y -= cr * f.y + ci * f.x;
     }
-    out[i] = p;
-    const double a2 = (double)p.x * p.x + (double)p.y * p.y;
+    const typename A::C o = A::from_d2(p);
+    out[i] = o;
+    const double a2 = A::norm2_d(o);
     n2 += a2;
     if (check) pv += V[i] * a2;
   }

@@ -1,5 +1,9 @@
-// Host-side launchers of the device kernels, one explicit instantiation per
-// arithmetic type (qfd_k64.cu: complex128, qfd_k32.cu: complex64).
+// Host-side launchers of the device kernels.
+//
+// Launch<A, N> holds the launchers of one arithmetic policy A (F64, F32, DF)
+// and lattice size N; qfd_inst.cu is compiled once per (A, N) pair so that
+// the large unrolled kernels compile in parallel.  The launch_* templates
+// below dispatch a runtime N to those instantiations.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,6 +12,9 @@
 namespace qfd {
 
 struct KinParams;
+struct F64;
+struct F32;
+struct DF;
 
 // Which pass (used for the per-kernel timing instrumentation too).
 enum PassKind {
@@ -25,34 +32,77 @@ enum PassKind {
 
 struct LaunchArgs {
   int64_t n = 0;
-  void* W = nullptr;          // work lattice (complex)
-  void* psi = nullptr;        // state lattice (complex)
-  const void* src = nullptr;  // forward-x input (may alias W)
-  void* psi_out = nullptr;    // forward-x: where to store the scaled input (or null)
-  const void* coef = nullptr; // update coefficients (double2 / float2 per site)
-  const double* V = nullptr;  // FP64 potential
+  void* W = nullptr;           // work lattice
+  void* psi = nullptr;         // state lattice
+  const void* src = nullptr;   // forward-x input (may alias W)
+  void* psi_out = nullptr;     // forward-x: where to store the scaled input (or null)
+  const void* coef = nullptr;  // update coefficients per site
+  const double* V = nullptr;   // FP64 potential
   const double* scale = nullptr;
-  const void* tw = nullptr;   // twiddles exp(-2 pi i e / N), e < N
-  const void* ktab = nullptr; // per-axis kinetic table
-  const void* kin = nullptr;  // KinParams*
-  double* part = nullptr;     // per-CTA partials
-  int check = 0;
+  const void* tw = nullptr;    // twiddles exp(-2 pi i e / N), e < N
+  const void* ktab = nullptr;  // per-axis kinetic table
+  const KinParams* kin = nullptr;
+  double* part = nullptr;      // per-CTA partials
+  int stats = 0;               // STATS_* for passes A / forward x, Parseval flag for pass C
   cudaStream_t stream = 0;
 };
 
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the
 // number of CTAs (= partials per reduced quantity) when non-null.
-template <typename R> cudaError_t launch_update_x(const LaunchArgs& a, int* nblocks);
-template <typename R> cudaError_t launch_forward_x(const LaunchArgs& a, int* nblocks);
-template <typename R> cudaError_t launch_fft_y(const LaunchArgs& a, int dir);
-template <typename R> cudaError_t launch_fft_x_plain(const LaunchArgs& a, int dir);
-template <typename R> cudaError_t launch_zpass(const LaunchArgs& a, int* nblocks);
-template <typename R> cudaError_t launch_gs_dots(const void* psi, const void* lower, int k, int parity, int offgrid,
-                                                 int64_t n, double* part, int nblocks, cudaStream_t st);
-template <typename R> cudaError_t launch_gs_apply(const void* psi, const void* lower, const double* sums, int k,
-                                                  int parity, int offgrid, int64_t n, void* out, const double* V,
-                                                  double* part, int check, int nblocks, cudaStream_t st);
-template <typename R> int max_partials(int64_t n);  // largest CTA count of any reducing pass
+template <class A, int N> struct Launch {
+  static cudaError_t update_x(const LaunchArgs& a, int* nblocks);
+  static cudaError_t forward_x(const LaunchArgs& a, int* nblocks);
+  static cudaError_t fft_y(const LaunchArgs& a, int dir);
+  static cudaError_t zpass(const LaunchArgs& a, int* nblocks);
+  static int partials();  // largest CTA count of a reducing pass
+};
+
+template <int N> struct Tag {
+  static constexpr int value = N;
+};
+
+template <class F>
+inline cudaError_t dispatch_n(int64_t n, F&& f) {
+  switch (n) {
+    case 8: return f(Tag<8>());
+    case 16: return f(Tag<16>());
+    case 32: return f(Tag<32>());
+    case 64: return f(Tag<64>());
+    case 128: return f(Tag<128>());
+    case 256: return f(Tag<256>());
+    case 512: return f(Tag<512>());
+    case 1024: return f(Tag<1024>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class A> cudaError_t launch_update_x(const LaunchArgs& a, int* nb) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::update_x(a, nb); });
+}
+template <class A> cudaError_t launch_forward_x(const LaunchArgs& a, int* nb) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::forward_x(a, nb); });
+}
+template <class A> cudaError_t launch_fft_y(const LaunchArgs& a, int dir) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::fft_y(a, dir); });
+}
+template <class A> cudaError_t launch_zpass(const LaunchArgs& a, int* nb) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::zpass(a, nb); });
+}
+template <class A> int max_partials(int64_t n) {
+  int out = 0;
+  dispatch_n(n, [&](auto t) {
+    out = Launch<A, decltype(t)::value>::partials();
+    return cudaSuccess;
+  });
+  return out;
+}
+
+// Gram-Schmidt / parity kernels (qfd_gs.cu).
+template <class A> cudaError_t launch_gs_dots(const void* psi, const void* lower, int k, int parity, int offgrid,
+                                              int64_t n, double* part, int nblocks, cudaStream_t st);
+template <class A> cudaError_t launch_gs_apply(const void* psi, const void* lower, const double* sums, int k,
+                                               int parity, int offgrid, int64_t n, void* out, const double* V,
+                                               double* part, int check, int nblocks, cudaStream_t st);
 bool supported_n(int64_t n);
 
 }  // namespace qfd

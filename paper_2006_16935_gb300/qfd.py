@@ -23,7 +23,7 @@ OK, ERR_ARG, ERR_OOM, ERR_UNSTABLE_DT, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_
 STATUS_NAMES = {0: "QFD_OK", -1: "QFD_ERR_ARG", -2: "QFD_ERR_OOM", -3: "QFD_ERR_UNSTABLE_DT",
                 -4: "QFD_ERR_DIVERGED", -5: "QFD_ERR_TIMEOUT", -6: "QFD_ERR_CUDA",
                 -7: "QFD_ERR_NOT_CONVERGED", -8: "QFD_ERR_STATE"}
-PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2}
+PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2, "df64": 3, "c64_refine_df": 4}
 CENTRE = {"grid": 0, "offgrid": 1}
 POTENTIAL = {"zero": 0, "ho": 1, "cornell": 2, "coulomb": 3, "softcoul": 4}
 PASS_KINDS = {"update_x": 0, "fwd_y": 1, "z_kinetic": 2, "inv_y": 3, "fwd_x": 4,

@@ -29,7 +29,7 @@ def plane_wave_lattice(n, idx, amp):
     return out
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", 3e-6)])
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("df64", 1e-11), ("c64", 3e-6)])
 def test_plane_wave_step_512(qfdlib, prec, tol):
     n, a, m, kin, dt = 512, 0.05, 1.0, 2, 5e-4
     idx, amp = inputs.plane_wave_mix(n, 5, modes=4)
@@ -55,7 +55,7 @@ def test_plane_wave_step_512(qfdlib, prec, tol):
     assert err < tol
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("df64", 1e-10), ("c64", 2e-6)])
 def test_random_state_steps_256_against_library_fft_oracle(qfdlib, prec, tol):
     n, a, m, kin = 256, 0.05, 1.5, 3
     dt = 0.001
