@@ -135,16 +135,6 @@ __global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C*
     out[i] = AO::from_d2(AI::to_d2(in[i]));
 }
 
-// psi *= scal[SC_SCALE] (mode 0) or 1 / sqrt(scal[SC_N2]) (mode 1).
-template <class A>
-__global__ void k_scale(typename A::C* __restrict__ psi, int64_t n3, const double* __restrict__ scal, int mode) {
-  const double f = mode == 0 ? scal[SC_SCALE] : 1.0 / sqrt(scal[SC_N2]);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = A::to_d2(psi[i]);
-    psi[i] = A::from_d2(double2{v.x * f, v.y * f});
-  }
-}
-
 }  // namespace qfd
 
 // ================================================================== plan
@@ -154,9 +144,13 @@ struct qfd_plan_s {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   std::string err;
-  // device memory
-  void* psi16 = nullptr;    // state stack, 16 bytes per site (F64 or DF)
-  float2* psi32 = nullptr;  // state stack, complex64
+  // device memory: nstates + 1 lattices per representation; sp16/sp32 map a
+  // state to its lattice and the extra one receives each projected state
+  void* psi16 = nullptr;    // state lattices, 16 bytes per site (F64 or DF)
+  float2* psi32 = nullptr;  // state lattices, complex64
+  std::vector<char*> sp16, sp32;
+  char* spare16 = nullptr;
+  char* spare32 = nullptr;
   double2* W = nullptr;     // work lattice (16 bytes per site; complex64 uses half)
   void* coef16 = nullptr;   // F64 {A, B dtau} or DF {B dtau, 1 - A}
   float2* coef32 = nullptr;
@@ -269,10 +263,17 @@ df host_split(double x) {
 }
 
 // ---------------------------------------------------------- policy access
-template <class A> typename A::C* psi_of(qfd_plan_t pl, int s);
-template <> double2* psi_of<F64>(qfd_plan_t pl, int s) { return (double2*)pl->psi16 + (int64_t)s * pl->n3; }
-template <> dfc* psi_of<DF>(qfd_plan_t pl, int s) { return (dfc*)pl->psi16 + (int64_t)s * pl->n3; }
-template <> float2* psi_of<F32>(qfd_plan_t pl, int s) { return pl->psi32 + (int64_t)s * pl->n3; }
+template <class A> typename A::C* psi_of(qfd_plan_t pl, int s) {
+  return reinterpret_cast<typename A::C*>(A::id == 1 ? pl->sp32[s] : pl->sp16[s]);
+}
+template <class A> typename A::C* spare_of(qfd_plan_t pl) {
+  return reinterpret_cast<typename A::C*>(A::id == 1 ? pl->spare32 : pl->spare16);
+}
+// The projected state now lives in the spare lattice: swap the two roles.
+template <class A> void swap_spare(qfd_plan_t pl, int s) {
+  if (A::id == 1) std::swap(pl->sp32[s], pl->spare32);
+  else std::swap(pl->sp16[s], pl->spare16);
+}
 template <class A> const void* coef_of(qfd_plan_t pl) { return A::id == 1 ? (const void*)pl->coef32 : pl->coef16; }
 template <class A> const void* tw_of(qfd_plan_t pl) {
   return A::id == 0 ? (const void*)pl->tw64 : A::id == 1 ? (const void*)pl->tw32 : (const void*)pl->twdf;
@@ -369,30 +370,34 @@ qfd_status ensure_w(qfd_plan_t pl, int s) {
 bool projects(qfd_plan_t pl, int s) { return s > 0 || pl->parity[s] != 0; }
 
 // Parity projection, Gram-Schmidt against states 0..s-1, normalisation.
-// With neither projection nor lower states the normalisation factor is only
+// The projection (when there is one) runs fused with the forward x transform
+// into the spare lattice; in every case the normalisation factor is only
 // computed here and applied by the next pass A (the update is linear).
 template <class A>
 qfd_status cadence(qfd_plan_t pl, int s, int check) {
-  const int k = s;
-  const int par = pl->parity[s];
-  const int offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
   qfd_status r;
   if (projects(pl, s)) {
     if (pl->pending) return fail(pl, QFD_ERR_STATE, "internal: pending scale at projection");
-    auto* psi = psi_of<A>(pl, s);
-    auto* lower = psi_of<A>(pl, 0);
-    if (k > 0) {
-      QFD_RUN(PASS_GS_DOTS, launch_gs_dots<A>(psi, lower, k, par, offgrid, pl->p.n, pl->partG, GS_BLOCKS, pl->st));
-      if ((r = finalize(pl, pl->partG, 2 * k, GS_BLOCKS, OP_SUMS)) != QFD_OK) return r;
+    LaunchArgs a = base_args<A>(pl);
+    a.src = psi_of<A>(pl, s);
+    a.dst = spare_of<A>(pl);
+    a.k = s;
+    for (int j = 0; j < s; ++j) a.lower[j] = psi_of<A>(pl, j);
+    a.parity = pl->parity[s];
+    a.offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
+    a.sums = pl->scal + SC_SUMS;
+    if (s > 0) {
+      a.part = pl->partG;
+      QFD_RUN(PASS_GS_DOTS, launch_gs_dots<A>(a, GS_BLOCKS));
+      if ((r = finalize(pl, pl->partG, 2 * s, GS_BLOCKS, OP_SUMS)) != QFD_OK) return r;
     }
-    QFD_RUN(PASS_GS_APPLY, launch_gs_apply<A>(psi, lower, pl->scal + SC_SUMS, k, par, offgrid, pl->p.n, pl->W, pl->V,
-                                              pl->partG, 0, GS_BLOCKS, pl->st));
-    if ((r = finalize(pl, pl->partG, 2, GS_BLOCKS, OP_NORM)) != QFD_OK) return r;
-    if ((r = pass_forward_x<A>(pl, pl->W, psi, true, check ? STATS_FULL : STATS_NONE)) != QFD_OK) return r;
-    if (check && (r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
+    a.part = pl->partA;
+    a.stats = check ? STATS_FULL : STATS_NORM;
+    int nb = 0;
+    QFD_RUN(PASS_GS_APPLY, launch_project_x<A>(a, &nb));
+    pl->nA = nb;
+    swap_spare<A>(pl, s);
     mark_w<A>(pl, s, ST_X);
-    pl->pending = false;
-    return QFD_OK;
   }
   if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_NORM)) != QFD_OK) return r;
   pl->pending = true;
@@ -407,8 +412,8 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
   const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
   const bool proj = projects(pl, s);
   int stats = STATS_NONE;
-  if (ortho_next && !proj) stats = check ? STATS_FULL : STATS_NORM;
-  else if (check && !(ortho_next && proj)) stats = STATS_FULL;
+  if (ortho_next) stats = proj ? STATS_NONE : (check ? STATS_FULL : STATS_NORM);
+  else if (check) stats = STATS_FULL;
   LaunchArgs a = base_args<A>(pl);
   a.psi = psi_of<A>(pl, s);
   a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
@@ -432,7 +437,7 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
 template <class A>
 qfd_status materialize(qfd_plan_t pl, int s) {
   if (pl->pending) {
-    QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal, 0),
+    QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal + SC_SCALE, 0),
                          cudaGetLastError()));
     pl->pending = false;
     pl->w_stage = ST_NONE;
@@ -498,7 +503,7 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
     have_prev = true;
   }
   // leave the state normalised (its last finalised N2 is of the stored values)
-  QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal, 1),
+  QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal + SC_N2, 1),
                        cudaGetLastError()));
   pl->pending = false;
   pl->w_stage = ST_NONE;
@@ -664,11 +669,11 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       {(void**)&pl->flag, sizeof(int)},
   };
   if (uses16(p.precision)) {
-    allocs.push_back({(void**)&pl->psi16, (size_t)p.nstates * n3 * 16});
+    allocs.push_back({(void**)&pl->psi16, (size_t)(p.nstates + 1) * n3 * 16});
     allocs.push_back({(void**)&pl->coef16, (size_t)n3 * 16});
   }
   if (uses32(p.precision)) {
-    allocs.push_back({(void**)&pl->psi32, (size_t)p.nstates * n3 * sizeof(float2)});
+    allocs.push_back({(void**)&pl->psi32, (size_t)(p.nstates + 1) * n3 * sizeof(float2)});
     allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
   }
   for (auto& a : allocs) {
@@ -679,6 +684,12 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       return cleanup_fail(QFD_ERR_OOM, buf);
     }
   }
+  for (int j = 0; j < p.nstates; ++j) {
+    pl->sp16.push_back(pl->psi16 ? (char*)pl->psi16 + (size_t)j * n3 * 16 : nullptr);
+    pl->sp32.push_back(pl->psi32 ? (char*)pl->psi32 + (size_t)j * n3 * sizeof(float2) : nullptr);
+  }
+  pl->spare16 = pl->psi16 ? (char*)pl->psi16 + (size_t)p.nstates * n3 * 16 : nullptr;
+  pl->spare32 = pl->psi32 ? (char*)pl->psi32 + (size_t)p.nstates * n3 * sizeof(float2) : nullptr;
   std::vector<double2> tw(n);
   std::vector<float2> tw32(n);
   std::vector<dfc> twdf(n);

@@ -42,6 +42,10 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C w) {  // a * con
   return C{fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y)};
 }
 template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return C{a.x * s, a.y * s}; }
+// butterfly additions (double-float overloads below defer the renormalisation)
+template <typename C> __device__ __forceinline__ C cadd_l(C a, C b) { return cadd(a, b); }
+template <typename C> __device__ __forceinline__ C csub_l(C a, C b) { return csub(a, b); }
+template <typename C> __device__ __forceinline__ C cnorm(C a) { return a; }
 // multiply by -i (DIR = -1, forward) or +i (DIR = +1, inverse)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   return DIR > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
@@ -116,6 +120,18 @@ __device__ __forceinline__ df dsplit(double x) {
 }
 __device__ __forceinline__ double dval(df a) { return (double)a.h + (double)a.l; }
 
+// Lazy sum inside a butterfly: error-free two-sum of the high parts, the low
+// parts added without renormalising; cnorm renormalises the butterfly outputs.
+// Within one radix-8 butterfly the low part stays within a few ulp of the high
+// part, so the accuracy of the renormalised result is unchanged.
+__device__ __forceinline__ df dadd_l(df a, df b) {
+  const df s = two_sum(a.h, b.h);
+  return df{s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ df dsub_l(df a, df b) { return dadd_l(a, dneg(b)); }
+__device__ __forceinline__ dfc cadd_l(dfc a, dfc b) { return dfc{dadd_l(a.x, b.x), dadd_l(a.y, b.y)}; }
+__device__ __forceinline__ dfc csub_l(dfc a, dfc b) { return dfc{dsub_l(a.x, b.x), dsub_l(a.y, b.y)}; }
+__device__ __forceinline__ dfc cnorm(dfc a) { return dfc{fast_two_sum(a.x.h, a.x.l), fast_two_sum(a.y.h, a.y.l)}; }
 __device__ __forceinline__ dfc cadd(dfc a, dfc b) { return dfc{dadd(a.x, b.x), dadd(a.y, b.y)}; }
 __device__ __forceinline__ dfc csub(dfc a, dfc b) { return dfc{dsub(a.x, b.x), dsub(a.y, b.y)}; }
 __device__ __forceinline__ dfc cmul(dfc a, dfc w) {
@@ -130,8 +146,8 @@ template <int DIR> __device__ __forceinline__ dfc mul_i(dfc a) {
 }
 template <int DIR> __device__ __forceinline__ dfc mul_w8(dfc a) {
   const df h{0.70710677f, 1.2101617486e-08f};  // sqrt(1/2) = h.h + h.l to 2^-51
-  return DIR > 0 ? dfc{dmul(dsub(a.x, a.y), h), dmul(dadd(a.x, a.y), h)}
-                 : dfc{dmul(dadd(a.x, a.y), h), dmul(dsub(a.y, a.x), h)};
+  return DIR > 0 ? dfc{dmul(dsub_l(a.x, a.y), h), dmul(dadd_l(a.x, a.y), h)}
+                 : dfc{dmul(dadd_l(a.x, a.y), h), dmul(dsub_l(a.y, a.x), h)};
 }
 
 // ================================================================ policies
@@ -165,10 +181,22 @@ struct F64 {
   static __device__ __forceinline__ C from_d2(double2 v) { return v; }
   static __device__ __forceinline__ double norm2_d(C v) { return v.x * v.x + v.y * v.y; }
   static __device__ __forceinline__ double tval(T t) { return t; }
+  // (p + par q) / 2
+  static __device__ __forceinline__ C half_comb(C p, C q, int par) {
+    return par > 0 ? C{0.5 * (p.x + q.x), 0.5 * (p.y + q.y)} : C{0.5 * (p.x - q.x), 0.5 * (p.y - q.y)};
+  }
   struct Acc {
     double s = 0.0;
     __device__ __forceinline__ void add_norm(C v) { s += v.x * v.x + v.y * v.y; }
     __device__ __forceinline__ double value() const { return s; }
+  };
+  struct Dot {  // sum of conj(f) p
+    double re = 0.0, im = 0.0;
+    __device__ __forceinline__ void add(C f, C p) {
+      re += f.x * p.x + f.y * p.y;
+      im += f.x * p.y - f.y * p.x;
+    }
+    __device__ __forceinline__ double2 value() const { return double2{re, im}; }
   };
 };
 
@@ -194,6 +222,9 @@ struct F32 {
     return (double)v.x * v.x + (double)v.y * v.y;
   }
   static __device__ __forceinline__ double tval(T t) { return t; }
+  static __device__ __forceinline__ C half_comb(C p, C q, int par) {
+    return par > 0 ? C{0.5f * (p.x + q.x), 0.5f * (p.y + q.y)} : C{0.5f * (p.x - q.x), 0.5f * (p.y - q.y)};
+  }
   struct Acc {  // exact double-float accumulation of the squares
     df s{0.f, 0.f};
     __device__ __forceinline__ void add_norm(C v) {
@@ -201,6 +232,14 @@ struct F32 {
       s = dadd(s, dadd(a, b));
     }
     __device__ __forceinline__ double value() const { return dval(s); }
+  };
+  struct Dot {  // sum of conj(f) p with error-free products, double-float sums
+    df re{0.f, 0.f}, im{0.f, 0.f};
+    __device__ __forceinline__ void add(C f, C p) {
+      re = dadd(re, dadd(two_prod(f.x, p.x), two_prod(f.y, p.y)));
+      im = dadd(im, dsub(two_prod(f.x, p.y), two_prod(f.y, p.x)));
+    }
+    __device__ __forceinline__ double2 value() const { return double2{dval(re), dval(im)}; }
   };
 };
 
@@ -230,6 +269,19 @@ struct DF {
     return d.x * d.x + d.y * d.y;
   }
   static __device__ __forceinline__ double tval(T t) { return dval(t); }
+  static __device__ __forceinline__ df half(df a) { return df{0.5f * a.h, 0.5f * a.l}; }  // exact
+  static __device__ __forceinline__ C half_comb(C p, C q, int par) {
+    return par > 0 ? dfc{half(dadd(p.x, q.x)), half(dadd(p.y, q.y))}
+                   : dfc{half(dsub(p.x, q.x)), half(dsub(p.y, q.y))};
+  }
+  struct Dot {
+    df re{0.f, 0.f}, im{0.f, 0.f};
+    __device__ __forceinline__ void add(C f, C p) {
+      re = dadd(re, dmul_add(f.x, p.x, f.y, p.y));
+      im = dadd(im, dmul_sub(f.x, p.y, f.y, p.x));
+    }
+    __device__ __forceinline__ double2 value() const { return double2{dval(re), dval(im)}; }
+  };
   struct Acc {
     df s{0.f, 0.f};
     __device__ __forceinline__ void add_norm(C v) {
@@ -260,16 +312,16 @@ template <int N> struct FftPlan {
 
 template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
   C t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+  a = cadd_l(t, b);
+  b = csub_l(t, b);
 }
 template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
-  C s0 = cadd(x0, x2), d0 = csub(x0, x2);
-  C s1 = cadd(x1, x3), d1 = mul_i<DIR>(csub(x1, x3));
-  x0 = cadd(s0, s1);
-  x2 = csub(s0, s1);
-  x1 = cadd(d0, d1);
-  x3 = csub(d0, d1);
+  C s0 = cadd_l(x0, x2), d0 = csub_l(x0, x2);
+  C s1 = cadd_l(x1, x3), d1 = mul_i<DIR>(csub_l(x1, x3));
+  x0 = cadd_l(s0, s1);
+  x2 = csub_l(s0, s1);
+  x1 = cadd_l(d0, d1);
+  x3 = csub_l(d0, d1);
 }
 template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
@@ -279,20 +331,20 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   o1 = mul_w8<DIR>(o1);
   o2 = mul_i<DIR>(o2);
   o3 = mul_i<DIR>(mul_w8<DIR>(o3));
-  x[0] = cadd(e0, o0);
-  x[4] = csub(e0, o0);
-  x[1] = cadd(e1, o1);
-  x[5] = csub(e1, o1);
-  x[2] = cadd(e2, o2);
-  x[6] = csub(e2, o2);
-  x[3] = cadd(e3, o3);
-  x[7] = csub(e3, o3);
+  x[0] = cadd_l(e0, o0);
+  x[4] = csub_l(e0, o0);
+  x[1] = cadd_l(e1, o1);
+  x[5] = csub_l(e1, o1);
+  x[2] = cadd_l(e2, o2);
+  x[6] = csub_l(e2, o2);
+  x[3] = cadd_l(e3, o3);
+  x[7] = csub_l(e3, o3);
 }
 
 // One Stockham stage on the register-resident canonical set v[m] = x[t + m N/8].
 // Butterfly b = t + u N/8 (u < 8/RAD) takes x[b + r N/RAD] = v[u + r (8/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
-template <class A, int N, int RAD, int NS, int DIR>
+template <class A, int N, int RAD, int NS, int DIR, bool LAST>
 __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw) {
   using C = typename A::C;
   constexpr int NB = 8 / RAD;
@@ -314,7 +366,7 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, cons
     if (RAD == 4) dft4<DIR>(x[0], x[1], x[2], x[3]);
     if (RAD == 2) dft2<DIR>(x[0], x[1]);
 #pragma unroll
-    for (int r = 0; r < RAD; ++r) v[u + r * NB] = x[r];
+    for (int r = 0; r < RAD; ++r) v[u + r * NB] = cnorm(x[r]);
   }
 }
 
@@ -341,7 +393,7 @@ __device__ __forceinline__ void fft_stages(typename A::C (&v)[8], int t, const t
   if constexpr (I < FftPlan<N>::S) {
     constexpr int RAD = FftPlan<N>::radix(I);
     constexpr int NS = FftPlan<N>::ns(I);
-    stage_compute<A, N, RAD, NS, DIR>(v, t, tw);
+    stage_compute<A, N, RAD, NS, DIR, I + 1 == FftPlan<N>::S>(v, t, tw);
     if constexpr (I + 1 < FftPlan<N>::S) stage_exchange<typename A::C, N, RAD, NS>(v, t, acc);
     fft_stages<A, N, DIR, I + 1>(v, t, tw, acc);
   }
@@ -354,30 +406,69 @@ __device__ __forceinline__ void fft_line(typename A::C (&v)[8], int t, const typ
   fft_stages<A, N, DIR, 0>(v, t, tw, acc);
 }
 
-// Shared-memory views. Tile of CW columns of a strided axis: [pos][col].
-template <typename C, int CW> struct AccTile {
+// Shared-memory views. Tile of CW columns of a strided axis: [pos][col] with a
+// row pitch of PITCH >= CW elements.
+template <typename C, int CW, int PITCH> struct AccTile {
   C* sm;
   int col;
-  __device__ __forceinline__ C& at(int pos) { return sm[pos * CW + col]; }
+  __device__ __forceinline__ C& at(int pos) { return sm[pos * PITCH + col]; }
 };
-// One contiguous line, padded by one element every 8 (bank-conflict free).
-template <typename C> struct AccLine {
+// One contiguous line, padded by one element every 2^PS elements (128 bytes).
+template <typename C, int PS> struct AccLine {
   C* sm;
-  __device__ __forceinline__ C& at(int pos) { return sm[pos + (pos >> 3)]; }
+  __device__ __forceinline__ C& at(int pos) { return sm[pos + (pos >> PS)]; }
 };
 
 // ---------------------------------------------------------- launch shapes
-template <class A, int N> struct Shape {
-  static constexpr int T = N / 8;                                     // threads per line
-  static constexpr int CMIN = sizeof(typename A::C) >= 16 ? 8 : 16;   // 128-byte row segments
-  static constexpr int C0 = (256 / T > CMIN) ? 256 / T : CMIN;
+// Tile shapes (overridable at compile time for tuning sweeps).  Strided tiles
+// hold COLS contiguous columns and aim at QFD_TILE_TARGET threads; the
+// x-direction tiles (stride N^2: one CTA touches the whole lattice) take at
+// least QFD_XCOLS_MIN16 / QFD_XCOLS_MIN8 columns of 16- / 8-byte elements, the
+// y-direction tiles (stride N) QFD_YCOLS_MIN16 / QFD_YCOLS_MIN8.  z-pass CTAs
+// aim at QFD_LINE_TARGET16 / QFD_LINE_TARGET8 threads.
+#ifndef QFD_XCOLS_MIN16
+#define QFD_XCOLS_MIN16 8
+#endif
+#ifndef QFD_XCOLS_MIN8
+#define QFD_XCOLS_MIN8 16
+#endif
+#ifndef QFD_YCOLS_MIN16
+#define QFD_YCOLS_MIN16 4
+#endif
+#ifndef QFD_YCOLS_MIN8
+#define QFD_YCOLS_MIN8 8
+#endif
+#ifndef QFD_TILE_TARGET
+#define QFD_TILE_TARGET 256
+#endif
+#ifndef QFD_LINE_TARGET16
+#define QFD_LINE_TARGET16 256
+#endif
+#ifndef QFD_LINE_TARGET8
+#define QFD_LINE_TARGET8 128
+#endif
+template <int N, int CMIN> struct TileCols {
+  static constexpr int T = N / 8;
+  static constexpr int C0 = (QFD_TILE_TARGET / T > CMIN) ? QFD_TILE_TARGET / T : CMIN;
   static constexpr int C1 = C0 < 1024 / T ? C0 : 1024 / T;
-  static constexpr int COLS = C1 < N ? C1 : N;  // strided-tile columns
-  static constexpr int TILE_THREADS = T * COLS;
-  static constexpr int LINES0 = (256 / T) > 1 ? 256 / T : 1;
+  static constexpr int value = C1 < N ? C1 : N;
+};
+template <class A, int N> struct Shape {
+  static constexpr bool WIDE = sizeof(typename A::C) >= 16;
+  static constexpr int T = N / 8;  // threads per line
+  static constexpr int XCOLS = TileCols<N, WIDE ? QFD_XCOLS_MIN16 : QFD_XCOLS_MIN8>::value;
+  static constexpr int YCOLS = TileCols<N, WIDE ? QFD_YCOLS_MIN16 : QFD_YCOLS_MIN8>::value;
+  static constexpr int XTHREADS = T * XCOLS;
+  static constexpr int YTHREADS = T * YCOLS;
+  static constexpr int XPITCH = XCOLS;  // shared-memory row pitch of the tiles
+  static constexpr int YPITCH = YCOLS;
+  static constexpr int LTARGET = WIDE ? QFD_LINE_TARGET16 : QFD_LINE_TARGET8;
+  static constexpr int LINES0 = (LTARGET / T) > 1 ? LTARGET / T : 1;
   static constexpr int LINES = LINES0 < N * N ? LINES0 : N * N;  // z-pass lines per CTA
   static constexpr int LINE_THREADS = T * LINES;
-  static constexpr int LPAD = N + N / 8;
+  // one padding element per 128 bytes of a line keeps the exchanges conflict-free
+  static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
+  static constexpr int LPAD = N + (N >> PAD_SHIFT);
 };
 
 // ------------------------------------------------------------- reductions
@@ -434,20 +525,20 @@ enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 // of COLS contiguous columns.  Tile id ->
 // base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
 template <class A, int N, int DIR>
-__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+__global__ void __launch_bounds__(Shape<A, N>::YTHREADS)
 k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
               int64_t outer_stride) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
+  const int col = threadIdx.x % SH::YCOLS, t = threadIdx.x / SH::YCOLS;
   const int64_t base = (int64_t)(blockIdx.x / tiles_inner) * outer_stride +
-                       (int64_t)(blockIdx.x % tiles_inner) * SH::COLS + col;
+                       (int64_t)(blockIdx.x % tiles_inner) * SH::YCOLS + col;
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
-  AccTile<C, SH::COLS> acc{sm, col};
+  AccTile<C, SH::YCOLS, SH::YPITCH> acc{sm, col};
   fft_line<A, N, DIR>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
@@ -471,7 +562,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = p[t + m * SH::T];
-  AccLine<C> acc{sm + l * SH::LPAD};
+  AccLine<C, SH::PAD_SHIFT> acc{sm + l * SH::LPAD};
   fft_line<A, N, -1>(v, t, tw, acc);
   const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
   double pt = 0.0;
@@ -493,23 +584,35 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
 // Eq. (iter_proced) with the coefficients of Sec. 2.2 (times an optional
 // normalisation factor *scale carried from the previous step); partial sums
-// per STATS; forward DFT_x of the new psi into W.
+// per STATS; forward DFT_x of the new psi into W.  psi and the coefficients
+// are loaded before the inverse transform so that their latency overlaps it.
 template <class A, int N, int STATS>
-__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
            const double* __restrict__ V, const double* __restrict__ scale, const typename A::C* __restrict__ tw,
            double* __restrict__ part) {
   using C = typename A::C;
+  using K = typename A::K;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
-  const int64_t base = (int64_t)blockIdx.x * SH::COLS + col;
+  const int col = threadIdx.x % SH::XCOLS, t = threadIdx.x / SH::XCOLS;
+  const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;
   constexpr int64_t S = (int64_t)N * N;
-  C v[8];
+  // psi and the coefficients are loaded before the inverse transform so that
+  // their latency overlaps it (measured faster for every policy)
+  constexpr bool EARLY = true;
+  C v[8], ps[EARLY ? 8 : 1];
+  K cf[EARLY ? 8 : 1];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (t + m * SH::T) * S];
-  AccTile<C, SH::COLS> acc{sm, col};
+  if constexpr (EARLY) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) cf[m] = coef[base + (t + m * SH::T) * S];
+  }
+  AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, +1>(v, t, tw, acc);
   const bool scaled = scale != nullptr;
   const typename A::S s = A::scalar(scaled ? *scale : 1.0);
@@ -518,7 +621,9 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
-    C nw = A::update(psi[idx], v[m], coef[idx]);
+    C nw;
+    if constexpr (EARLY) nw = A::update(ps[m], v[m], cf[m]);
+    else nw = A::update(psi[idx], v[m], coef[idx]);
     if (scaled) nw = cscale(nw, s);
     psi[idx] = nw;
     v[m] = nw;
@@ -543,15 +648,15 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
 // psi_out) into W; partials per STATS of the scaled input.  src may alias W
 // (each CTA reads its whole tile before writing it).
 template <class A, int N, int STATS>
-__global__ void __launch_bounds__(Shape<A, N>::TILE_THREADS)
+__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, const double* __restrict__ V,
             const double* __restrict__ scale, const typename A::C* __restrict__ tw, double* __restrict__ part) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int col = threadIdx.x % SH::COLS, t = threadIdx.x / SH::COLS;
-  const int64_t base = (int64_t)blockIdx.x * SH::COLS + col;
+  const int col = threadIdx.x % SH::XCOLS, t = threadIdx.x / SH::XCOLS;
+  const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;
   constexpr int64_t S = (int64_t)N * N;
   const bool scaled = scale != nullptr;
   const typename A::S s = A::scalar(scaled ? *scale : 1.0);
@@ -575,7 +680,7 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
 #pragma unroll
     for (int m = 0; m < 8; ++m) psi_out[base + (t + m * SH::T) * S] = v[m];
   }
-  AccTile<C, SH::COLS> acc{sm, col};
+  AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
@@ -586,72 +691,116 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   }
 }
 
-// ------------------------------------------------- elementwise site kernels
-__host__ __device__ __forceinline__ int64_t reflect_index(int64_t i, int64_t n, int offgrid) {
-  const int64_t z = i % n, y = (i / n) % n, x = i / (n * n);
-  const int64_t rx = offgrid ? n - 1 - x : (n - x) % n;
-  const int64_t ry = offgrid ? n - 1 - y : (n - y) % n;
-  const int64_t rz = offgrid ? n - 1 - z : (n - z) % n;
-  return (rx * n + ry) * n + rz;
-}
-
+// ------------------------------------------------- projection and overlaps
 constexpr int MAX_LOWER = 8;
 
-// Overlaps <phi_j | P psi> (FP64) for j < k, P the parity projector (Eq. parity).
-template <class A>
-__global__ void k_gs_dots(const typename A::C* __restrict__ psi, const typename A::C* __restrict__ lower, int k,
-                          int parity, int offgrid, int64_t n, double* __restrict__ part) {
-  const int64_t n3 = n * n * n;
-  double acc[2 * MAX_LOWER];
-#pragma unroll
-  for (int j = 0; j < 2 * MAX_LOWER; ++j) acc[j] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 p = A::to_d2(psi[i]);
-    if (parity) {
-      const double2 q = A::to_d2(psi[reflect_index(i, n, offgrid)]);
-      p = double2{0.5 * (p.x + parity * q.x), 0.5 * (p.y + parity * q.y)};
-    }
-#pragma unroll
-    for (int j = 0; j < MAX_LOWER; ++j) {
-      if (j < k) {
-        const double2 f = A::to_d2(lower[j * n3 + i]);
-        acc[2 * j] += f.x * p.x + f.y * p.y;
-        acc[2 * j + 1] += f.x * p.y - f.y * p.x;
-      }
-    }
-  }
-  block_reduce_store<2 * MAX_LOWER>(acc, part);
+// Up to MAX_LOWER lower states (each a whole lattice), passed by value.
+struct LowerPtrs {
+  const void* p[MAX_LOWER];
+};
+
+// Lattice reflection r -> -r about the potential's centre (Eq. (parity)):
+// grid centre x -> (N - x) mod N, off-grid centre x -> N - 1 - x.
+template <int N>
+__device__ __forceinline__ int reflect1(int x, int offgrid) {
+  return offgrid ? N - 1 - x : (N - x) & (N - 1);
 }
 
-// out = P psi - sum_j c_j phi_j  (c_j = sums[2j] + i sums[2j+1]);
-// partials of sum |out|^2 and sum V |out|^2 (FP64).
-template <class A>
-__global__ void k_gs_apply(const typename A::C* __restrict__ psi, const typename A::C* __restrict__ lower,
-                           const double* __restrict__ sums, int k, int parity, int offgrid, int64_t n,
-                           typename A::C* __restrict__ out, const double* __restrict__ V, double* __restrict__ part,
-                           int check) {
-  const int64_t n3 = n * n * n;
-  double n2 = 0.0, pv = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 p = A::to_d2(psi[i]);
+// Overlaps <phi_j | P psi> for j < k (P the parity projector of Eq. (parity),
+// the identity for parity 0), summed per CTA in the policy's exact
+// accumulator and stored as FP64 partials (2 per lower state).
+template <class A, int N>
+__global__ void __launch_bounds__(256)
+k_gs_dots(const typename A::C* __restrict__ psi, LowerPtrs lower, int k, int parity, int offgrid,
+          double* __restrict__ part) {
+  using C = typename A::C;
+  constexpr int LG = ilog2c(N);
+  constexpr int64_t N3 = (int64_t)N * N * N;
+  typename A::Dot acc[MAX_LOWER];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N3; i += (int64_t)gridDim.x * blockDim.x) {
+    C p = psi[i];
     if (parity) {
-      const double2 q = A::to_d2(psi[reflect_index(i, n, offgrid)]);
-      p = double2{0.5 * (p.x + parity * q.x), 0.5 * (p.y + parity * q.y)};
+      const int z = (int)(i & (N - 1)), y = (int)((i >> LG) & (N - 1)), x = (int)(i >> (2 * LG));
+      const int64_t ri = ((int64_t)reflect1<N>(x, offgrid) << (2 * LG)) + ((int64_t)reflect1<N>(y, offgrid) << LG) +
+                         reflect1<N>(z, offgrid);
+      p = A::half_comb(p, psi[ri], parity);
     }
-    for (int j = 0; j < k; ++j) {
-      const double2 f = A::to_d2(lower[j * n3 + i]);
-      const double cr = sums[2 * j], ci = sums[2 * j + 1];
-      p.x -= cr * f.x - ci * f.y;
-      p.y -= cr * f.y + ci * f.x;
-    }
-    const typename A::C o = A::from_d2(p);
-    out[i] = o;
-    const double a2 = A::norm2_d(o);
-    n2 += a2;
-    if (check) pv += V[i] * a2;
+#pragma unroll
+    for (int j = 0; j < MAX_LOWER; ++j)
+      if (j < k) acc[j].add(static_cast<const C*>(lower.p[j])[i], p);
   }
-  double q[2] = {n2, pv};
-  block_reduce_store<2>(q, part);
+  double q[2 * MAX_LOWER];
+#pragma unroll
+  for (int j = 0; j < MAX_LOWER; ++j) {
+    const double2 d = acc[j].value();
+    q[2 * j] = d.x;
+    q[2 * j + 1] = d.y;
+  }
+  block_reduce_store<2 * MAX_LOWER>(q, part);
+}
+
+// The cadence's projection fused with the forward x transform: psi' = P psi -
+// sum_j c_j phi_j (c_j = sums[2j] + i sums[2j+1], the overlaps of k_gs_dots)
+// is written to dst (a different buffer than src: other CTAs still read the
+// reflected sites of src) and its forward DFT_x to W; partials per STATS of
+// psi'.  The normalisation is applied by the next pass A.
+template <class A, int N, int STATS>
+__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
+k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double* __restrict__ sums, int k, int parity,
+            int offgrid, typename A::C* __restrict__ dst, typename A::C* __restrict__ W, const double* __restrict__ V,
+            const typename A::C* __restrict__ tw, double* __restrict__ part) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int col = threadIdx.x % SH::XCOLS, t = threadIdx.x / SH::XCOLS;
+  const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;  // = y * N + z
+  constexpr int64_t S = (int64_t)N * N;
+  const int y = (int)(base / N), z = (int)(base % N);
+  const int64_t rbase = (int64_t)reflect1<N>(y, offgrid) * N + reflect1<N>(z, offgrid);
+  C cc[MAX_LOWER];
+#pragma unroll
+  for (int j = 0; j < MAX_LOWER; ++j)
+    if (j < k) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
+  C v[8];
+  typename A::Acc nacc;
+  double n2 = 0.0, pv = 0.0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int x = t + m * SH::T;
+    const int64_t idx = base + x * S;
+    C p = src[idx];
+    if (parity) p = A::half_comb(p, src[rbase + (int64_t)reflect1<N>(x, offgrid) * S], parity);
+#pragma unroll
+    for (int j = 0; j < MAX_LOWER; ++j)
+      if (j < k) p = csub(p, cmul(static_cast<const C*>(lower.p[j])[idx], cc[j]));
+    dst[idx] = p;
+    v[m] = p;
+    if constexpr (STATS == STATS_NORM) nacc.add_norm(p);
+    if constexpr (STATS == STATS_FULL) {
+      const double a2 = A::norm2_d(p);
+      n2 += a2;
+      pv += V[idx] * a2;
+    }
+  }
+  AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
+  fft_line<A, N, -1>(v, t, tw, acc);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
+  if constexpr (STATS != STATS_NONE) {
+    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+    double q[2] = {n2, pv};
+    block_reduce_store<2>(q, part);
+  }
+}
+
+// psi *= f in the policy's arithmetic, f = scal[0] (mode 0) or 1 / sqrt(scal[1]) (mode 1).
+template <class A>
+__global__ void k_scale(typename A::C* __restrict__ psi, int64_t n3, const double* __restrict__ f_or_n2, int mode) {
+  const double f = mode == 0 ? f_or_n2[0] : 1.0 / sqrt(f_or_n2[0]);
+  const typename A::S fs = A::scalar(f);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    psi[i] = cscale(psi[i], fs);
 }
 
 }  // namespace qfd

@@ -45,6 +45,13 @@ struct LaunchArgs {
   double* part = nullptr;      // per-CTA partials
   int stats = 0;               // STATS_* for passes A / forward x, Parseval flag for pass C
   cudaStream_t stream = 0;
+  // projection / Gram-Schmidt
+  const void* lower[8] = {};   // lower states (k of them)
+  int k = 0;                   // number of lower states
+  int parity = 0;              // 0, +1, -1
+  int offgrid = 0;             // reflection about the off-grid centre
+  const double* sums = nullptr;  // overlaps (2 doubles per lower state)
+  void* dst = nullptr;         // projected state output
 };
 
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the
@@ -54,6 +61,8 @@ template <class A, int N> struct Launch {
   static cudaError_t forward_x(const LaunchArgs& a, int* nblocks);
   static cudaError_t fft_y(const LaunchArgs& a, int dir);
   static cudaError_t zpass(const LaunchArgs& a, int* nblocks);
+  static cudaError_t project_x(const LaunchArgs& a, int* nblocks);
+  static cudaError_t gs_dots(const LaunchArgs& a, int nblocks);
   static int partials();  // largest CTA count of a reducing pass
 };
 
@@ -88,6 +97,12 @@ template <class A> cudaError_t launch_fft_y(const LaunchArgs& a, int dir) {
 template <class A> cudaError_t launch_zpass(const LaunchArgs& a, int* nb) {
   return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::zpass(a, nb); });
 }
+template <class A> cudaError_t launch_project_x(const LaunchArgs& a, int* nb) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::project_x(a, nb); });
+}
+template <class A> cudaError_t launch_gs_dots(const LaunchArgs& a, int nblocks) {
+  return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::gs_dots(a, nblocks); });
+}
 template <class A> int max_partials(int64_t n) {
   int out = 0;
   dispatch_n(n, [&](auto t) {
@@ -97,12 +112,6 @@ template <class A> int max_partials(int64_t n) {
   return out;
 }
 
-// Gram-Schmidt / parity kernels (qfd_gs.cu).
-template <class A> cudaError_t launch_gs_dots(const void* psi, const void* lower, int k, int parity, int offgrid,
-                                              int64_t n, double* part, int nblocks, cudaStream_t st);
-template <class A> cudaError_t launch_gs_apply(const void* psi, const void* lower, const double* sums, int k,
-                                               int parity, int offgrid, int64_t n, void* out, const double* V,
-                                               double* part, int check, int nblocks, cudaStream_t st);
 bool supported_n(int64_t n);
 
 }  // namespace qfd

@@ -16,11 +16,11 @@ template <class A, int N>
 cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
   using SH = Shape<A, N>;
-  const size_t smem = (size_t)N * SH::COLS * sizeof(C);
-  const int grid = (int)((int64_t)N * N / SH::COLS);
+  const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
+  const int grid = (int)((int64_t)N * N / SH::XCOLS);
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
-    kern<<<grid, SH::TILE_THREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, a.V, a.scale,
+    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, a.V, a.scale,
                                                       (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL>);
@@ -34,11 +34,11 @@ template <class A, int N>
 cudaError_t Launch<A, N>::forward_x(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
   using SH = Shape<A, N>;
-  const size_t smem = (size_t)N * SH::COLS * sizeof(C);
-  const int grid = (int)((int64_t)N * N / SH::COLS);
+  const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
+  const int grid = (int)((int64_t)N * N / SH::XCOLS);
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
-    kern<<<grid, SH::TILE_THREADS, smem, a.stream>>>((const C*)a.src, (C*)a.W, (C*)a.psi_out, a.V, a.scale,
+    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, (C*)a.W, (C*)a.psi_out, a.V, a.scale,
                                                       (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_forward_x<A, N, STATS_FULL>);
@@ -52,12 +52,12 @@ template <class A, int N>
 cudaError_t Launch<A, N>::fft_y(const LaunchArgs& a, int dir) {
   using C = typename A::C;
   using SH = Shape<A, N>;
-  const size_t smem = (size_t)N * SH::COLS * sizeof(C);
-  const int tiles_inner = N / SH::COLS;
+  const size_t smem = (size_t)N * SH::YPITCH * sizeof(C);
+  const int tiles_inner = N / SH::YCOLS;
   const int grid = N * tiles_inner;
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
-    kern<<<grid, SH::TILE_THREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
+    kern<<<grid, SH::YTHREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
                                                       (int64_t)N * N);
   };
   if (dir < 0) go(k_fft_strided<A, N, -1>);
@@ -83,9 +83,36 @@ cudaError_t Launch<A, N>::zpass(const LaunchArgs& a, int* nblocks) {
 }
 
 template <class A, int N>
+cudaError_t Launch<A, N>::project_x(const LaunchArgs& a, int* nblocks) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
+  const int grid = (int)((int64_t)N * N / SH::XCOLS);
+  LowerPtrs lp;
+  for (int j = 0; j < MAX_LOWER; ++j) lp.p[j] = a.lower[j];
+  auto go = [&](auto kern) {
+    ensure_smem(kern, smem);
+    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, lp, a.sums, a.k, a.parity, a.offgrid,
+                                                      (C*)a.dst, (C*)a.W, a.V, (const C*)a.tw, a.part);
+  };
+  if (a.stats == STATS_FULL) go(k_project_x<A, N, STATS_FULL>);
+  else go(k_project_x<A, N, STATS_NORM>);
+  if (nblocks) *nblocks = grid;
+  return cudaGetLastError();
+}
+
+template <class A, int N>
+cudaError_t Launch<A, N>::gs_dots(const LaunchArgs& a, int nblocks) {
+  LowerPtrs lp;
+  for (int j = 0; j < MAX_LOWER; ++j) lp.p[j] = a.lower[j];
+  k_gs_dots<A, N><<<nblocks, 256, 0, a.stream>>>((const typename A::C*)a.src, lp, a.k, a.parity, a.offgrid, a.part);
+  return cudaGetLastError();
+}
+
+template <class A, int N>
 int Launch<A, N>::partials() {
   using SH = Shape<A, N>;
-  const int x = (int)((int64_t)N * N / SH::COLS);
+  const int x = (int)((int64_t)N * N / SH::XCOLS);
   const int z = (int)((int64_t)N * N / SH::LINES);
   return x > z ? x : z;
 }

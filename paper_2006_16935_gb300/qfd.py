@@ -15,7 +15,8 @@ import re
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libqfd.so")
+# QFD_LIBRARY selects another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("QFD_LIBRARY") or os.path.join(_PKG, "libqfd.so")
 HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "qfd.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_UNSTABLE_DT, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_NOT_CONVERGED, ERR_STATE = (
@@ -27,7 +28,7 @@ PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2, "df64": 3, "c64_refine_df": 4
 CENTRE = {"grid": 0, "offgrid": 1}
 POTENTIAL = {"zero": 0, "ho": 1, "cornell": 2, "coulomb": 3, "softcoul": 4}
 PASS_KINDS = {"update_x": 0, "fwd_y": 1, "z_kinetic": 2, "inv_y": 3, "fwd_x": 4,
-              "gs_dots": 5, "gs_apply": 6, "reduce": 7, "other": 8}
+              "gs_dots": 5, "project_x": 6, "reduce": 7, "other": 8}
 
 
 class QfdError(RuntimeError):
