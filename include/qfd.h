@@ -188,6 +188,25 @@ qfd_status qfd_timing_reset(qfd_plan_t plan);
 qfd_status qfd_timing_query(qfd_plan_t plan, int kind, int64_t* launches, double* total_ms);
 int64_t qfd_launch_count(qfd_plan_t plan);
 
+/* Rayleigh energy <psi|H_K + V|psi> / <psi|psi> and sum |psi|^2 of a lattice
+ * that lives in the caller's device memory, computed in FP64 without
+ * allocating any device memory.  There is no counterpart in the paper: this
+ * entry point exists for callers that cannot allocate device memory (for
+ * example a serving process that gives its whole memory budget to its own
+ * pool up front, or a latency-critical path where a cudaMalloc could fail or
+ * stall).  Its scratch (work lattice, partial sums, tables) is one static
+ * device array of about 33 MiB that every GPU loading this library holds
+ * until exit; it bounds the lattice to n <= 128 (QFD_ERR_ARG above that).
+ * psi: device, interleaved complex128, n^3 sites [x][y][z]; V: device, n^3
+ * doubles; a, mass, kinetic, rest_mass as in qfd_params; stream: cudaStream_t
+ * or NULL.  E and norm2 are host outputs (either may be NULL); the call
+ * synchronises the stream.  The array is shared by every call and keeps the
+ * last call's contents; calls that overlap on the GPU race on it.  The first
+ * call on a device looks up the array's device address (with that device
+ * current); make it before any stream capture. */
+qfd_status qfd_energy_noalloc(const double* psi, const double* V, int64_t n, double a, double mass, int kinetic,
+                              int rest_mass, void* stream, double* E, double* norm2);
+
 /* The plan's CUDA stream (cudaStream_t) for event recording by the caller. */
 void* qfd_get_stream(qfd_plan_t plan);
 

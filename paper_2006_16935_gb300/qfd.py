@@ -86,6 +86,7 @@ def load():
         "qfd_launch_count": (I64, [P]),
         "qfd_get_stream": (P, [P]),
         "qfd_sync": (I, [P]),
+        "qfd_energy_noalloc": (I, [P, P, I64, D, D, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -106,6 +107,23 @@ def _ptr(arr, dtype):
         return arr.data_ptr(), int(arr.is_cuda), arr
     a = np.ascontiguousarray(arr, dtype=dtype)
     return a.ctypes.data, 0, a
+
+
+def energy_noalloc(psi, V, n, a, mass, kinetic, rest_mass=0, stream=None):
+    """qfd_energy_noalloc on device tensors psi (complex128, n^3) and V (float64, n^3):
+    the energy and squared norm, evaluated without any device allocation (n <= 128)."""
+    lib = load()
+    pp, dev_p, keep_p = _ptr(psi, np.complex128)
+    pv, dev_v, keep_v = _ptr(V, np.float64)
+    if not (dev_p and dev_v):
+        raise TypeError("psi and V must be CUDA device tensors")
+    e, n2 = ctypes.c_double(), ctypes.c_double()
+    st = lib.qfd_energy_noalloc(pp, pv, int(n), float(a), float(mass), int(kinetic), int(rest_mass), stream,
+                                ctypes.byref(e), ctypes.byref(n2))
+    if st != OK:
+        raise QfdError(st, "qfd_energy_noalloc failed")
+    del keep_p, keep_v
+    return e.value, n2.value
 
 
 class Plan:
