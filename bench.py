@@ -141,6 +141,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, device=None, op="max") -> float:
+    """x reduced over the ranks of the default process group (max, or min); x itself
+    when no group is initialised.  Works with NCCL (CUDA device) and gloo (CPU)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.MIN)
+    return float(t.item())
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -325,17 +338,12 @@ def run_qfd(args):
     plan, ms, steps, energy, launches, per_pass = time_precision(torch, Q, args, prec, dev, True)
     clk = clocks.stop()
     plan.close()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     total_units = float(N) ** 3 * steps * world
     value = total_units / (ms / 1e3)
     e2e = e2e_rate(torch, Q, args, prec, dev)
-    if world > 1:
-        t = torch.tensor([e2e["value"]], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * world
+    if world > 1:  # slowest replica's rate times the replica count
+        e2e["value"] = max_over_ranks(e2e["value"], dev, op="min") * world
     others = {}
     for other in [p for p in ("c128", "df64", "c64") if p != prec]:
         pl_o, ms_o, steps_o, e_o, _, per_pass_o = time_precision(torch, Q, args, other, dev, True)
@@ -374,20 +382,24 @@ def run_qfd(args):
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
                                     "sample": "skipped: less than 24 GB host memory available"}
     if args.solve:
-        line["solve"] = full_solves(torch, Q, dev)
+        c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
+            others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
+        line["solve"] = full_solves(torch, Q, dev, args.solve.split(","), c128_ms)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
     return 0
 
 
-def full_solves(torch, Q, dev):
-    """Ground state to |dE|/|E| <= 1e-9 in complex128 and in complex64 + refinement."""
+def full_solves(torch, Q, dev, which, ms_step_c128=None):
+    """Ground state of the workload to |dE|/|E| <= 1e-9 (checks every 100 steps,
+    normalisation + parity every 10) in each requested arithmetic; the complex64
+    bulk of the mixed forms hands over at tol_bulk or at its FP32 noise floor."""
     out = {}
     stream = torch.cuda.current_stream(dev)
-    for prec in ("c128", "df64", "c64_refine", "c64_refine_df"):
+    for prec in which:
         plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=10, check_every=100, max_steps=400000,
-                      tol=1e-9, tol_bulk=1e-7, stream=stream.cuda_stream)
+                      tol=1e-9, tol_bulk=1e-10, stream=stream.cuda_stream)
         plan.fill_potential(*POT)
         plan.fill_psi_uniform(0, SEED)
         torch.cuda.synchronize(dev)
@@ -395,10 +407,21 @@ def full_solves(torch, Q, dev):
         es, steps, conv = plan.solve_states(1, [1], allow_unconverged=True)
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
+        hist = plan.history(0)
         out[prec] = {"energy": es[0], "steps": steps[0], "converged": conv, "seconds": dt,
                      "solves_per_s": 1.0 / dt, "site_updates_per_s": float(N) ** 3 * steps[0] / dt,
-                     **plan.stats(0)}
+                     "checks": len(hist), **plan.stats(0)}
         plan.close()
+    ref = out.get("df64") or out.get("c128")
+    if ref:
+        for k, v in out.items():
+            v["rel_energy_diff_vs_fp64_class"] = abs(v["energy"] - ref["energy"]) / abs(ref["energy"])
+    if ms_step_c128 and "df64" in out and "c128" not in out:
+        # the native complex128 solve runs the same iteration (same step count) at the
+        # measured complex128 step time; estimated, not run (it takes ~35 min at 512^3)
+        st = out["df64"]["steps"]
+        out["c128_estimated"] = {"steps": st, "seconds": st * ms_step_c128 / 1e3,
+                                 "solves_per_s": 1e3 / (st * ms_step_c128), "estimated": True}
     return out
 
 
@@ -409,7 +432,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["qfd", "reference"], default="qfd")
     ap.add_argument("--precision", choices=["c128", "df64", "c64"], default="c128")
-    ap.add_argument("--solve", action="store_true", help="also run the full 1e-9 solves (minutes)")
+    ap.add_argument("--solve", default="", help="comma list of precisions for full 1e-9 solves "
+                    "(e.g. c64_refine_df,c64_refine,df64; minutes each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

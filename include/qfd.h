@@ -142,6 +142,16 @@ qfd_status qfd_fill_psi_uniform(qfd_plan_t plan, int state, uint64_t seed);
 /* Copies state `state` out (interleaved complex128) into the caller's buffer. */
 qfd_status qfd_get_psi(qfd_plan_t plan, int state, double* out, int on_device);
 
+/* Observables of `state` in lattice units, d = x - centre per axis (FP64):
+ * out[0] sum |psi|^2; out[1] the same over the effective volume of Sec. 2.3
+ * (sites with |d_l| <= (1 - min_sep_edge) N / 2 on every axis); out[2] the
+ * box-normalised average radius <rho>_box of Eq. (box_normalization);
+ * out[3] <rho^2>, out[4..6] <x>, <y>, <z> over the full lattice (the UPDATE
+ * observables of Sec. 5.1); out[7], out[8] the box-normalised weights of the
+ * parity projections P+ and P- (Sec. 2.4, they sum to 1).  The first nout
+ * (<= 9) values are written; 0 <= min_sep_edge < 1. */
+qfd_status qfd_observables(qfd_plan_t plan, int state, double min_sep_edge, double* out, int nout);
+
 /* Parity sector applied to `state` at every cadence (QFD_PAR_*). */
 qfd_status qfd_set_parity(qfd_plan_t plan, int state, int parity);
 
@@ -161,8 +171,10 @@ qfd_status qfd_energy(qfd_plan_t plan, int state, double* E, double* norm2);
  * parity projected with parity[i] (parity may be NULL), deflated against the
  * converged states 0..i-1, stepped until the relative energy change between
  * two checks is <= tol (or max_steps), and left normalised.  For
- * QFD_C64_REFINE each state first runs in complex64 to tol_bulk, then in
- * complex128 to tol.  E_out[i] receives the final energy and steps_out[i]
+ * QFD_C64_REFINE / QFD_C64_REFINE_DF each state first runs in complex64 to
+ * tol_bulk (or until its energy rises between two checks after the third
+ * one: FP32 rounding then dominates the decay), then in the FP64-class
+ * arithmetic to tol.  E_out[i] receives the final energy and steps_out[i]
  * the total number of steps (both may be NULL).  Returns
  * QFD_ERR_NOT_CONVERGED (outputs still filled) if a state reached
  * max_steps, QFD_ERR_DIVERGED on a non-finite energy. */
@@ -176,6 +188,12 @@ qfd_status qfd_set_limits(qfd_plan_t plan, int64_t max_steps, double tol, double
  * complex64 and complex128 and the energy at the end of the complex64 phase
  * (NaN if none).  Any output may be NULL. */
 qfd_status qfd_get_stats(qfd_plan_t plan, int state, int64_t* steps_c64, int64_t* steps_c128, double* e_bulk);
+
+/* Energy history of `state` in its last qfd_solve_states (the SAVEDECAY table
+ * of Sec. 5.1): for every check, the step count within its phase and the
+ * energy; the complex64 checks of a mixed solve come first.  Copies at most
+ * `capacity` entries into steps[] and E[] and sets *count to the total. */
+qfd_status qfd_get_history(qfd_plan_t plan, int state, int64_t* steps, double* E, int capacity, int* count);
 
 /* Kernel timing: when enabled, every kernel launch of the plan is bracketed
  * by CUDA events on the plan's stream.  qfd_timing_query synchronises and

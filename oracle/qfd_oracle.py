@@ -34,7 +34,8 @@ band-limited Gaussian against the continuum Laplacian; the update on plane
 waves with constant V; the converged iteration against dense eigen-solvers of
 independently assembled matrices (ground state, parity sector, Gram-Schmidt
 deflated state); the 3D oscillator levels 3/2 w and 5/2 w; the heavy-mass
-limit; parity and orthogonality invariants.  No function here is unpinned.
+limit; parity and orthogonality invariants; the box-normalised hydrogen radii
+printed in Sec. 3.3 (observables).  No function here is unpinned.
 """
 from __future__ import annotations
 
@@ -266,6 +267,41 @@ def potential(n: int, a: float, kind: str, params=(), centre: str = "grid") -> n
         eps2 = params[0] if params else 0.01
         return -1.0 / np.sqrt(r * r + eps2)
     raise ValueError(kind)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3 / 2.4 / 5.1: observables
+# --------------------------------------------------------------------------
+
+
+def observables(psi, centre: str = "grid", min_sep_edge: float = 0.3) -> dict:
+    """Observables of a state, in lattice units, d = x - centre per axis:
+
+    box normalisation (Sec. 2.3): the effective volume keeps the sites with
+    |d_l| <= (1 - min_sep_edge) N / 2 on every axis; <rho>_box = sum over the box
+    of rho |psi|^2 / sum over the box of |psi|^2 (Eq. (box_normalization));
+    parity weights (Sec. 2.4): sum over the box of |P+- psi|^2, box-normalised,
+    so that w+ + w- = 1;
+    UPDATE observables (Sec. 5.1): <x>, <y>, <z>, <rho^2> over the full lattice.
+    """
+    n = psi.shape[0]
+    d = displacement(n, centre)
+    d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+    rho = np.sqrt(d1 * d1 + d2 * d2 + d3 * d3)
+    half = (1.0 - min_sep_edge) * n / 2.0
+    box = (np.abs(d1) <= half) & (np.abs(d2) <= half) & (np.abs(d3) <= half)
+    p2 = np.abs(psi) ** 2
+    n_full = p2.sum()
+    n_box = p2[box].sum()
+    refl = reflect(psi, centre)
+    wp = (np.abs(0.5 * (psi + refl)) ** 2)[box].sum() / n_box
+    wm = (np.abs(0.5 * (psi - refl)) ** 2)[box].sum() / n_box
+    return {"norm2": float(n_full), "norm2_box": float(n_box),
+            "rho_box": float((rho * p2)[box].sum() / n_box),
+            "rho2": float((rho * rho * p2).sum() / n_full),
+            "x": float((d1 * p2).sum() / n_full), "y": float((d2 * p2).sum() / n_full),
+            "z": float((d3 * p2).sum() / n_full),
+            "w_plus": float(wp), "w_minus": float(wm)}
 
 
 # --------------------------------------------------------------------------

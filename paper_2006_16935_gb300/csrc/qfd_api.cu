@@ -28,7 +28,8 @@ thread_local std::string g_create_error;
 enum Stage { ST_NONE = 0, ST_X = 1, ST_XY = 2, ST_C = 3, ST_D = 4 };
 // device scalar slots
 enum { SC_SUMS = 0, SC_N2 = 40, SC_PV = 41, SC_PT = 42, SC_SCALE = 43, SC_E = 44, SC_COUNT = 64 };
-enum { OP_SUMS = 0, OP_NORM = 1, OP_N2PV = 2, OP_ENERGY = 3 };
+enum { OP_SUMS = 0, OP_NORM = 1, OP_N2PV = 2, OP_ENERGY = 3, OP_OBS = 4 };
+constexpr int NOBS = 9;
 constexpr int GS_BLOCKS = 4 * 152;
 constexpr int FIN_THREADS = 1024;
 
@@ -68,6 +69,18 @@ k_finalize_op(const double* __restrict__ part, int nq, int count, double* __rest
     } else if (op == OP_ENERGY) {
       scal[SC_PT] = sums[0];
       scal[SC_E] = (sums[0] + scal[SC_PV]) / scal[SC_N2];
+    } else if (op == OP_OBS) {
+      // sums: n2, n2_box, rho_box, rho^2, x, y, z, |P+ psi|^2_box, |P- psi|^2_box
+      const double n2 = sums[0], nb = sums[1];
+      scal[SC_SUMS + 0] = n2;
+      scal[SC_SUMS + 1] = nb;
+      scal[SC_SUMS + 2] = sums[2] / nb;
+      scal[SC_SUMS + 3] = sums[3] / n2;
+      scal[SC_SUMS + 4] = sums[4] / n2;
+      scal[SC_SUMS + 5] = sums[5] / n2;
+      scal[SC_SUMS + 6] = sums[6] / n2;
+      scal[SC_SUMS + 7] = sums[7] / nb;
+      scal[SC_SUMS + 8] = sums[8] / nb;
     }
   }
 }
@@ -129,6 +142,42 @@ __global__ void k_fill_uniform(typename A::C* __restrict__ psi, int64_t n3, uint
   }
 }
 
+// Observables of Sec. 2.3 / 2.4 / 5.1 in lattice units (d = x - centre per
+// axis): partial sums of |psi|^2 (full and effective volume), rho |psi|^2 over
+// the effective volume (|d_l| <= half on every axis), rho^2 |psi|^2, d |psi|^2,
+// and |P+- psi|^2 over the effective volume, all in FP64.
+template <class A>
+__global__ void __launch_bounds__(256)
+k_observables(const typename A::C* __restrict__ psi, int lg, int offgrid, double half, double* __restrict__ part) {
+  const int64_t n = (int64_t)1 << lg, n3 = n * n * n;
+  const double cen = offgrid ? 0.5 * (double)(n - 1) : (double)(n / 2);
+  double acc[NOBS];
+#pragma unroll
+  for (int q = 0; q < NOBS; ++q) acc[q] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = i & (n - 1), y = (i >> lg) & (n - 1), x = i >> (2 * lg);
+    const int64_t rx = offgrid ? n - 1 - x : (n - x) & (n - 1), ry = offgrid ? n - 1 - y : (n - y) & (n - 1),
+                  rz = offgrid ? n - 1 - z : (n - z) & (n - 1);
+    const double2 p = A::to_d2(psi[i]), r = A::to_d2(psi[(rx << (2 * lg)) + (ry << lg) + rz]);
+    const double dx = (double)x - cen, dy = (double)y - cen, dz = (double)z - cen;
+    const double rho2 = dx * dx + dy * dy + dz * dz;
+    const double a2 = p.x * p.x + p.y * p.y;
+    acc[0] += a2;
+    acc[3] += rho2 * a2;
+    acc[4] += dx * a2;
+    acc[5] += dy * a2;
+    acc[6] += dz * a2;
+    if (fabs(dx) <= half && fabs(dy) <= half && fabs(dz) <= half) {
+      acc[1] += a2;
+      acc[2] += sqrt(rho2) * a2;
+      const double sx = 0.5 * (p.x + r.x), sy = 0.5 * (p.y + r.y), mx = 0.5 * (p.x - r.x), my = 0.5 * (p.y - r.y);
+      acc[7] += sx * sx + sy * sy;
+      acc[8] += mx * mx + my * my;
+    }
+  }
+  block_reduce_store<NOBS>(acc, part);
+}
+
 template <class AI, class AO>
 __global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C* __restrict__ out, int64_t n3) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
@@ -174,6 +223,8 @@ struct qfd_plan_s {
   std::vector<int> parity;
   std::vector<int64_t> steps16, steps32;
   std::vector<double> ebulk;
+  // energy at every check of the last solve, per state: (phase-local step, E)
+  std::vector<std::vector<std::pair<int64_t, double>>> hist;
   int w_state = -1, w_stage = ST_NONE, w_phase = -1;
   bool pending = false;
   int phase = 0;  // policy id of the current arithmetic
@@ -475,7 +526,7 @@ qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
 // steps, each followed by the energy and the relative-change test.
 template <class A>
 qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, double* E_out, int64_t* steps,
-                       bool* converged) {
+                       bool* converged, bool bulk = false) {
   qfd_status r;
   pl->t[s] = 0;
   pl->pending = false;
@@ -486,7 +537,7 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
   }
   if ((r = cadence<A>(pl, s, 0)) != QFD_OK) return r;
   double e = NAN, e_prev = NAN, n2 = NAN;
-  bool have_prev = false;
+  int checks = 0;
   *converged = false;
   const int ce = pl->p.check_every;
   while (pl->t[s] < max_steps) {
@@ -495,12 +546,19 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
     if ((r = energy_tail<A>(pl, &e, &n2)) != QFD_OK) return r;
     if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
       return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
-    if (tol >= 0 && have_prev && std::fabs(e - e_prev) <= tol * std::fabs(e)) {
+    pl->hist[s].push_back({pl->t[s], e});
+    ++checks;
+    if (tol >= 0 && checks > 1 && std::fabs(e - e_prev) <= tol * std::fabs(e)) {
+      *converged = true;
+      break;
+    }
+    // complex64 bulk of a mixed solve: once the energy rises between checks the
+    // FP32 rounding noise dominates the decay and the refinement takes over
+    if (bulk && checks > 3 && e > e_prev) {
       *converged = true;
       break;
     }
     e_prev = e;
-    have_prev = true;
   }
   // leave the state normalised (its last finalised N2 is of the stored values)
   QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal + SC_N2, 1),
@@ -631,6 +689,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->steps16.assign(p.nstates, 0);
   pl->steps32.assign(p.nstates, 0);
   pl->ebulk.assign(p.nstates, NAN);
+  pl->hist.assign(p.nstates, {});
   pl->arith16 = (p.precision == QFD_DF64 || p.precision == QFD_C64_REFINE_DF) ? 2 : 0;
   pl->phase = uses32(p.precision) ? 1 : pl->arith16;
 
@@ -831,6 +890,31 @@ qfd_status qfd_get_psi(qfd_plan_t pl, int s, double* out, int on_device) {
   return QFD_OK;
 }
 
+qfd_status qfd_observables(qfd_plan_t pl, int s, double min_sep_edge, double* out, int nout) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!out || nout < 1 || !(min_sep_edge >= 0.0) || !(min_sep_edge < 1.0))
+    return fail(pl, QFD_ERR_ARG, "need an output buffer and 0 <= min_sep_edge < 1");
+  int lg = 0;
+  while (((int64_t)1 << lg) < pl->p.n) ++lg;
+  const double half = (1.0 - min_sep_edge) * (double)pl->p.n / 2.0;
+  const int offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
+  r = with_policy(pl->phase, [&](auto pol) -> qfd_status {
+    using A = decltype(pol);
+    qfd_status q = materialize<A>(pl, s);
+    if (q != QFD_OK) return q;
+    QFD_RUN(PASS_OTHER, (k_observables<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), lg, offgrid, half, pl->partG),
+                         cudaGetLastError()));
+    return finalize(pl, pl->partG, NOBS, GS_BLOCKS, OP_OBS);
+  });
+  if (r != QFD_OK) return r;
+  double h[NOBS];
+  QFD_CK(cudaMemcpyAsync(h, pl->scal + SC_SUMS, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  for (int i = 0; i < nout && i < NOBS; ++i) out[i] = h[i];
+  return QFD_OK;
+}
+
 qfd_status qfd_set_parity(qfd_plan_t pl, int s, int parity) {
   qfd_status r = check_state(pl, s);
   if (r != QFD_OK) return r;
@@ -877,11 +961,13 @@ qfd_status qfd_solve_states(qfd_plan_t pl, int nstates, const int* parity, doubl
     qfd_status r;
     pl->steps32[s] = pl->steps16[s] = 0;
     pl->ebulk[s] = NAN;
+    pl->hist[s].clear();
     if (refine) {
       // complex64 bulk to tol_bulk, then the 16-byte arithmetic to tol
       pl->phase = 1;
       if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
-      if ((r = solve_phase<F32>(pl, s, pl->p.tol_bulk, pl->p.max_steps, &e, &steps, &conv)) != QFD_OK) return r;
+      if ((r = solve_phase<F32>(pl, s, pl->p.tol_bulk, pl->p.max_steps, &e, &steps, &conv, true)) != QFD_OK)
+        return r;
       pl->steps32[s] = steps;
       pl->ebulk[s] = e;
       if ((r = convert_state(pl, s, 0)) != QFD_OK) return r;
@@ -920,6 +1006,20 @@ qfd_status qfd_get_stats(qfd_plan_t pl, int s, int64_t* steps_c64, int64_t* step
   if (steps_c64) *steps_c64 = pl->steps32[s];
   if (steps_c128) *steps_c128 = pl->steps16[s];
   if (e_bulk) *e_bulk = pl->ebulk[s];
+  return QFD_OK;
+}
+
+qfd_status qfd_get_history(qfd_plan_t pl, int s, int64_t* steps, double* E, int capacity, int* count) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (capacity < 0 || (capacity > 0 && (!steps || !E))) return fail(pl, QFD_ERR_ARG, "bad history buffers");
+  const auto& h = pl->hist[s];
+  const int n = (int)std::min<size_t>(h.size(), (size_t)capacity);
+  for (int i = 0; i < n; ++i) {
+    steps[i] = h[i].first;
+    E[i] = h[i].second;
+  }
+  if (count) *count = (int)h.size();
   return QFD_OK;
 }
 

@@ -381,10 +381,10 @@ __device__ __forceinline__ void stage_exchange(C (&v)[8], int t, Acc& acc) {
 #pragma unroll
     for (int r = 0; r < RAD; ++r) acc.at(base + r * NS) = v[u + r * NB];
   }
-  __syncthreads();
+  acc.sync();
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = acc.at(t + m * (N / 8));
-  __syncthreads();
+  acc.sync();
 }
 
 template <class A, int N, int DIR, int I, class Acc>
@@ -408,15 +408,28 @@ __device__ __forceinline__ void fft_line(typename A::C (&v)[8], int t, const typ
 
 // Shared-memory views. Tile of CW columns of a strided axis: [pos][col] with a
 // row pitch of PITCH >= CW elements.
+// The columns of a tile interleave across all warps of the CTA, so an exchange
+// synchronises the whole CTA.
 template <typename C, int CW, int PITCH> struct AccTile {
   C* sm;
   int col;
   __device__ __forceinline__ C& at(int pos) { return sm[pos * PITCH + col]; }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
 };
-// One contiguous line, padded by one element every 2^PS elements (128 bytes).
-template <typename C, int PS> struct AccLine {
+// One contiguous line of T threads, padded by one element every 2^PS elements
+// (128 bytes).  Lines synchronise independently: a warp barrier when lines do
+// not straddle warps (T <= 32), else the named barrier 1 + line (T threads).
+template <typename C, int PS, int T> struct AccLine {
   C* sm;
+  int line;
   __device__ __forceinline__ C& at(int pos) { return sm[pos + (pos >> PS)]; }
+  __device__ __forceinline__ void sync() {
+    if constexpr (T <= 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + line), "r"(T) : "memory");
+    }
+  }
 };
 
 // ---------------------------------------------------------- launch shapes
@@ -562,7 +575,8 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = p[t + m * SH::T];
-  AccLine<C, SH::PAD_SHIFT> acc{sm + l * SH::LPAD};
+  static_assert(SH::T <= 32 || SH::LINES <= 15, "one named barrier per line");
+  AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
   fft_line<A, N, -1>(v, t, tw, acc);
   const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
   double pt = 0.0;

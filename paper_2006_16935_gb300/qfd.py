@@ -75,10 +75,12 @@ def load():
         "qfd_fill_psi_uniform": (I, [P, I, ctypes.c_uint64]),
         "qfd_get_psi": (I, [P, I, P, I]),
         "qfd_set_parity": (I, [P, I, I]),
+        "qfd_observables": (I, [P, I, D, ctypes.POINTER(D), I]),
         "qfd_step": (I, [P, I, I64]),
         "qfd_energy": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_set_limits": (I, [P, I64, D, D]),
+        "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
         "qfd_timing_enable": (I, [P, I]),
         "qfd_timing_reset": (I, [P]),
@@ -208,6 +210,13 @@ class Plan:
         self._check(self.lib.qfd_get_psi(self.h, state, ptr, dev))
         return out
 
+    def observables(self, state=0, min_sep_edge=0.3):
+        """dict of the observables of qfd_observables (lattice units)."""
+        out = (ctypes.c_double * 9)()
+        self._check(self.lib.qfd_observables(self.h, state, float(min_sep_edge), out, 9))
+        keys = ["norm2", "norm2_box", "rho_box", "rho2", "x", "y", "z", "w_plus", "w_minus"]
+        return dict(zip(keys, list(out)))
+
     def step(self, state, nsteps):
         self._check(self.lib.qfd_step(self.h, state, nsteps))
 
@@ -228,6 +237,16 @@ class Plan:
         tb = self.params.tol_bulk if tol_bulk is None else tol_bulk
         self._check(self.lib.qfd_set_limits(self.h, int(max_steps), float(tol), float(tb)))
         self.params.max_steps, self.params.tol, self.params.tol_bulk = int(max_steps), float(tol), float(tb)
+
+    def history(self, state):
+        """[(step, E)] of every check of the last solve of `state`."""
+        cnt = ctypes.c_int()
+        self._check(self.lib.qfd_get_history(self.h, state, None, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        st = (ctypes.c_int64 * max(1, n))()
+        es = (ctypes.c_double * max(1, n))()
+        self._check(self.lib.qfd_get_history(self.h, state, st, es, n, ctypes.byref(cnt)))
+        return [(st[i], es[i]) for i in range(n)]
 
     def stats(self, state):
         s64, s128, eb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()

@@ -271,3 +271,26 @@ def test_timing_and_launch_counters(qfdlib):
         assert cnt == 20 and ms > 0
         assert p.timing_query("z_kinetic")[0] == 20
         assert p.launch_count() >= 80
+
+
+# ---------------------------------------------------------- observables ----
+
+@pytest.mark.parametrize("prec", ["c128", "df64", "c64"])
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+def test_observables_match_oracle(qfdlib, prec, centre):
+    n = 32
+    psi = inputs.uniform_psi(n, 61)
+    d = O.displacement(n, centre)
+    d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+    psi = psi * np.exp(-((d1 - 2) ** 2 + d2 ** 2 + (d3 + 1) ** 2) / 60.0)  # localised, off-centre
+    if prec == "c64":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    if prec == "df64":
+        psi = df_round(psi)
+    with Q.Plan(n, 0.1, 1.0, 1e-4, 2, precision=prec, centre=centre) as p:
+        p.fill_potential("zero")
+        p.set_psi(0, psi)
+        got = p.observables(0, 0.3)
+    ref = O.observables(psi, centre, 0.3)
+    for k, v in ref.items():
+        assert got[k] == pytest.approx(v, rel=1e-12, abs=1e-12), k
