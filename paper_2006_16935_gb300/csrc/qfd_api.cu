@@ -40,7 +40,8 @@ namespace qfd {
 
 // Fixed-order sums of per-CTA partials, then the derived scalars of `op`.
 __global__ void __launch_bounds__(FIN_THREADS)
-k_finalize_op(const double* __restrict__ part, int nq, int count, double* __restrict__ scal, int op) {
+k_finalize_op(const double* __restrict__ part, int nq, int count, double* __restrict__ scal, float* __restrict__ scalf,
+              int op) {
   __shared__ double red[32];
   __shared__ double sums[2 * MAX_LOWER];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -65,7 +66,14 @@ k_finalize_op(const double* __restrict__ part, int nq, int count, double* __rest
     } else if (op == OP_NORM || op == OP_N2PV) {
       scal[SC_N2] = sums[0];
       scal[SC_PV] = sums[1];
-      if (op == OP_NORM) scal[SC_SCALE] = 1.0 / sqrt(sums[0]);
+      if (op == OP_NORM) {
+        const double f = 1.0 / sqrt(sums[0]);
+        scal[SC_SCALE] = f;
+        const df d = dsplit(f);
+        scalf[0] = (float)f;
+        scalf[1] = d.h;
+        scalf[2] = d.l;
+      }
     } else if (op == OP_ENERGY) {
       scal[SC_PT] = sums[0];
       scal[SC_E] = (sums[0] + scal[SC_PV]) / scal[SC_N2];
@@ -215,6 +223,7 @@ struct qfd_plan_s {
   double* partG = nullptr;
   int nA = 0, nC = 0;
   double* scal = nullptr;
+  float* scalf = nullptr;  // the normalisation factor in FP32 and double-float form
   int* flag = nullptr;
   // host-side state
   KinParams kin{};
@@ -357,7 +366,8 @@ LaunchArgs base_args(qfd_plan_t pl) {
 
 qfd_status finalize(qfd_plan_t pl, const double* part, int nq, int count, int op) {
   QFD_RUN(PASS_FINALIZE,
-          (k_finalize_op<<<1, FIN_THREADS, 0, pl->st>>>(part, nq, count, pl->scal, op), cudaGetLastError()));
+          (k_finalize_op<<<1, FIN_THREADS, 0, pl->st>>>(part, nq, count, pl->scal, pl->scalf, op),
+           cudaGetLastError()));
   return QFD_OK;
 }
 
@@ -369,6 +379,7 @@ qfd_status pass_forward_x(qfd_plan_t pl, const void* src, void* psi_out, bool us
   a.src = src;
   a.psi_out = psi_out;
   a.scale = use_scale ? pl->scal + SC_SCALE : nullptr;
+  a.scale_f = pl->scalf;
   a.part = pl->partA;
   a.stats = stats;
   int nb = 0;
@@ -468,6 +479,7 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
   LaunchArgs a = base_args<A>(pl);
   a.psi = psi_of<A>(pl, s);
   a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
+  a.scale_f = pl->scalf;
   a.part = pl->partA;
   a.stats = stats;
   int nb = 0;
@@ -725,6 +737,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       {(void**)&pl->partC, (size_t)npart * sizeof(double)},
       {(void**)&pl->partG, (size_t)2 * MAX_LOWER * npart * sizeof(double)},
       {(void**)&pl->scal, SC_COUNT * sizeof(double)},
+      {(void**)&pl->scalf, 16 * sizeof(float)},
       {(void**)&pl->flag, sizeof(int)},
   };
   if (uses16(p.precision)) {
@@ -780,7 +793,7 @@ void qfd_destroy(qfd_plan_t pl) {
   if (pl->st) cudaStreamSynchronize(pl->st);
   void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
                   pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
-                  pl->partG, pl->scal,  pl->flag};
+                  pl->partG, pl->scal,  pl->scalf, pl->flag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : pl->ev)

@@ -173,6 +173,9 @@ struct F64 {
     return kp.kinterm == 3 ? sqrt(s + kp.am2) * kp.inv_a_n3 - kp.m0_n3 : s * kp.pref;
   }
   static __device__ __forceinline__ S scalar(double s) { return s; }
+  // the normalisation factor as written by the reduction kernel: FP64 value,
+  // then its FP32 rounding and double-float split in a float array
+  static __device__ __forceinline__ S load_scale(const double* d, const float*) { return *d; }
   // Eq. (iter_proced) as printed: A psi - (B dtau) H_K psi
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     return C{cf.x * ps.x - cf.y * hk.x, cf.x * ps.y - cf.y * hk.y};
@@ -212,6 +215,7 @@ struct F32 {
     return kp.kinterm == 3 ? sqrtf(s + kp.f_am2) * kp.f_ia - kp.f_m0 : s * kp.f_pref;
   }
   static __device__ __forceinline__ S scalar(double s) { return (float)s; }
+  static __device__ __forceinline__ S load_scale(const double*, const float* f) { return f[0]; }
   // psi - ((1 - A) psi + (B dtau) H_K psi): the O(dtau) increment keeps FP32 relative precision
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     return C{ps.x - (cf.y * ps.x + cf.x * hk.x), ps.y - (cf.y * ps.y + cf.x * hk.y)};
@@ -258,6 +262,7 @@ struct DF {
     return kp.kinterm == 3 ? dsub(dmul(dsqrt(dadd(s, kp.d_am2)), kp.d_ia), kp.d_m0) : dmul(s, kp.d_pref);
   }
   static __device__ __forceinline__ S scalar(double s) { return dsplit(s); }
+  static __device__ __forceinline__ S load_scale(const double*, const float* f) { return df{f[1], f[2]}; }
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     const df dx = dmul_add(cf.y, ps.x, cf.x, hk.x), dy = dmul_add(cf.y, ps.y, cf.x, hk.y);
     return dfc{dsub(ps.x, dx), dsub(ps.y, dy)};
@@ -451,6 +456,9 @@ template <typename C, int PS, int T> struct AccLine {
 #ifndef QFD_YCOLS_MIN8
 #define QFD_YCOLS_MIN8 8
 #endif
+#ifndef QFD_EARLY_COEF16
+#define QFD_EARLY_COEF16 1
+#endif
 #ifndef QFD_TILE_TARGET
 #define QFD_TILE_TARGET 256
 #endif
@@ -603,8 +611,8 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 template <class A, int N, int STATS>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
-           const double* __restrict__ V, const double* __restrict__ scale, const typename A::C* __restrict__ tw,
-           double* __restrict__ part) {
+           const double* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
+           const typename A::C* __restrict__ tw, double* __restrict__ part) {
   using C = typename A::C;
   using K = typename A::K;
   using SH = Shape<A, N>;
@@ -613,31 +621,33 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   const int col = threadIdx.x % SH::XCOLS, t = threadIdx.x / SH::XCOLS;
   const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;
   constexpr int64_t S = (int64_t)N * N;
-  // psi and the coefficients are loaded before the inverse transform so that
-  // their latency overlaps it (measured faster for every policy)
-  constexpr bool EARLY = true;
-  C v[8], ps[EARLY ? 8 : 1];
-  K cf[EARLY ? 8 : 1];
+  // psi (and, unless QFD_EARLY_COEF16 is 0 for 16-byte policies, the
+  // coefficients) are loaded before the inverse transform so that their
+  // latency overlaps it
+  constexpr bool EARLY_K = sizeof(C) == 8 || QFD_EARLY_COEF16;
+  C v[8], ps[8];
+  K cf[EARLY_K ? 8 : 1];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (t + m * SH::T) * S];
-  if constexpr (EARLY) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
+  for (int m = 0; m < 8; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
+  if constexpr (EARLY_K) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) cf[m] = coef[base + (t + m * SH::T) * S];
   }
   AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, +1>(v, t, tw, acc);
   const bool scaled = scale != nullptr;
-  const typename A::S s = A::scalar(scaled ? *scale : 1.0);
+  typename A::S s{};
+  if (scaled) s = A::load_scale(scale, scale_f);
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
     C nw;
-    if constexpr (EARLY) nw = A::update(ps[m], v[m], cf[m]);
-    else nw = A::update(psi[idx], v[m], coef[idx]);
+    if constexpr (EARLY_K) nw = A::update(ps[m], v[m], cf[m]);
+    else nw = A::update(ps[m], v[m], coef[idx]);
     if (scaled) nw = cscale(nw, s);
     psi[idx] = nw;
     v[m] = nw;
@@ -664,7 +674,8 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
 template <class A, int N, int STATS>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, const double* __restrict__ V,
-            const double* __restrict__ scale, const typename A::C* __restrict__ tw, double* __restrict__ part) {
+            const double* __restrict__ scale, const float* __restrict__ scale_f, const typename A::C* __restrict__ tw,
+            double* __restrict__ part) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -673,7 +684,8 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;
   constexpr int64_t S = (int64_t)N * N;
   const bool scaled = scale != nullptr;
-  const typename A::S s = A::scalar(scaled ? *scale : 1.0);
+  typename A::S s{};
+  if (scaled) s = A::load_scale(scale, scale_f);
   C v[8];
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
@@ -772,10 +784,12 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
   constexpr int64_t S = (int64_t)N * N;
   const int y = (int)(base / N), z = (int)(base % N);
   const int64_t rbase = (int64_t)reflect1<N>(y, offgrid) * N + reflect1<N>(z, offgrid);
+  // the overlaps in the policy's representation (converted only when there
+  // are lower states: conversions from FP64 run on the slow FP64 pipe)
   C cc[MAX_LOWER];
-#pragma unroll
-  for (int j = 0; j < MAX_LOWER; ++j)
-    if (j < k) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
+  if (k > 0) {
+    for (int j = 0; j < k; ++j) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
+  }
   C v[8];
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;

@@ -38,7 +38,8 @@ struct LaunchArgs {
   void* psi_out = nullptr;     // forward-x: where to store the scaled input (or null)
   const void* coef = nullptr;  // update coefficients per site
   const double* V = nullptr;   // FP64 potential
-  const double* scale = nullptr;
+  const double* scale = nullptr;  // normalisation factor (FP64) or null
+  const float* scale_f = nullptr;  // its FP32 rounding and double-float split
   const void* tw = nullptr;    // twiddles exp(-2 pi i e / N), e < N
   const void* ktab = nullptr;  // per-axis kinetic table
   const KinParams* kin = nullptr;

@@ -21,7 +21,7 @@ cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<grid, SH::XTHREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, a.V, a.scale,
-                                                      (const C*)a.tw, a.part);
+                                                  a.scale_f, (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL>);
   else if (a.stats == STATS_NORM) go(k_update_x<A, N, STATS_NORM>);
@@ -39,7 +39,7 @@ cudaError_t Launch<A, N>::forward_x(const LaunchArgs& a, int* nblocks) {
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, (C*)a.W, (C*)a.psi_out, a.V, a.scale,
-                                                      (const C*)a.tw, a.part);
+                                                  a.scale_f, (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_forward_x<A, N, STATS_FULL>);
   else if (a.stats == STATS_NORM) go(k_forward_x<A, N, STATS_NORM>);
