@@ -225,6 +225,7 @@ struct qfd_plan_s {
   double* scal = nullptr;
   float* scalf = nullptr;  // the normalisation factor in FP32 and double-float form
   int* flag = nullptr;
+  int* errflag = nullptr;  // set by a kernel whose bounded wait for a bulk copy ran out
   // host-side state
   KinParams kin{};
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
@@ -360,8 +361,21 @@ LaunchArgs base_args(qfd_plan_t pl) {
   a.kin = &pl->kin;
   a.coef = coef_of<A>(pl);
   a.V = pl->V;
+  a.err = pl->errflag;
   a.stream = pl->st;
   return a;
+}
+
+// QFD_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check.
+qfd_status check_kernel_errors(qfd_plan_t pl) {
+  int e = 0;
+  QFD_CK(cudaMemcpyAsync(&e, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  if (e) {
+    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
+    return fail(pl, QFD_ERR_TIMEOUT, "a bulk copy did not complete within the kernel's bounded wait");
+  }
+  return QFD_OK;
 }
 
 qfd_status finalize(qfd_plan_t pl, const double* part, int nq, int count, int op) {
@@ -518,7 +532,7 @@ qfd_status energy_tail(qfd_plan_t pl, double* E, double* n2) {
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   double h[SC_COUNT];
   QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
-  QFD_CK(cudaStreamSynchronize(pl->st));
+  if ((r = check_kernel_errors(pl)) != QFD_OK) return r;
   if (E) *E = h[SC_E];
   if (n2) *n2 = h[SC_N2];
   return QFD_OK;
@@ -739,6 +753,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       {(void**)&pl->scal, SC_COUNT * sizeof(double)},
       {(void**)&pl->scalf, 16 * sizeof(float)},
       {(void**)&pl->flag, sizeof(int)},
+      {(void**)&pl->errflag, sizeof(int)},
   };
   if (uses16(p.precision)) {
     allocs.push_back({(void**)&pl->psi16, (size_t)(p.nstates + 1) * n3 * 16});
@@ -782,7 +797,8 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
             cudaMemcpy(pl->ktab64, ktab.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktab32, kt32.data(), n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktabdf, ktdf.data(), n * sizeof(df), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess;
+            cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess &&
+            cudaMemset(pl->errflag, 0, sizeof(int)) == cudaSuccess;
   if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
   *out = pl;
   return QFD_OK;
@@ -793,7 +809,7 @@ void qfd_destroy(qfd_plan_t pl) {
   if (pl->st) cudaStreamSynchronize(pl->st);
   void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
                   pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
-                  pl->partG, pl->scal,  pl->scalf, pl->flag};
+                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->errflag};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : pl->ev)
@@ -947,7 +963,8 @@ qfd_status qfd_step(qfd_plan_t pl, int s, int64_t nsteps) {
       qfd_status q = step_once<A>(pl, s, 0);
       if (q != QFD_OK) return q;
     }
-    return materialize<A>(pl, s);
+    qfd_status q = materialize<A>(pl, s);
+    return q != QFD_OK ? q : check_kernel_errors(pl);
   });
 }
 

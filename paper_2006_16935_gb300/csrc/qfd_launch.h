@@ -44,6 +44,7 @@ struct LaunchArgs {
   const void* ktab = nullptr;  // per-axis kinetic table
   const KinParams* kin = nullptr;
   double* part = nullptr;      // per-CTA partials
+  int* err = nullptr;          // set to nonzero by a kernel whose bounded wait ran out
   int stats = 0;               // STATS_* for passes A / forward x, Parseval flag for pass C
   cudaStream_t stream = 0;
   // projection / Gram-Schmidt

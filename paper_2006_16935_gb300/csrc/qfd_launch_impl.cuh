@@ -113,7 +113,7 @@ template <class A, int N>
 int Launch<A, N>::partials() {
   using SH = Shape<A, N>;
   const int x = (int)((int64_t)N * N / SH::XCOLS);
-  const int z = (int)((int64_t)N * N / SH::LINES);
+  const int z = (int)((int64_t)N * N / SH::LINES);  // bounds the persistent z-pass grid too
   return x > z ? x : z;
 }
 
