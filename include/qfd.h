@@ -34,6 +34,7 @@
 #ifndef QFD_H
 #define QFD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -224,6 +225,68 @@ int64_t qfd_launch_count(qfd_plan_t plan);
  * current); make it before any stream capture. */
 qfd_status qfd_energy_noalloc(const double* psi, const double* V, int64_t n, double a, double mass, int kinetic,
                               int rest_mass, void* stream, double* E, double* norm2);
+
+/* Device bytes a plan with these parameters allocates (used for admission by
+ * budget). */
+size_t qfd_plan_bytes(const qfd_params* params);
+
+/* ------------------------------------------------------------- server ----
+ * Continuous batching of solve requests (a serving form of the method; the
+ * paper has a single solve per run).  Requests wait in FIFO order and are
+ * admitted while the device bytes of the admitted requests (qfd_plan_bytes)
+ * stay within hbm_budget_bytes; each admitted request owns a plan on its own
+ * stream, so requests overlap on the device.  qfd_server_poll admits what
+ * fits, advances every active request by one period (check_every steps and
+ * an energy check, exactly as qfd_solve_states does), applies each request's
+ * stop rule and moves it to its next phase or state, and returns the results
+ * of the requests that finished.  While the set of active requests and their
+ * phases do not change, the period is captured once as a CUDA graph and
+ * replayed.  A request's numbers are the same alone and in any mix. */
+typedef struct qfd_server_s* qfd_server_t;
+
+typedef struct {
+  double hbm_budget_bytes; /* admission budget (device bytes of admitted requests) */
+  int32_t max_active;      /* at most this many requests at once (0: no limit) */
+  int32_t check_every;     /* steps per period; a multiple of ortho_every */
+  int32_t ortho_every;     /* projection / normalisation cadence of every request */
+  int32_t use_graphs;      /* 1: capture and replay a period of an unchanged set */
+  void* stream;            /* cudaStream_t the periods fork from, or NULL */
+} qfd_server_params;
+
+typedef struct {
+  int64_t n;               /* lattice as in qfd_params */
+  double a, mass, dtau;
+  int32_t kinetic, rest_mass;
+  int32_t nstates;         /* 1..8 states, solved in turn with Gram-Schmidt */
+  int32_t precision;       /* QFD_C128, QFD_C64, QFD_DF64, QFD_C64_REFINE, QFD_C64_REFINE_DF */
+  int32_t potential;       /* QFD_POT_* with coefficients pot_coeffs[0..1] */
+  double pot_coeffs[2];
+  int32_t centre;
+  int32_t parity[8];       /* per state */
+  uint64_t seed;           /* state i starts from qfd_fill_psi_uniform(seed + i) */
+  int64_t max_steps;       /* per state and phase */
+  double tol, tol_bulk;
+} qfd_request;
+
+typedef struct {
+  int64_t id;
+  int32_t status;          /* QFD_OK, QFD_ERR_NOT_CONVERGED, or the error that ended it */
+  int32_t nstates;
+  double energy[8];        /* final energy per state */
+  int64_t steps[8];        /* steps per state (all phases) */
+  int64_t steps_c64[8];    /* of which complex64 bulk steps */
+  double t_submit, t_admit, t_done; /* seconds on the server clock */
+} qfd_result;
+
+qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out);
+void qfd_server_destroy(qfd_server_t server);
+const char* qfd_server_last_error(qfd_server_t server);
+double qfd_server_clock(qfd_server_t server);
+qfd_status qfd_server_submit(qfd_server_t server, const qfd_request* request, int64_t* id);
+/* One scheduling round; up to `capacity` finished results are written to out. */
+qfd_status qfd_server_poll(qfd_server_t server, qfd_result* out, int capacity, int* count);
+qfd_status qfd_server_stats(qfd_server_t server, int* waiting, int* active, double* used_bytes, int64_t* periods,
+                            int64_t* graph_replays, int64_t* graph_captures);
 
 /* The plan's CUDA stream (cudaStream_t) for event recording by the caller. */
 void* qfd_get_stream(qfd_plan_t plan);

@@ -9,7 +9,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <deque>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -226,6 +228,7 @@ struct qfd_plan_s {
   float* scalf = nullptr;  // the normalisation factor in FP32 and double-float form
   int* flag = nullptr;
   int* errflag = nullptr;  // set by a kernel whose bounded wait for a bulk copy ran out
+  double* hscal = nullptr;  // pinned host copy of the scalars (+ the error flag)
   // host-side state
   KinParams kin{};
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
@@ -548,11 +551,13 @@ qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
   return energy_tail<A>(pl, E, n2);
 }
 
-// One state in one arithmetic: cadence at t = 0, then blocks of check_every
-// steps, each followed by the energy and the relative-change test.
+// One state in one arithmetic is a phase: begin_phase (counter reset and the
+// cadence at t = 0), then periods of check_every steps each ending with the
+// energy, then finish_phase (normalise).  qfd_solve_states and the request
+// server share these pieces, so a request gives the same numbers alone, in a
+// server mix, or through qfd_solve_states.
 template <class A>
-qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, double* E_out, int64_t* steps,
-                       bool* converged, bool bulk = false) {
+qfd_status begin_phase(qfd_plan_t pl, int s) {
   qfd_status r;
   pl->t[s] = 0;
   pl->pending = false;
@@ -561,36 +566,80 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
     if ((r = pass_forward_x<A>(pl, psi_of<A>(pl, s), nullptr, false, STATS_NORM)) != QFD_OK) return r;
     mark_w<A>(pl, s, ST_X);
   }
-  if ((r = cadence<A>(pl, s, 0)) != QFD_OK) return r;
-  double e = NAN, e_prev = NAN, n2 = NAN;
-  int checks = 0;
-  *converged = false;
+  return cadence<A>(pl, s, 0);
+}
+
+// check_every steps and the energy of their last state; the scalars (E at
+// SC_E, N2 at SC_N2) and the kernel error flag are copied asynchronously into
+// `host` (pinned, SC_COUNT doubles followed by one int).  Nothing here
+// synchronises, so a period can be captured into a CUDA graph.
+template <class A>
+qfd_status period_launch(qfd_plan_t pl, int s, double* host) {
+  qfd_status r;
   const int ce = pl->p.check_every;
-  while (pl->t[s] < max_steps) {
-    for (int j = 0; j < ce; ++j)
-      if ((r = step_once<A>(pl, s, j == ce - 1)) != QFD_OK) return r;
-    if ((r = energy_tail<A>(pl, &e, &n2)) != QFD_OK) return r;
-    if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
-      return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
-    pl->hist[s].push_back({pl->t[s], e});
-    ++checks;
-    if (tol >= 0 && checks > 1 && std::fabs(e - e_prev) <= tol * std::fabs(e)) {
-      *converged = true;
-      break;
-    }
-    // complex64 bulk of a mixed solve: once the energy rises between checks the
-    // FP32 rounding noise dominates the decay and the refinement takes over
-    if (bulk && checks > 3 && e > e_prev) {
-      *converged = true;
-      break;
-    }
-    e_prev = e;
-  }
+  for (int j = 0; j < ce; ++j)
+    if ((r = step_once<A>(pl, s, j == ce - 1)) != QFD_OK) return r;
+  if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
+  if ((r = advance_to_d<A>(pl, 1)) != QFD_OK) return r;
+  if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
+  QFD_CK(cudaMemcpyAsync(host, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaMemcpyAsync(host + SC_COUNT, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
+  return QFD_OK;
+}
+
+template <class A>
+qfd_status finish_phase(qfd_plan_t pl, int s) {
   // leave the state normalised (its last finalised N2 is of the stored values)
   QFD_RUN(PASS_OTHER, (k_scale<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->n3, pl->scal + SC_N2, 1),
                        cudaGetLastError()));
   pl->pending = false;
   pl->w_stage = ST_NONE;
+  return QFD_OK;
+}
+
+// The stop rule applied after every period (TOLERANCE of Sec. 5.1): done when
+// |E - E_prev| <= tol |E| from the second check on; a complex64 bulk phase also
+// stops once its energy rises between checks after the third one (FP32 noise
+// floor).  Returns QFD_ERR_DIVERGED for a non-finite energy or norm.
+struct PhaseTracker {
+  double e_prev = NAN;
+  int checks = 0;
+};
+qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, bool bulk, PhaseTracker& tr,
+                       bool* done, double* e_out) {
+  const double e = host[SC_E], n2 = host[SC_N2];
+  int kerr = 0;
+  std::memcpy(&kerr, host + SC_COUNT, sizeof(int));
+  if (kerr) {
+    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
+    return fail(pl, QFD_ERR_TIMEOUT, "a bulk copy did not complete within the kernel's bounded wait");
+  }
+  if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
+    return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
+  pl->hist[s].push_back({pl->t[s], e});
+  ++tr.checks;
+  *done = (tol >= 0 && tr.checks > 1 && std::fabs(e - tr.e_prev) <= tol * std::fabs(e)) ||
+          (bulk && tr.checks > 3 && e > tr.e_prev);
+  tr.e_prev = e;
+  *e_out = e;
+  return QFD_OK;
+}
+
+template <class A>
+qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, double* E_out, int64_t* steps,
+                       bool* converged, bool bulk = false) {
+  qfd_status r;
+  if ((r = begin_phase<A>(pl, s)) != QFD_OK) return r;
+  PhaseTracker tr;
+  double e = NAN;
+  *converged = false;
+  while (pl->t[s] < max_steps) {
+    if ((r = period_launch<A>(pl, s, pl->hscal)) != QFD_OK) return r;
+    QFD_CK(cudaStreamSynchronize(pl->st));
+    if ((r = phase_check(pl, s, pl->hscal, tol, bulk, tr, converged, &e)) != QFD_OK) return r;
+    if (*converged) break;
+  }
+  if ((r = finish_phase<A>(pl, s)) != QFD_OK) return r;
   *E_out = e;
   *steps = pl->t[s];
   return QFD_OK;
@@ -638,6 +687,17 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
 }
 
 bool uses16(int precision) { return precision != QFD_C64; }
+bool uses32(int precision);
+// Device bytes a plan with these parameters allocates (lattices, tables, partials).
+size_t plan_device_bytes(const qfd_params& p) {
+  const size_t n = (size_t)p.n, n3 = n * n * n;
+  const size_t npart = (size_t)std::max(
+      std::max(std::max(max_partials<F64>(p.n), max_partials<F32>(p.n)), max_partials<DF>(p.n)), GS_BLOCKS);
+  size_t b = n3 * 16 + n3 * 8 + n * (16 + 8 + 16 + 8 + 4 + 8) + npart * 8 * (3 + 2 * MAX_LOWER) + 1024;
+  if (uses16(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 16;
+  if (uses32(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 8;
+  return b;
+}
 bool uses32(int precision) {
   return precision == QFD_C64 || precision == QFD_C64_REFINE || precision == QFD_C64_REFINE_DF;
 }
@@ -800,6 +860,8 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
             cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess &&
             cudaMemset(pl->errflag, 0, sizeof(int)) == cudaSuccess;
   if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
+  if (cudaHostAlloc((void**)&pl->hscal, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+    return cleanup_fail(QFD_ERR_OOM, "pinned host buffer allocation failed");
   *out = pl;
   return QFD_OK;
 }
@@ -812,6 +874,7 @@ void qfd_destroy(qfd_plan_t pl) {
                   pl->partG, pl->scal,  pl->scalf, pl->flag, pl->errflag};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (pl->hscal) cudaFreeHost(pl->hscal);
   for (auto& v : pl->ev)
     for (auto e : v) cudaEventDestroy(e);
   if (pl->own_stream && pl->st) cudaStreamDestroy(pl->st);
@@ -1089,6 +1152,382 @@ void* qfd_get_stream(qfd_plan_t pl) { return pl ? (void*)pl->st : nullptr; }
 qfd_status qfd_sync(qfd_plan_t pl) {
   if (!pl) return QFD_ERR_ARG;
   QFD_CK(cudaStreamSynchronize(pl->st));
+  return QFD_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ server
+static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 144 && sizeof(qfd_result) == 232 &&
+                  sizeof(qfd_server_params) == 32,
+              "C ABI struct layouts are fixed (the Python binding mirrors them)");
+// Continuous batching of solve requests: requests wait in FIFO order and are
+// admitted while their device bytes fit the budget; every admitted request
+// owns a plan with its own stream, so the requests' kernels overlap on the
+// device.  qfd_server_poll advances every active request by one period
+// (check_every steps and an energy check) - forked from the server stream to
+// the request streams and joined back - then applies each request's stop rule
+// and moves it to its next phase, state or completion.  While the active set
+// and every request's phase stay the same, the period is captured once as a
+// CUDA graph and replayed.
+struct ReqRun {
+  int64_t id = 0;
+  qfd_request req{};
+  qfd_plan_t plan = nullptr;
+  size_t bytes = 0;
+  int state = 0;
+  int phase = 0;      // policy id of the running phase
+  bool bulk = false;  // complex64 bulk of a mixed request
+  bool fresh = true;  // its first period in this phase is still to run
+  PhaseTracker tr;
+  qfd_result res{};
+};
+
+struct qfd_server_s {
+  qfd_server_params p{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::deque<ReqRun*> waiting;
+  std::vector<ReqRun*> active;
+  std::vector<qfd_result> done;
+  size_t used = 0;
+  int64_t next_id = 1;
+  double* hbuf = nullptr;  // pinned, (SC_COUNT + 1) doubles per active request
+  size_t hcap = 0;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> gsig;  // (id, state, phase) of the captured period
+  int64_t periods = 0, replays = 0, captures = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+};
+
+namespace {
+
+double server_clock(qfd_server_t sv) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - sv->t0).count();
+}
+
+qfd_status sfail(qfd_server_t sv, qfd_status s, const std::string& msg) {
+  sv->err = msg;
+  return s;
+}
+
+qfd_params request_params(const qfd_server_t sv, const qfd_request& r) {
+  qfd_params p{};
+  p.n = r.n;
+  p.a = r.a;
+  p.mass = r.mass;
+  p.dtau = r.dtau;
+  p.kinetic = r.kinetic;
+  p.rest_mass = r.rest_mass;
+  p.nstates = r.nstates;
+  p.precision = r.precision;
+  p.ortho_every = sv->p.ortho_every;
+  p.check_every = sv->p.check_every;
+  p.centre = r.centre;
+  p.max_steps = r.max_steps;
+  p.tol = r.tol;
+  p.tol_bulk = r.tol_bulk;
+  p.stream = nullptr;
+  return p;
+}
+
+// Starts state `s` of a request: the complex64 bulk for mixed requests, else
+// the plan's arithmetic.
+qfd_status start_state(ReqRun* m, int s) {
+  qfd_plan_t pl = m->plan;
+  qfd_status r;
+  m->state = s;
+  m->tr = PhaseTracker{};
+  m->fresh = true;
+  pl->parity[s] = m->req.parity[s];
+  pl->steps32[s] = pl->steps16[s] = 0;
+  pl->ebulk[s] = NAN;
+  pl->hist[s].clear();
+  if (refines(pl->p.precision)) {
+    m->bulk = true;
+    m->phase = 1;
+    if ((r = convert_state(pl, s, 1)) != QFD_OK) return r;
+  } else {
+    m->bulk = false;
+    m->phase = uses32(pl->p.precision) ? 1 : pl->arith16;
+  }
+  pl->phase = m->phase;
+  return with_policy(m->phase, [&](auto pol) -> qfd_status { return begin_phase<decltype(pol)>(pl, s); });
+}
+
+qfd_status admit(qfd_server_t sv) {
+  while (!sv->waiting.empty()) {
+    if (sv->p.max_active > 0 && (int)sv->active.size() >= sv->p.max_active) break;
+    ReqRun* m = sv->waiting.front();
+    const qfd_params prm = request_params(sv, m->req);
+    m->bytes = plan_device_bytes(prm);
+    if (sv->used + m->bytes > (size_t)sv->p.hbm_budget_bytes) {
+      if (!sv->active.empty()) break;  // wait for memory to free up
+      m->res.status = QFD_ERR_OOM;     // can never fit the budget
+      m->res.t_done = server_clock(sv);
+      sv->done.push_back(m->res);
+      sv->waiting.pop_front();
+      delete m;
+      continue;
+    }
+    qfd_status r = qfd_plan(&prm, &m->plan);
+    if (r == QFD_ERR_OOM && !sv->active.empty()) break;
+    sv->waiting.pop_front();
+    if (r == QFD_OK) {
+      const double c[2] = {m->req.pot_coeffs[0], m->req.pot_coeffs[1]};
+      r = qfd_fill_potential(m->plan, m->req.potential, c, 2);
+      for (int s = 0; r == QFD_OK && s < m->req.nstates; ++s) r = qfd_fill_psi_uniform(m->plan, s, m->req.seed + s);
+      if (r == QFD_OK) r = start_state(m, 0);
+    }
+    if (r != QFD_OK) {
+      m->res.status = r;
+      m->res.t_done = server_clock(sv);
+      sv->done.push_back(m->res);
+      qfd_destroy(m->plan);
+      delete m;
+      continue;
+    }
+    m->res.t_admit = server_clock(sv);
+    sv->used += m->bytes;
+    sv->active.push_back(m);
+  }
+  return QFD_OK;
+}
+
+// After a period: stop rule, then the next phase, state or completion.
+qfd_status advance_request(qfd_server_t sv, ReqRun* m, const double* host, bool* finished) {
+  qfd_plan_t pl = m->plan;
+  const int s = m->state;
+  *finished = false;
+  m->fresh = false;
+  bool done = false;
+  double e = NAN;
+  qfd_status r = phase_check(pl, s, host, m->bulk ? pl->p.tol_bulk : pl->p.tol, m->bulk, m->tr, &done, &e);
+  if (r != QFD_OK) return r;
+  if (!done && pl->t[s] < pl->p.max_steps) return QFD_OK;
+  const bool converged = done;
+  r = with_policy(m->phase, [&](auto pol) -> qfd_status { return finish_phase<decltype(pol)>(pl, s); });
+  if (r != QFD_OK) return r;
+  if (m->bulk) {  // hand the state over to the refinement arithmetic
+    pl->steps32[s] = pl->t[s];
+    pl->ebulk[s] = e;
+    if ((r = convert_state(pl, s, 0)) != QFD_OK) return r;
+    m->bulk = false;
+    m->phase = pl->arith16;
+    pl->phase = m->phase;
+    m->tr = PhaseTracker{};
+    m->fresh = true;
+    return with_policy(m->phase, [&](auto pol) -> qfd_status { return begin_phase<decltype(pol)>(pl, s); });
+  }
+  if (m->phase == 1) pl->steps32[s] = pl->t[s];
+  else pl->steps16[s] = pl->t[s];
+  m->res.energy[s] = e;
+  m->res.steps[s] = pl->steps32[s] + pl->steps16[s];
+  m->res.steps_c64[s] = pl->steps32[s];
+  if (!converged && pl->p.tol >= 0) m->res.status = QFD_ERR_NOT_CONVERGED;
+  if (refines(pl->p.precision) && (r = convert_state(pl, s, 1)) != QFD_OK) return r;
+  if (s + 1 < m->req.nstates) return start_state(m, s + 1);
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  *finished = true;
+  return QFD_OK;
+}
+
+// Issues one period of every active request, forked from the server stream.
+qfd_status issue_period(qfd_server_t sv) {
+  cudaEventRecord(sv->fork, sv->st);
+  for (size_t i = 0; i < sv->active.size(); ++i) {
+    ReqRun* m = sv->active[i];
+    if (cudaStreamWaitEvent(m->plan->st, sv->fork, 0) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "fork");
+    double* slot = sv->hbuf + i * (SC_COUNT + 1);
+    qfd_status r = with_policy(m->phase, [&](auto pol) -> qfd_status {
+      return period_launch<decltype(pol)>(m->plan, m->state, slot);
+    });
+    if (r != QFD_OK) return sfail(sv, r, m->plan->err);
+    cudaEventRecord(sv->joins[i], m->plan->st);
+    cudaStreamWaitEvent(sv->st, sv->joins[i], 0);
+  }
+  return QFD_OK;
+}
+
+qfd_status run_period(qfd_server_t sv) {
+  const size_t na = sv->active.size();
+  if (na > sv->hcap) {
+    if (sv->exec) {
+      cudaGraphExecDestroy(sv->exec);
+      sv->exec = nullptr;
+    }
+    if (sv->hbuf) cudaFreeHost(sv->hbuf);
+    sv->hcap = std::max<size_t>(na, 2 * sv->hcap);
+    if (cudaHostAlloc((void**)&sv->hbuf, sv->hcap * (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault) !=
+        cudaSuccess) {
+      sv->hbuf = nullptr;
+      sv->hcap = 0;
+      return sfail(sv, QFD_ERR_OOM, "pinned host buffer");
+    }
+  }
+  while (sv->joins.size() < na) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "event");
+    sv->joins.push_back(e);
+  }
+  std::vector<int64_t> sig;
+  bool any_fresh = false;
+  for (ReqRun* m : sv->active) {
+    sig.push_back(m->id);
+    sig.push_back(m->state);
+    sig.push_back(m->phase);
+    any_fresh = any_fresh || m->fresh;
+  }
+  qfd_status r = QFD_OK;
+  if (!sv->p.use_graphs || any_fresh) {
+    r = issue_period(sv);
+  } else if (sv->exec && sig == sv->gsig) {
+    // replay: the device repeats the captured period; the host state advances as
+    // it did during the capture (only the step counters change between periods)
+    if (cudaGraphLaunch(sv->exec, sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    for (ReqRun* m : sv->active) m->plan->t[m->state] += m->plan->p.check_every;
+    ++sv->replays;
+  } else {
+    if (sv->exec) {
+      cudaGraphExecDestroy(sv->exec);
+      sv->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(sv->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return sfail(sv, QFD_ERR_CUDA, "begin capture");
+    r = issue_period(sv);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(sv->st, &g);
+    if (r != QFD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ce != cudaSuccess || !g) return sfail(sv, QFD_ERR_CUDA, "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&sv->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph instantiate");
+    sv->gsig = sig;
+    if (cudaGraphLaunch(sv->exec, sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    ++sv->captures;
+  }
+  if (r != QFD_OK) return r;
+  if (cudaStreamSynchronize(sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "period synchronise");
+  ++sv->periods;
+  std::vector<ReqRun*> keep;
+  for (size_t i = 0; i < na; ++i) {
+    ReqRun* m = sv->active[i];
+    bool finished = false;
+    qfd_status q = advance_request(sv, m, sv->hbuf + i * (SC_COUNT + 1), &finished);
+    if (q != QFD_OK) {
+      m->res.status = q;
+      finished = true;
+      cudaStreamSynchronize(m->plan->st);
+    }
+    if (finished) {
+      m->res.t_done = server_clock(sv);
+      m->res.nstates = m->req.nstates;
+      sv->done.push_back(m->res);
+      sv->used -= m->bytes;
+      qfd_destroy(m->plan);
+      delete m;
+    } else {
+      keep.push_back(m);
+    }
+  }
+  sv->active.swap(keep);
+  return QFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qfd_plan_bytes(const qfd_params* p) { return p ? plan_device_bytes(*p) : 0; }
+
+qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out) {
+  if (out) *out = nullptr;
+  if (!params || !out || !(params->hbm_budget_bytes > 0) || params->ortho_every < 1 || params->check_every < 1 ||
+      params->check_every % params->ortho_every != 0 || params->max_active < 0)
+    return QFD_ERR_ARG;
+  qfd_server_t sv = new qfd_server_s();
+  sv->p = *params;
+  if (params->stream) {
+    sv->st = (cudaStream_t)params->stream;
+  } else if (cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete sv;
+    return QFD_ERR_CUDA;
+  } else {
+    sv->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming) != cudaSuccess) {
+    qfd_server_destroy(sv);
+    return QFD_ERR_CUDA;
+  }
+  *out = sv;
+  return QFD_OK;
+}
+
+void qfd_server_destroy(qfd_server_t sv) {
+  if (!sv) return;
+  if (sv->st) cudaStreamSynchronize(sv->st);
+  for (ReqRun* m : sv->active) {
+    qfd_destroy(m->plan);
+    delete m;
+  }
+  for (ReqRun* m : sv->waiting) delete m;
+  if (sv->exec) cudaGraphExecDestroy(sv->exec);
+  for (auto e : sv->joins) cudaEventDestroy(e);
+  if (sv->fork) cudaEventDestroy(sv->fork);
+  if (sv->hbuf) cudaFreeHost(sv->hbuf);
+  if (sv->own_stream && sv->st) cudaStreamDestroy(sv->st);
+  delete sv;
+}
+
+const char* qfd_server_last_error(qfd_server_t sv) { return sv ? sv->err.c_str() : ""; }
+
+double qfd_server_clock(qfd_server_t sv) { return sv ? server_clock(sv) : 0.0; }
+
+qfd_status qfd_server_submit(qfd_server_t sv, const qfd_request* req, int64_t* id) {
+  if (!sv || !req) return QFD_ERR_ARG;
+  if (req->nstates < 1 || req->nstates > MAX_LOWER || !supported_n(req->n))
+    return sfail(sv, QFD_ERR_ARG, "request: nstates 1..8 and a supported n");
+  for (int s = 0; s < req->nstates; ++s)
+    if (req->parity[s] < -1 || req->parity[s] > 1) return sfail(sv, QFD_ERR_ARG, "request: parity -1, 0 or 1");
+  ReqRun* m = new ReqRun();
+  m->id = sv->next_id++;
+  m->req = *req;
+  m->res.id = m->id;
+  m->res.status = QFD_OK;
+  m->res.nstates = req->nstates;
+  m->res.t_submit = server_clock(sv);
+  for (int s = 0; s < 8; ++s) m->res.energy[s] = NAN;
+  sv->waiting.push_back(m);
+  if (id) *id = m->id;
+  return QFD_OK;
+}
+
+qfd_status qfd_server_poll(qfd_server_t sv, qfd_result* out, int capacity, int* count) {
+  if (!sv || capacity < 0 || (capacity > 0 && !out)) return QFD_ERR_ARG;
+  qfd_status r = admit(sv);
+  if (r == QFD_OK && !sv->active.empty()) r = run_period(sv);
+  const int n = (int)std::min<size_t>(sv->done.size(), (size_t)capacity);
+  for (int i = 0; i < n; ++i) out[i] = sv->done[i];
+  sv->done.erase(sv->done.begin(), sv->done.begin() + n);
+  if (count) *count = n;
+  return r;
+}
+
+qfd_status qfd_server_stats(qfd_server_t sv, int* waiting, int* active, double* used_bytes, int64_t* periods,
+                            int64_t* graph_replays, int64_t* graph_captures) {
+  if (!sv) return QFD_ERR_ARG;
+  if (waiting) *waiting = (int)sv->waiting.size();
+  if (active) *active = (int)sv->active.size();
+  if (used_bytes) *used_bytes = (double)sv->used;
+  if (periods) *periods = sv->periods;
+  if (graph_replays) *graph_replays = sv->replays;
+  if (graph_captures) *graph_captures = sv->captures;
   return QFD_OK;
 }
 

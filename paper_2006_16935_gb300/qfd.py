@@ -46,6 +46,26 @@ class QfdParams(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("ortho_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("a", ctypes.c_double), ("mass", ctypes.c_double), ("dtau", ctypes.c_double),
+                ("kinetic", ctypes.c_int32), ("rest_mass", ctypes.c_int32), ("nstates", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("potential", ctypes.c_int32), ("pot_coeffs", ctypes.c_double * 2),
+                ("centre", ctypes.c_int32), ("parity", ctypes.c_int32 * 8), ("seed", ctypes.c_uint64),
+                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("nstates", ctypes.c_int32),
+                ("energy", ctypes.c_double * 8), ("steps", ctypes.c_int64 * 8), ("steps_c64", ctypes.c_int64 * 8),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -89,6 +109,15 @@ def load():
         "qfd_get_stream": (P, [P]),
         "qfd_sync": (I, [P]),
         "qfd_energy_noalloc": (I, [P, P, I64, D, D, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "qfd_plan_bytes": (ctypes.c_size_t, [ctypes.POINTER(QfdParams)]),
+        "qfd_server_create": (I, [ctypes.POINTER(ServerParams), ctypes.POINTER(P)]),
+        "qfd_server_destroy": (None, [P]),
+        "qfd_server_last_error": (ctypes.c_char_p, [P]),
+        "qfd_server_clock": (D, [P]),
+        "qfd_server_submit": (I, [P, ctypes.POINTER(Request), ctypes.POINTER(I64)]),
+        "qfd_server_poll": (I, [P, ctypes.POINTER(Result), I, ctypes.POINTER(I)]),
+        "qfd_server_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64),
+                                 ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -275,3 +304,99 @@ class Plan:
 
     def sync(self):
         self._check(self.lib.qfd_sync(self.h))
+
+
+def make_request(n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision="c128", potential="ho",
+                 pot_coeffs=(1.0, 0.0), centre="grid", parity=None, seed=1, max_steps=100000, tol=1e-9,
+                 tol_bulk=1e-10):
+    """A qfd_request structure from keyword arguments."""
+    r = Request(n=n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=rest_mass, nstates=nstates,
+                precision=PRECISION[precision], potential=POTENTIAL[potential], centre=CENTRE[centre], seed=seed,
+                max_steps=max_steps, tol=tol, tol_bulk=tol_bulk)
+    r.pot_coeffs[0], r.pot_coeffs[1] = (list(pot_coeffs) + [0.0, 0.0])[:2]
+    for i, v in enumerate(parity or [0] * nstates):
+        r.parity[i] = v
+    return r
+
+
+class Server:
+    """Continuous-batching request server of the C ABI (qfd_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, *, max_active=0, check_every=100, ortho_every=10, use_graphs=True,
+                 stream=None):
+        self.lib = load()
+        prm = ServerParams(hbm_budget_bytes=float(hbm_budget_bytes), max_active=max_active, check_every=check_every,
+                           ortho_every=ortho_every, use_graphs=int(use_graphs), stream=stream)
+        h = ctypes.c_void_p()
+        st = self.lib.qfd_server_create(ctypes.byref(prm), ctypes.byref(h))
+        if st != OK:
+            raise QfdError(st, "qfd_server_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qfd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def clock(self):
+        return self.lib.qfd_server_clock(self.h)
+
+    def submit(self, request):
+        rid = ctypes.c_int64()
+        st = self.lib.qfd_server_submit(self.h, ctypes.byref(request), ctypes.byref(rid))
+        if st != OK:
+            raise QfdError(st, self.lib.qfd_server_last_error(self.h).decode())
+        return rid.value
+
+    def poll(self, capacity=256):
+        buf = (Result * capacity)()
+        cnt = ctypes.c_int()
+        st = self.lib.qfd_server_poll(self.h, buf, capacity, ctypes.byref(cnt))
+        if st != OK:
+            raise QfdError(st, self.lib.qfd_server_last_error(self.h).decode())
+        out = []
+        for i in range(cnt.value):
+            r = buf[i]
+            out.append({"id": r.id, "status": r.status, "nstates": r.nstates,
+                        "energy": [r.energy[k] for k in range(r.nstates)],
+                        "steps": [r.steps[k] for k in range(r.nstates)],
+                        "steps_c64": [r.steps_c64[k] for k in range(r.nstates)],
+                        "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done})
+        return out
+
+    def stats(self):
+        w, a, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        per, rep, cap = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        st = self.lib.qfd_server_stats(self.h, ctypes.byref(w), ctypes.byref(a), ctypes.byref(u), ctypes.byref(per),
+                                       ctypes.byref(rep), ctypes.byref(cap))
+        if st != OK:
+            raise QfdError(st, "qfd_server_stats failed")
+        return {"waiting": w.value, "active": a.value, "used_bytes": u.value, "periods": per.value,
+                "graph_replays": rep.value, "graph_captures": cap.value}
+
+    def run_until_done(self, n_expected, capacity=256):
+        """Polls until n_expected results have come back; returns them by id."""
+        res = {}
+        while len(res) < n_expected:
+            for r in self.poll(capacity):
+                res[r["id"]] = r
+        return res
+
+
+def plan_bytes(n, precision="c128", nstates=1):
+    """Device bytes of a plan (qfd_plan_bytes)."""
+    p = QfdParams(n=n, a=1.0, mass=1.0, dtau=1e-6, kinetic=2, nstates=nstates, precision=PRECISION[precision],
+                  ortho_every=1, check_every=1)
+    return load().qfd_plan_bytes(ctypes.byref(p))

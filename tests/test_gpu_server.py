@@ -1,0 +1,71 @@
+"""The request server (continuous batching): results are the same for a request
+alone, in a mix with other requests, and through qfd_solve_states; admission
+respects the device-memory budget; unchanged periods replay a CUDA graph."""
+import pytest
+
+from paper_2006_16935_gb300 import qfd as Q
+
+pytestmark = pytest.mark.gpu
+
+CHECK, ORTHO = 40, 10
+REQS = [
+    dict(n=16, a=0.4, mass=1.5, dtau=0.02, kinetic=3, nstates=2, precision="c128", potential="cornell",
+         pot_coeffs=(0.3, 0.2), parity=[1, -1], seed=11, tol=1e-9, max_steps=20000),
+    dict(n=32, a=0.2, mass=1.0, dtau=0.004, kinetic=2, nstates=1, precision="c64_refine_df", potential="ho",
+         pot_coeffs=(1.0, 0.0), seed=12, tol=1e-9, max_steps=20000),
+    dict(n=16, a=0.3, mass=2.0, dtau=0.01, kinetic=1, nstates=1, precision="df64", potential="softcoul",
+         pot_coeffs=(0.01, 0.0), seed=13, tol=1e-9, max_steps=20000),
+    dict(n=8, a=0.5, mass=1.0, dtau=0.05, kinetic=2, nstates=3, precision="c64_refine", potential="ho",
+         pot_coeffs=(1.0, 0.0), parity=[1, -1, 1], seed=14, tol=1e-9, max_steps=20000),
+]
+
+
+def via_solve_states(req):
+    kw = {k: v for k, v in req.items() if k not in ("potential", "pot_coeffs", "parity", "seed", "nstates")}
+    with Q.Plan(req["n"], req["a"], req["mass"], req["dtau"], req["kinetic"], nstates=req["nstates"],
+                precision=req["precision"], ortho_every=ORTHO, check_every=CHECK, max_steps=req["max_steps"],
+                tol=req["tol"], tol_bulk=1e-10) as p:
+        p.fill_potential(req["potential"], req["pot_coeffs"])
+        for s in range(req["nstates"]):
+            p.fill_psi_uniform(s, req["seed"] + s)
+        es, steps, _ = p.solve_states(req["nstates"], req.get("parity"), allow_unconverged=True)
+    del kw
+    return es, steps
+
+
+def run_server(reqs, budget=64e9, use_graphs=True, max_active=0):
+    with Q.Server(budget, check_every=CHECK, ortho_every=ORTHO, use_graphs=use_graphs, max_active=max_active) as sv:
+        ids = [sv.submit(Q.make_request(**r)) for r in reqs]
+        res = sv.run_until_done(len(ids))
+        return [res[i] for i in ids], sv.stats()
+
+
+def test_results_same_alone_in_mix_and_through_solve_states(qfdlib):
+    mix, stats = run_server(REQS)
+    assert stats["graph_replays"] > 0 and stats["graph_captures"] > 0
+    for req, got in zip(REQS, mix):
+        assert got["status"] == 0
+        alone, _ = run_server([req])
+        es, steps = via_solve_states(req)
+        assert got["energy"] == alone[0]["energy"] == es
+        assert got["steps"] == alone[0]["steps"] == steps
+
+
+def test_graph_replay_matches_direct_launches(qfdlib):
+    a, _ = run_server(REQS[:2], use_graphs=True)
+    b, _ = run_server(REQS[:2], use_graphs=False)
+    assert [r["energy"] for r in a] == [r["energy"] for r in b]
+
+
+def test_admission_respects_the_memory_budget(qfdlib):
+    budget = 1.5 * max(Q.plan_bytes(r["n"], r["precision"], r["nstates"]) for r in REQS)
+    with Q.Server(budget, check_every=CHECK, ortho_every=ORTHO) as sv:
+        ids = [sv.submit(Q.make_request(**r)) for r in REQS]
+        got = {}
+        while len(got) < len(ids):
+            st = sv.stats()
+            assert st["used_bytes"] <= budget
+            for r in sv.poll():
+                got[r["id"]] = r
+        assert all(got[i]["status"] == 0 for i in ids)
+        assert all(got[i]["t_admit"] >= got[i]["t_submit"] for i in ids)
