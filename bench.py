@@ -381,6 +381,9 @@ def run_qfd(args):
         else:
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
                                     "sample": "skipped: less than 24 GB host memory available"}
+    if args.serve > 0:
+        line["serve"] = serve_section(torch, Q, dev, args.serve, [int(x) for x in args.serve_sizes.split(",")],
+                                      args.serve_precisions.split(","))
     if args.solve:
         c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
             others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
@@ -425,6 +428,67 @@ def full_solves(torch, Q, dev, which, ms_step_c128=None):
     return out
 
 
+def serve_section(torch, Q, dev, count, sizes, precisions):
+    """A bounded sample of the serving workload: the first `count` requests of
+    the seeded Poisson stream (mean 20 req/s; n from `sizes`, weighted 0.4 /
+    0.3 / 0.2 / 0.1 toward small lattices; random kinetic term, mass U[1,5],
+    1-3 states, Cornell potential, |dE| <= 1e-9 |E| under the tail stop rule),
+    offered in real time to a server with a 150 GB admission budget, once per
+    arithmetic.  Latency runs from a request's arrival to its result."""
+    from paper_2006_16935_gb300 import serve as S
+
+    w = dict(zip(S.SIZES, S.WEIGHTS))
+    stream = S.poisson_stream(count, sizes=sizes, weights=[w[n] for n in sizes])
+    out = {"requests": count, "arrivals": "Poisson, mean 20 req/s (seed 5)", "sizes": list(sizes),
+           "spacing_a": stream[0][1]["a"], "tol": 1e-9, "stop_rule": "tail", "budget_gb": 150,
+           "check_every": 100, "ortho_every": 10, "arms": {}}
+    energies = {}
+    for prec in precisions:
+        torch.cuda.synchronize(dev)
+        recs, st = S.serve(stream, prec)
+        summ = S.summarize(recs)
+        summ.update({"graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"],
+                     "periods": st["periods"]})
+        out["arms"][prec] = summ
+        energies[prec] = [r["energy"] for r in recs]
+    ref = next((p for p in ("c128", "df64") if p in energies), None)
+    if ref:
+        for prec, es in energies.items():
+            if prec == ref:
+                continue
+            d = max(abs(x - y) / abs(y) for ea, eb in zip(es, energies[ref]) for x, y in zip(ea, eb))
+            out["arms"][prec]["max_rel_energy_diff_vs_" + ref] = d
+            out["arms"][prec]["solves_per_s_ratio_vs_" + ref] = \
+                out["arms"][prec]["solves_per_s"] / out["arms"][ref]["solves_per_s"]
+    return out
+
+
+def run_serve_only(args):
+    import torch
+
+    from paper_2006_16935_gb300 import build
+    from paper_2006_16935_gb300 import qfd as Q
+
+    rank, local, world = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build_library()
+    clocks = ClockSampler(local)
+    clocks.start()
+    sec = serve_section(torch, Q, dev, args.serve, [int(x) for x in args.serve_sizes.split(",")],
+                        args.serve_precisions.split(","))
+    clk = clocks.stop()
+    if rank == 0:
+        first = sec["arms"][args.serve_precisions.split(",")[0]]
+        line = {"metric": "serve: solves/s (p50/p99 latency beside it)", "value": first["solves_per_s"],
+                "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.serve_precisions.split(",")[0], "data": "synthetic",
+                "config": {"workload": "serving sample of the Poisson request stream"}, "serve": sec,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,11 +499,17 @@ def main():
     ap.add_argument("--solve", default="", help="comma list of precisions for full 1e-9 solves "
                     "(e.g. c64_refine_df,c64_refine,df64; minutes each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", type=int, default=12, help="requests of the serving sample (0: none)")
+    ap.add_argument("--serve-sizes", default="64,128,256")
+    ap.add_argument("--serve-precisions", default="c64_refine_df,df64")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving sample")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_only:
+        return run_serve_only(args)
     return run_qfd(args)
 
 

@@ -83,6 +83,20 @@ enum { QFD_CENTRE_GRID = 0, QFD_CENTRE_OFFGRID = 1 };
  *  SOFTCOUL  V = -1 / sqrt(r^2 + c0)               (softened Coulomb) */
 enum { QFD_POT_ZERO = 0, QFD_POT_HO = 1, QFD_POT_CORNELL = 2, QFD_POT_COULOMB = 3, QFD_POT_SOFTCOUL = 4 };
 
+/* Stop rules, applied after every energy check (every check_every steps) with
+ * D_k = E_k - E_(k-1):
+ *  PAPER  |D_k| <= tol |E_k|  (TOLERANCE of Sec. 5.1).
+ *  TAIL   PAPER, and the change still to come is bounded as well: either
+ *         |D_k| <= 1e-3 tol |E_k|, or D_k, D_(k-1), D_(k-2) share one sign, the
+ *         ratio r = D_k / D_(k-1) is below 1 and not below 0.9 D_(k-1)/D_(k-2),
+ *         and the geometric tail |D_k| r / (1 - r) <= tol |E_k|.  The update
+ *         of Sec. 2.2 is not a symmetric operator, so the energy can fall
+ *         below its limit and creep back: PAPER then stops near the turn, up to
+ *         tens of tol away from the limit; TAIL does not.  Not in the paper.
+ * A complex64 bulk phase always uses PAPER with tol_bulk and additionally
+ * stops once its energy rises after the third check. */
+enum { QFD_STOP_PAPER = 0, QFD_STOP_TAIL = 1 };
+
 typedef struct {
   int64_t n;            /* lattice points per axis (NUM) */
   double a;             /* lattice spacing A (> 0) */
@@ -95,7 +109,7 @@ typedef struct {
   int32_t ortho_every;  /* steps between parity / Gram-Schmidt / normalisation (>= 1) */
   int32_t check_every;  /* steps between energy checks in qfd_solve_states (>= 1) */
   int32_t centre;       /* QFD_CENTRE_* */
-  int32_t reserved;     /* must be 0 */
+  int32_t stop_rule;    /* QFD_STOP_PAPER or QFD_STOP_TAIL (the final phase's stop rule) */
   int64_t max_steps;    /* per state (per phase for QFD_C64_REFINE) */
   double tol;           /* relative energy tolerance of the final phase (< 0: run max_steps) */
   double tol_bulk;      /* relative energy tolerance of the complex64 bulk phase */
@@ -235,12 +249,14 @@ size_t qfd_plan_bytes(const qfd_params* params);
  * paper has a single solve per run).  Requests wait in FIFO order and are
  * admitted while the device bytes of the admitted requests (qfd_plan_bytes)
  * stay within hbm_budget_bytes; each admitted request owns a plan on its own
- * stream, so requests overlap on the device.  qfd_server_poll admits what
- * fits, advances every active request by one period (check_every steps and
- * an energy check, exactly as qfd_solve_states does), applies each request's
- * stop rule and moves it to its next phase or state, and returns the results
- * of the requests that finished.  While the set of active requests and their
- * phases do not change, the period is captured once as a CUDA graph and
+ * stream (priority rising as the lattice shrinks), so requests overlap on the
+ * device and each advances at its own pace.  qfd_server_poll admits what
+ * fits, queues one period (check_every steps and an energy check, exactly as
+ * qfd_solve_states runs them) for every admitted request with none queued,
+ * blocks until at least one queued period has ended, applies the stop rule of
+ * each request whose period ended, moves it to its next phase or state, and
+ * returns the results of the requests that finished.  From the second period
+ * of a phase on, a request's period is captured once as a CUDA graph and
  * replayed.  A request's numbers are the same alone and in any mix. */
 typedef struct qfd_server_s* qfd_server_t;
 
@@ -249,8 +265,8 @@ typedef struct {
   int32_t max_active;      /* at most this many requests at once (0: no limit) */
   int32_t check_every;     /* steps per period; a multiple of ortho_every */
   int32_t ortho_every;     /* projection / normalisation cadence of every request */
-  int32_t use_graphs;      /* 1: capture and replay a period of an unchanged set */
-  void* stream;            /* cudaStream_t the periods fork from, or NULL */
+  int32_t use_graphs;      /* 1: capture a request's period once per phase and replay it */
+  void* stream;            /* cudaStream_t whose queued work admitted requests follow, or NULL */
 } qfd_server_params;
 
 typedef struct {
@@ -260,6 +276,7 @@ typedef struct {
   int32_t nstates;         /* 1..8 states, solved in turn with Gram-Schmidt */
   int32_t precision;       /* QFD_C128, QFD_C64, QFD_DF64, QFD_C64_REFINE, QFD_C64_REFINE_DF */
   int32_t potential;       /* QFD_POT_* with coefficients pot_coeffs[0..1] */
+  int32_t stop_rule;       /* QFD_STOP_* */
   double pot_coeffs[2];
   int32_t centre;
   int32_t parity[8];       /* per state */
@@ -283,7 +300,8 @@ void qfd_server_destroy(qfd_server_t server);
 const char* qfd_server_last_error(qfd_server_t server);
 double qfd_server_clock(qfd_server_t server);
 qfd_status qfd_server_submit(qfd_server_t server, const qfd_request* request, int64_t* id);
-/* One scheduling round; up to `capacity` finished results are written to out. */
+/* One scheduling round (see above); up to `capacity` finished results are
+ * written to out, the rest stay for the next call. */
 qfd_status qfd_server_poll(qfd_server_t server, qfd_result* out, int capacity, int* count);
 qfd_status qfd_server_stats(qfd_server_t server, int* waiting, int* active, double* used_bytes, int64_t* periods,
                             int64_t* graph_replays, int64_t* graph_captures);

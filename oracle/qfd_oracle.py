@@ -358,33 +358,63 @@ class StateResult:
     history: list
 
 
-def solve_state(psi0, prob: Problem, max_steps: int, tol: float, parity: int = 0, lower=()):
+def stop_check(energies, tol: float, rule: str = "paper") -> bool:
+    """Stop rule after the latest energy check (energies: every check so far).
+
+    "paper": TOLERANCE of Sec. 5.1, d_k = |E_k - E_(k-1)| <= tol |E_k|.
+    "tail": the same, and besides the change still to come is bounded.  The
+    update operator is not symmetric, so its fixed point is not an eigenvector
+    of H and the energy error is linear in the slowest remaining modes: it can
+    fall below the limit and turn back, and a component of one sign can hide
+    behind a faster one of the other.  So stop only when d_k <= 1e-3 tol |E_k|,
+    or when the last three differences share one sign, their ratio
+    r = D_k / D_(k-1) has not fallen (r >= 0.9 D_(k-1) / D_(k-2), i.e. one mode
+    dominates) and the geometric tail d_k r / (1 - r) <= tol |E_k|."""
+    if tol < 0 or len(energies) < 2:
+        return False
+    e = energies[-1]
+    dk = e - energies[-2]
+    if abs(dk) > tol * abs(e):
+        return False
+    if rule == "paper" or abs(dk) <= 1e-3 * tol * abs(e):
+        return True
+    if len(energies) < 4:
+        return False
+    d1 = energies[-2] - energies[-3]
+    d2 = energies[-3] - energies[-4]
+    if not (dk * d1 > 0 and d1 * d2 > 0):
+        return False
+    r, r_prev = dk / d1, d1 / d2
+    return r < 1.0 and r >= 0.9 * r_prev and abs(dk) * r / (1.0 - r) <= tol * abs(e)
+
+
+def solve_state(psi0, prob: Problem, max_steps: int, tol: float, parity: int = 0, lower=(), rule: str = "paper"):
     """One state: cadence at t = 0, then steps; every check_every steps the energy
-    is taken and the loop stops once |E_t - E_prev| <= tol |E_t| (tol < 0: never)."""
+    is taken and the loop stops once stop_check says so (tol < 0: never)."""
     psi = cadence(psi0.astype(np.complex128), prob, parity, lower)
     t = 0
-    e_prev = None
+    energies = []
     hist = []
     converged = False
     while t < max_steps:
         psi, t = evolve(psi, prob, prob.check_every, t, parity, lower)
         e = energy(psi, prob.V, prob.T, prob.method)
         hist.append((t, e))
-        if tol >= 0 and e_prev is not None and abs(e - e_prev) <= tol * abs(e):
+        energies.append(e)
+        if stop_check(energies, tol, rule):
             converged = True
             break
-        e_prev = e
     return StateResult(e, normalize(psi), t, converged, hist)
 
 
-def solve_states(psi0s, prob: Problem, max_steps: int, tol: float, parities=None):
+def solve_states(psi0s, prob: Problem, max_steps: int, tol: float, parities=None, rule: str = "paper"):
     """Ground and excited states in turn; state i is Gram-Schmidt deflated
     against the converged states 0..i-1 (each normalised)."""
     out = []
     lower = []
     for i, p0 in enumerate(psi0s):
         par = 0 if parities is None else parities[i]
-        res = solve_state(p0, prob, max_steps, tol, par, tuple(lower))
+        res = solve_state(p0, prob, max_steps, tol, par, tuple(lower), rule)
         out.append(res)
         lower.append(res.psi)
     return out

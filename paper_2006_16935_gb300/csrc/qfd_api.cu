@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "qfd.h"
@@ -598,11 +599,17 @@ qfd_status finish_phase(qfd_plan_t pl, int s) {
 }
 
 // The stop rule applied after every period (TOLERANCE of Sec. 5.1): done when
-// |E - E_prev| <= tol |E| from the second check on; a complex64 bulk phase also
-// stops once its energy rises between checks after the third one (FP32 noise
-// floor).  Returns QFD_ERR_DIVERGED for a non-finite energy or norm.
+// |E - E_prev| <= tol |E| from the second check on; under QFD_STOP_TAIL a final
+// phase also needs a change below 1e-3 tol |E|, or three changes of one sign
+// whose ratio r has not fallen and whose geometric tail d r / (1 - r) is within
+// tol |E| (the update is not symmetric: the energy can undershoot its limit and
+// turn back, so neither a small change nor a single ratio suffices).  A complex64
+// bulk phase also stops once its energy rises between checks after the third
+// one (FP32 noise floor).  Returns QFD_ERR_DIVERGED for a non-finite energy or
+// norm.
 struct PhaseTracker {
   double e_prev = NAN;
+  double d1 = 0.0, d2 = 0.0;  // the last two signed changes E_k - E_(k-1)
   int checks = 0;
 };
 qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, bool bulk, PhaseTracker& tr,
@@ -618,8 +625,21 @@ qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, boo
     return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
   pl->hist[s].push_back({pl->t[s], e});
   ++tr.checks;
-  *done = (tol >= 0 && tr.checks > 1 && std::fabs(e - tr.e_prev) <= tol * std::fabs(e)) ||
-          (bulk && tr.checks > 3 && e > tr.e_prev);
+  const double dk = tr.checks > 1 ? e - tr.e_prev : INFINITY;
+  const double ae = std::fabs(e);
+  bool stop = tol >= 0 && std::fabs(dk) <= tol * ae;
+  if (stop && !bulk && pl->p.stop_rule == QFD_STOP_TAIL && std::fabs(dk) > 1e-3 * tol * ae) {
+    // one sign over the last three changes, a ratio that has not fallen, and a
+    // geometric tail within tolerance
+    stop = false;
+    if (tr.checks > 3 && dk * tr.d1 > 0 && tr.d1 * tr.d2 > 0) {
+      const double r = dk / tr.d1, r_prev = tr.d1 / tr.d2;
+      stop = r < 1.0 && r >= 0.9 * r_prev && std::fabs(dk) * r / (1.0 - r) <= tol * ae;
+    }
+  }
+  *done = stop || (bulk && tr.checks > 3 && e > tr.e_prev);
+  tr.d2 = tr.d1;
+  tr.d1 = dk;
   tr.e_prev = e;
   *e_out = e;
   return QFD_OK;
@@ -721,7 +741,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   }
   if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 1 || p.kinetic > 3 || p.nstates < 1 ||
       p.nstates > MAX_LOWER || p.precision < 0 || p.precision > QFD_C64_REFINE_DF || p.ortho_every < 1 ||
-      p.check_every < 1 || (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || p.reserved != 0 ||
+      p.check_every < 1 || (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || (p.stop_rule != QFD_STOP_PAPER && p.stop_rule != QFD_STOP_TAIL) ||
       p.max_steps < 0 || (p.rest_mass != 0 && p.rest_mass != 1)) {
     g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 1..3; nstates 1..8; precision 0..4; cadences >= 1)";
     return QFD_ERR_ARG;
@@ -1162,23 +1182,29 @@ static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 144 && sizeof(q
                   sizeof(qfd_server_params) == 32,
               "C ABI struct layouts are fixed (the Python binding mirrors them)");
 // Continuous batching of solve requests: requests wait in FIFO order and are
-// admitted while their device bytes fit the budget; every admitted request
-// owns a plan with its own stream, so the requests' kernels overlap on the
-// device.  qfd_server_poll advances every active request by one period
-// (check_every steps and an energy check) - forked from the server stream to
-// the request streams and joined back - then applies each request's stop rule
-// and moves it to its next phase, state or completion.  While the active set
-// and every request's phase stay the same, the period is captured once as a
-// CUDA graph and replayed.
+// admitted while their device bytes fit the budget.  Every admitted request
+// owns a plan on its own stream, whose priority rises as the lattice shrinks
+// (short solves are not held behind the blocks of long ones), and advances by
+// periods (check_every steps and an energy check) independently of the
+// others: qfd_server_poll issues a period for every request that has none in
+// flight, waits until at least one period has ended, and applies the stop rule
+// of each ended request, moving it to its next phase, state or completion.
+// From its second period in a phase on, a request's period is captured once as
+// a CUDA graph on its stream and replayed.
 struct ReqRun {
   int64_t id = 0;
   qfd_request req{};
   qfd_plan_t plan = nullptr;
+  cudaStream_t st = nullptr;        // the request's stream (owned by the server)
+  cudaEvent_t ev = nullptr;         // end of the period in flight
+  cudaGraphExec_t exec = nullptr;   // captured period of (gstate, gphase)
+  int gstate = -1, gphase = -1;
   size_t bytes = 0;
   int state = 0;
-  int phase = 0;      // policy id of the running phase
-  bool bulk = false;  // complex64 bulk of a mixed request
-  bool fresh = true;  // its first period in this phase is still to run
+  int phase = 0;          // policy id of the running phase
+  bool bulk = false;      // complex64 bulk of a mixed request
+  bool fresh = true;      // its first period in this phase is still to run
+  bool inflight = false;  // a period is queued on st
   PhaseTracker tr;
   qfd_result res{};
 };
@@ -1193,12 +1219,8 @@ struct qfd_server_s {
   std::vector<qfd_result> done;
   size_t used = 0;
   int64_t next_id = 1;
-  double* hbuf = nullptr;  // pinned, (SC_COUNT + 1) doubles per active request
-  size_t hcap = 0;
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> joins;
-  cudaGraphExec_t exec = nullptr;
-  std::vector<int64_t> gsig;  // (id, state, phase) of the captured period
+  cudaEvent_t fork = nullptr;  // admitted requests start after the server stream's work
+  int prio_least = 0, prio_greatest = 0;
   int64_t periods = 0, replays = 0, captures = 0;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
@@ -1227,11 +1249,29 @@ qfd_params request_params(const qfd_server_t sv, const qfd_request& r) {
   p.ortho_every = sv->p.ortho_every;
   p.check_every = sv->p.check_every;
   p.centre = r.centre;
+  p.stop_rule = r.stop_rule;
   p.max_steps = r.max_steps;
   p.tol = r.tol;
   p.tol_bulk = r.tol_bulk;
   p.stream = nullptr;
   return p;
+}
+
+// Stream priority of a request: the highest for n <= 64, one level lower per
+// doubling of n, clamped to the device's range.
+int request_priority(const qfd_server_t sv, int64_t n) {
+  int lvl = 0;
+  for (int64_t m = n; m > 64; m >>= 1) ++lvl;
+  return std::min(sv->prio_greatest + lvl, sv->prio_least);
+}
+
+void release_request(ReqRun* m) {
+  if (m->st) cudaStreamSynchronize(m->st);
+  if (m->plan) qfd_destroy(m->plan);
+  if (m->exec) cudaGraphExecDestroy(m->exec);
+  if (m->ev) cudaEventDestroy(m->ev);
+  if (m->st) cudaStreamDestroy(m->st);
+  delete m;
 }
 
 // Starts state `s` of a request: the complex64 bulk for mixed requests, else
@@ -1258,23 +1298,43 @@ qfd_status start_state(ReqRun* m, int s) {
   return with_policy(m->phase, [&](auto pol) -> qfd_status { return begin_phase<decltype(pol)>(pl, s); });
 }
 
+void finish_request(qfd_server_t sv, ReqRun* m, qfd_status status) {
+  if (status != QFD_OK) m->res.status = status;
+  m->res.t_done = server_clock(sv);
+  m->res.nstates = m->req.nstates;
+  sv->done.push_back(m->res);
+}
+
 qfd_status admit(qfd_server_t sv) {
   while (!sv->waiting.empty()) {
     if (sv->p.max_active > 0 && (int)sv->active.size() >= sv->p.max_active) break;
     ReqRun* m = sv->waiting.front();
-    const qfd_params prm = request_params(sv, m->req);
+    qfd_params prm = request_params(sv, m->req);
     m->bytes = plan_device_bytes(prm);
     if (sv->used + m->bytes > (size_t)sv->p.hbm_budget_bytes) {
       if (!sv->active.empty()) break;  // wait for memory to free up
-      m->res.status = QFD_ERR_OOM;     // can never fit the budget
-      m->res.t_done = server_clock(sv);
-      sv->done.push_back(m->res);
-      sv->waiting.pop_front();
+      sv->waiting.pop_front();         // can never fit the budget
+      finish_request(sv, m, QFD_ERR_OOM);
       delete m;
       continue;
     }
+    if (cudaStreamCreateWithPriority(&m->st, cudaStreamNonBlocking, request_priority(sv, m->req.n)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamWaitEvent(m->st, sv->fork, 0) != cudaSuccess) {
+      sv->waiting.pop_front();
+      finish_request(sv, m, QFD_ERR_CUDA);
+      release_request(m);
+      continue;
+    }
+    prm.stream = (void*)m->st;
     qfd_status r = qfd_plan(&prm, &m->plan);
-    if (r == QFD_ERR_OOM && !sv->active.empty()) break;
+    if (r == QFD_ERR_OOM && !sv->active.empty()) {  // retry once memory frees up
+      cudaStreamDestroy(m->st);
+      cudaEventDestroy(m->ev);
+      m->st = nullptr;
+      m->ev = nullptr;
+      break;
+    }
     sv->waiting.pop_front();
     if (r == QFD_OK) {
       const double c[2] = {m->req.pot_coeffs[0], m->req.pot_coeffs[1]};
@@ -1283,11 +1343,8 @@ qfd_status admit(qfd_server_t sv) {
       if (r == QFD_OK) r = start_state(m, 0);
     }
     if (r != QFD_OK) {
-      m->res.status = r;
-      m->res.t_done = server_clock(sv);
-      sv->done.push_back(m->res);
-      qfd_destroy(m->plan);
-      delete m;
+      finish_request(sv, m, r);
+      release_request(m);
       continue;
     }
     m->res.t_admit = server_clock(sv);
@@ -1298,14 +1355,14 @@ qfd_status admit(qfd_server_t sv) {
 }
 
 // After a period: stop rule, then the next phase, state or completion.
-qfd_status advance_request(qfd_server_t sv, ReqRun* m, const double* host, bool* finished) {
+qfd_status advance_request(ReqRun* m, bool* finished) {
   qfd_plan_t pl = m->plan;
   const int s = m->state;
   *finished = false;
   m->fresh = false;
   bool done = false;
   double e = NAN;
-  qfd_status r = phase_check(pl, s, host, m->bulk ? pl->p.tol_bulk : pl->p.tol, m->bulk, m->tr, &done, &e);
+  qfd_status r = phase_check(pl, s, pl->hscal, m->bulk ? pl->p.tol_bulk : pl->p.tol, m->bulk, m->tr, &done, &e);
   if (r != QFD_OK) return r;
   if (!done && pl->t[s] < pl->p.max_steps) return QFD_OK;
   const bool converged = done;
@@ -1335,103 +1392,105 @@ qfd_status advance_request(qfd_server_t sv, ReqRun* m, const double* host, bool*
   return QFD_OK;
 }
 
-// Issues one period of every active request, forked from the server stream.
-qfd_status issue_period(qfd_server_t sv) {
-  cudaEventRecord(sv->fork, sv->st);
-  for (size_t i = 0; i < sv->active.size(); ++i) {
-    ReqRun* m = sv->active[i];
-    if (cudaStreamWaitEvent(m->plan->st, sv->fork, 0) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "fork");
-    double* slot = sv->hbuf + i * (SC_COUNT + 1);
+// Queues one period of request m on its stream: directly for the first period
+// of a phase (or without graphs), else by replaying - after capturing once -
+// the graph of the period.  The device repeats the captured period; the host
+// state advances as it did during the capture (only the step counter of the
+// state changes between periods of a phase).
+qfd_status issue_period(qfd_server_t sv, ReqRun* m) {
+  qfd_plan_t pl = m->plan;
+  auto launch = [&]() -> qfd_status {
     qfd_status r = with_policy(m->phase, [&](auto pol) -> qfd_status {
-      return period_launch<decltype(pol)>(m->plan, m->state, slot);
+      return period_launch<decltype(pol)>(pl, m->state, pl->hscal);
     });
-    if (r != QFD_OK) return sfail(sv, r, m->plan->err);
-    cudaEventRecord(sv->joins[i], m->plan->st);
-    cudaStreamWaitEvent(sv->st, sv->joins[i], 0);
-  }
-  return QFD_OK;
-}
-
-qfd_status run_period(qfd_server_t sv) {
-  const size_t na = sv->active.size();
-  if (na > sv->hcap) {
-    if (sv->exec) {
-      cudaGraphExecDestroy(sv->exec);
-      sv->exec = nullptr;
-    }
-    if (sv->hbuf) cudaFreeHost(sv->hbuf);
-    sv->hcap = std::max<size_t>(na, 2 * sv->hcap);
-    if (cudaHostAlloc((void**)&sv->hbuf, sv->hcap * (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault) !=
-        cudaSuccess) {
-      sv->hbuf = nullptr;
-      sv->hcap = 0;
-      return sfail(sv, QFD_ERR_OOM, "pinned host buffer");
-    }
-  }
-  while (sv->joins.size() < na) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "event");
-    sv->joins.push_back(e);
-  }
-  std::vector<int64_t> sig;
-  bool any_fresh = false;
-  for (ReqRun* m : sv->active) {
-    sig.push_back(m->id);
-    sig.push_back(m->state);
-    sig.push_back(m->phase);
-    any_fresh = any_fresh || m->fresh;
-  }
+    return r == QFD_OK ? r : sfail(sv, r, pl->err);
+  };
   qfd_status r = QFD_OK;
-  if (!sv->p.use_graphs || any_fresh) {
-    r = issue_period(sv);
-  } else if (sv->exec && sig == sv->gsig) {
-    // replay: the device repeats the captured period; the host state advances as
-    // it did during the capture (only the step counters change between periods)
-    if (cudaGraphLaunch(sv->exec, sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
-    for (ReqRun* m : sv->active) m->plan->t[m->state] += m->plan->p.check_every;
+  if (!sv->p.use_graphs || m->fresh) {
+    r = launch();
+  } else if (m->exec && m->gstate == m->state && m->gphase == m->phase) {
+    if (cudaGraphLaunch(m->exec, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    pl->t[m->state] += pl->p.check_every;
     ++sv->replays;
   } else {
-    if (sv->exec) {
-      cudaGraphExecDestroy(sv->exec);
-      sv->exec = nullptr;
+    if (m->exec) {
+      cudaGraphExecDestroy(m->exec);
+      m->exec = nullptr;
     }
-    if (cudaStreamBeginCapture(sv->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    if (cudaStreamBeginCapture(m->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return sfail(sv, QFD_ERR_CUDA, "begin capture");
-    r = issue_period(sv);
+    r = launch();
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(sv->st, &g);
+    const cudaError_t ce = cudaStreamEndCapture(m->st, &g);
     if (r != QFD_OK) {
       if (g) cudaGraphDestroy(g);
       return r;
     }
     if (ce != cudaSuccess || !g) return sfail(sv, QFD_ERR_CUDA, "end capture");
-    const cudaError_t ie = cudaGraphInstantiate(&sv->exec, g, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&m->exec, g, 0);
     cudaGraphDestroy(g);
-    if (ie != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph instantiate");
-    sv->gsig = sig;
-    if (cudaGraphLaunch(sv->exec, sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    if (ie != cudaSuccess) {
+      m->exec = nullptr;
+      return sfail(sv, QFD_ERR_CUDA, "graph instantiate");
+    }
+    m->gstate = m->state;
+    m->gphase = m->phase;
+    if (cudaGraphLaunch(m->exec, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
     ++sv->captures;
   }
   if (r != QFD_OK) return r;
-  if (cudaStreamSynchronize(sv->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "period synchronise");
+  if (cudaEventRecord(m->ev, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "event record");
+  m->inflight = true;
   ++sv->periods;
+  return QFD_OK;
+}
+
+// Issues a period for every active request without one in flight, waits until
+// at least one period has ended, and retires the requests whose periods ended.
+qfd_status run_periods(qfd_server_t sv) {
   std::vector<ReqRun*> keep;
-  for (size_t i = 0; i < na; ++i) {
+  std::vector<char> ended(sv->active.size(), 0);
+  bool any_ended = false;
+  for (size_t i = 0; i < sv->active.size(); ++i) {
     ReqRun* m = sv->active[i];
-    bool finished = false;
-    qfd_status q = advance_request(sv, m, sv->hbuf + i * (SC_COUNT + 1), &finished);
-    if (q != QFD_OK) {
-      m->res.status = q;
-      finished = true;
-      cudaStreamSynchronize(m->plan->st);
+    if (m->inflight) continue;
+    const qfd_status r = issue_period(sv, m);
+    if (r != QFD_OK) {  // the request ends with the error; the others go on
+      m->res.status = r;
+      ended[i] = 2;
+      any_ended = true;
+    }
+  }
+  while (!any_ended) {
+    bool waiting_any = false;
+    for (size_t i = 0; i < sv->active.size(); ++i) {
+      ReqRun* m = sv->active[i];
+      if (!m->inflight) continue;
+      waiting_any = true;
+      const cudaError_t q = cudaEventQuery(m->ev);
+      if (q == cudaSuccess) {
+        m->inflight = false;
+        ended[i] = 1;
+        any_ended = true;
+      } else if (q != cudaErrorNotReady) {
+        return sfail(sv, QFD_ERR_CUDA, cudaGetErrorString(q));
+      }
+    }
+    if (!waiting_any || any_ended) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  for (size_t i = 0; i < sv->active.size(); ++i) {
+    ReqRun* m = sv->active[i];
+    bool finished = ended[i] == 2;
+    qfd_status q = finished ? (qfd_status)m->res.status : QFD_OK;
+    if (ended[i] == 1) {
+      q = advance_request(m, &finished);
+      if (q != QFD_OK) finished = true;
     }
     if (finished) {
-      m->res.t_done = server_clock(sv);
-      m->res.nstates = m->req.nstates;
-      sv->done.push_back(m->res);
+      finish_request(sv, m, q);
       sv->used -= m->bytes;
-      qfd_destroy(m->plan);
-      delete m;
+      release_request(m);
     } else {
       keep.push_back(m);
     }
@@ -1461,7 +1520,8 @@ qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out)
   } else {
     sv->own_stream = true;
   }
-  if (cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&sv->prio_least, &sv->prio_greatest) != cudaSuccess) {
     qfd_server_destroy(sv);
     return QFD_ERR_CUDA;
   }
@@ -1472,15 +1532,9 @@ qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out)
 void qfd_server_destroy(qfd_server_t sv) {
   if (!sv) return;
   if (sv->st) cudaStreamSynchronize(sv->st);
-  for (ReqRun* m : sv->active) {
-    qfd_destroy(m->plan);
-    delete m;
-  }
+  for (ReqRun* m : sv->active) release_request(m);
   for (ReqRun* m : sv->waiting) delete m;
-  if (sv->exec) cudaGraphExecDestroy(sv->exec);
-  for (auto e : sv->joins) cudaEventDestroy(e);
   if (sv->fork) cudaEventDestroy(sv->fork);
-  if (sv->hbuf) cudaFreeHost(sv->hbuf);
   if (sv->own_stream && sv->st) cudaStreamDestroy(sv->st);
   delete sv;
 }
@@ -1510,8 +1564,10 @@ qfd_status qfd_server_submit(qfd_server_t sv, const qfd_request* req, int64_t* i
 
 qfd_status qfd_server_poll(qfd_server_t sv, qfd_result* out, int capacity, int* count) {
   if (!sv || capacity < 0 || (capacity > 0 && !out)) return QFD_ERR_ARG;
+  if (!sv->waiting.empty() && cudaEventRecord(sv->fork, sv->st) != cudaSuccess)
+    return sfail(sv, QFD_ERR_CUDA, "fork event");
   qfd_status r = admit(sv);
-  if (r == QFD_OK && !sv->active.empty()) r = run_period(sv);
+  if (r == QFD_OK && !sv->active.empty()) r = run_periods(sv);
   const int n = (int)std::min<size_t>(sv->done.size(), (size_t)capacity);
   for (int i = 0; i < n; ++i) out[i] = sv->done[i];
   sv->done.erase(sv->done.begin(), sv->done.begin() + n);

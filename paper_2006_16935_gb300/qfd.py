@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "QFD_OK", -1: "QFD_ERR_ARG", -2: "QFD_ERR_OOM", -3: "QFD_ERR_
 PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2, "df64": 3, "c64_refine_df": 4}
 CENTRE = {"grid": 0, "offgrid": 1}
 POTENTIAL = {"zero": 0, "ho": 1, "cornell": 2, "coulomb": 3, "softcoul": 4}
+STOP_RULE = {"paper": 0, "tail": 1}
 PASS_KINDS = {"update_x": 0, "fwd_y": 1, "z_kinetic": 2, "inv_y": 3, "fwd_x": 4,
               "gs_dots": 5, "project_x": 6, "reduce": 7, "other": 8}
 
@@ -41,7 +42,7 @@ class QfdParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("a", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dtau", ctypes.c_double), ("kinetic", ctypes.c_int32), ("rest_mass", ctypes.c_int32),
                 ("nstates", ctypes.c_int32), ("precision", ctypes.c_int32), ("ortho_every", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("centre", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("centre", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
@@ -55,7 +56,8 @@ class ServerParams(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("a", ctypes.c_double), ("mass", ctypes.c_double), ("dtau", ctypes.c_double),
                 ("kinetic", ctypes.c_int32), ("rest_mass", ctypes.c_int32), ("nstates", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("potential", ctypes.c_int32), ("pot_coeffs", ctypes.c_double * 2),
+                ("precision", ctypes.c_int32), ("potential", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
+                ("pot_coeffs", ctypes.c_double * 2),
                 ("centre", ctypes.c_int32), ("parity", ctypes.c_int32 * 8), ("seed", ctypes.c_uint64),
                 ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double)]
 
@@ -162,12 +164,13 @@ class Plan:
 
     def __init__(self, n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision="c128",
                  ortho_every=10, check_every=100, centre="grid", max_steps=100000, tol=1e-9,
-                 tol_bulk=1e-6, stream=None):
+                 tol_bulk=1e-6, stop_rule="paper", stream=None):
         self.lib = load()
         self.n = int(n)
         p = QfdParams(n=self.n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=rest_mass,
                       nstates=nstates, precision=PRECISION[precision], ortho_every=ortho_every,
-                      check_every=check_every, centre=CENTRE[centre], reserved=0, max_steps=max_steps,
+                      check_every=check_every, centre=CENTRE[centre], stop_rule=STOP_RULE[stop_rule],
+                      max_steps=max_steps,
                       tol=tol, tol_bulk=tol_bulk, stream=stream)
         self.params = p
         h = ctypes.c_void_p()
@@ -308,10 +311,11 @@ class Plan:
 
 def make_request(n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision="c128", potential="ho",
                  pot_coeffs=(1.0, 0.0), centre="grid", parity=None, seed=1, max_steps=100000, tol=1e-9,
-                 tol_bulk=1e-10):
+                 tol_bulk=1e-10, stop_rule="paper"):
     """A qfd_request structure from keyword arguments."""
     r = Request(n=n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=rest_mass, nstates=nstates,
-                precision=PRECISION[precision], potential=POTENTIAL[potential], centre=CENTRE[centre], seed=seed,
+                precision=PRECISION[precision], potential=POTENTIAL[potential], stop_rule=STOP_RULE[stop_rule],
+                centre=CENTRE[centre], seed=seed,
                 max_steps=max_steps, tol=tol, tol_bulk=tol_bulk)
     r.pot_coeffs[0], r.pot_coeffs[1] = (list(pot_coeffs) + [0.0, 0.0])[:2]
     for i, v in enumerate(parity or [0] * nstates):

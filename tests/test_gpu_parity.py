@@ -219,6 +219,34 @@ def test_solve_states_excited_with_parity(qfdlib, prec):
     assert es[0] < es[1] and es[0] < es[2]
 
 
+@pytest.mark.parametrize("prec", FP64_CLASS + ["c64_refine_df"])
+def test_tail_stop_rule_matches_oracle_and_reaches_the_limit(qfdlib, prec):
+    # the states of the excited-state case under the tail stop rule: same checks as
+    # the oracle's rule (FP64 class), and every energy within tol of its limit
+    n, a, m, kin = 16, 0.4, 1.5, 3
+    dt = stable_dt(n, a, m, kin, 0.5)
+    par, tol = [1, -1, 1], 1e-9
+    with Q.Plan(n, a, m, dt, kin, nstates=3, ortho_every=10, check_every=50, max_steps=40000, tol=tol,
+                tol_bulk=1e-10, stop_rule="tail", precision=prec) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        for s in range(3):
+            p.fill_psi_uniform(s, 100 + s)
+        es, steps, conv = p.solve_states(3, par)
+    assert conv
+    V = O.potential(n, a, "cornell", (0.3, 0.2))
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=10, check_every=50)
+    psi0 = [inputs.uniform_psi(n, 100 + s) for s in range(3)]
+    limit = O.solve_states(psi0, prob, 60000, 1e-14, par)
+    if prec != "c64_refine_df":
+        res = O.solve_states(psi0, prob, 40000, tol, par, rule="tail")
+        paper = O.solve_states(psi0, prob, 40000, tol, par)
+        for s in range(3):
+            assert steps[s] == res[s].steps >= paper[s].steps
+            assert abs(es[s] - res[s].energy) <= TOL_E * abs(res[s].energy)
+    for s in range(3):
+        assert abs(es[s] - limit[s].energy) <= 2 * tol * abs(limit[s].energy)
+
+
 # ------------------------------------------------------------- complex64 ----
 
 @pytest.mark.parametrize("kin", [1, 2, 3])

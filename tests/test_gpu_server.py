@@ -69,3 +69,19 @@ def test_admission_respects_the_memory_budget(qfdlib):
                 got[r["id"]] = r
         assert all(got[i]["status"] == 0 for i in ids)
         assert all(got[i]["t_admit"] >= got[i]["t_submit"] for i in ids)
+
+
+def test_short_requests_overtake_a_long_one(qfdlib):
+    """Requests advance independently: short solves queued behind a long one are
+    admitted at once (budget permitting) and finish first."""
+    long_req = dict(n=64, a=0.1, mass=1.0, dtau=0.001, kinetic=1, nstates=1, precision="c128", potential="ho",
+                    pot_coeffs=(1.0, 0.0), seed=21, tol=-1.0, max_steps=4000)
+    with Q.Server(64e9, check_every=CHECK, ortho_every=ORTHO) as sv:
+        lid = sv.submit(Q.make_request(**long_req))
+        sids = [sv.submit(Q.make_request(**r)) for r in REQS[2:]]
+        res = sv.run_until_done(1 + len(sids))
+    assert res[lid]["status"] == 0 and res[lid]["steps"] == [4000]
+    for i in sids:
+        assert res[i]["status"] == 0
+        assert res[i]["t_admit"] < res[lid]["t_done"]
+        assert res[i]["t_done"] < res[lid]["t_done"]

@@ -25,7 +25,7 @@ def test_library_exports_every_header_function(lib):
 
 def _params(**kw):
     base = dict(n=32, a=0.1, mass=1.0, dtau=0.001, kinetic=1, rest_mass=0, nstates=1, precision=0,
-                ortho_every=100, check_every=100, centre=0, reserved=0, max_steps=2000, tol=-1.0,
+                ortho_every=100, check_every=100, centre=0, stop_rule=0, max_steps=2000, tol=-1.0,
                 tol_bulk=1e-6, stream=None)
     base.update(kw)
     return qfd.QfdParams(**base)
@@ -42,7 +42,7 @@ def _plan_status(lib, **kw):
 @pytest.mark.parametrize("bad", [dict(n=48), dict(n=2048), dict(a=0.0), dict(mass=-1.0), dict(dtau=0.0),
                                  dict(kinetic=0), dict(kinetic=4), dict(nstates=0), dict(nstates=9),
                                  dict(precision=5), dict(ortho_every=0), dict(check_every=0), dict(centre=2),
-                                 dict(reserved=1), dict(rest_mass=2), dict(max_steps=-1)])
+                                 dict(stop_rule=2), dict(rest_mass=2), dict(max_steps=-1)])
 def test_plan_rejects_bad_arguments(lib, bad):
     st, msg = _plan_status(lib, **bad)
     assert st == qfd.ERR_ARG and msg
@@ -79,3 +79,12 @@ def test_uniform_psi_is_seeded_and_in_range():
     # chunked generation is identical to one-shot generation
     d = inputs.uniform_psi(8, 3, chunk=7)
     assert np.array_equal(a, d)
+
+
+def test_binding_struct_sizes_match_the_header():
+    import ctypes
+
+    assert ctypes.sizeof(qfd.QfdParams) == 96
+    assert ctypes.sizeof(qfd.Request) == 144 and qfd.Request.pot_coeffs.offset == 56
+    assert ctypes.sizeof(qfd.Result) == 232
+    assert ctypes.sizeof(qfd.ServerParams) == 32

@@ -394,6 +394,68 @@ def test_solve_state_stop_rule_and_step_count():
     assert res2.steps == 60 and not res2.converged
 
 
+def test_tail_stop_rule_bounds_the_remaining_error_of_geometric_convergence():
+    """E_k = E* + c q^k (slow q): the paper's rule stops while the error is still
+    far above tol; the tail rule stops only once |E_k - E*| <= tol |E_k|, and at
+    the first such check after the consecutive difference also fell below tol."""
+    e_star, c, tol = 0.6, 0.5, 1e-9
+    for q in (0.3, 0.9, 0.99):
+        seq = [e_star + c * q ** k for k in range(20000)]
+        stops = {}
+        for rule in ("paper", "tail"):
+            k = 2
+            while not O.stop_check(seq[:k], tol, rule):
+                k += 1
+            stops[rule] = k - 1
+        kt, kp = stops["tail"], stops["paper"]
+        err = lambda k: abs(seq[k] - e_star) / abs(seq[k])
+        # the ratio comes from differences of rounded energies: a few per cent of slack
+        assert err(kt) <= 1.05 * tol
+        # and it stops no later than needed: within two checks of the first one
+        # where both the error and the consecutive difference are below tol
+        k_exact = next(k for k in range(1, len(seq))
+                       if err(k) <= tol and abs(seq[k] - seq[k - 1]) <= tol * abs(seq[k]))
+        assert abs(kt - k_exact) <= 2
+        if q >= 0.99:
+            assert err(kp) > 10 * tol and kt > kp
+    # (closer to q = 1 the ratio of differences of rounded energies loses its
+    # digits: at q = 0.999 and d ~ 1e-12 it is good to a few tenths of 1 - q)
+
+
+def test_tail_stop_rule_on_a_turning_approach():
+    """E_k = E* + c1 q1^k - c2 q2^k with q1 < q2: the energy falls below the limit,
+    turns and creeps back up (as the non-symmetric update does).  The paper's
+    rule stops near the turn, far from E*; the tail rule ends within tol."""
+    e_star, tol = 0.6, 1e-9
+    for c1, q1, c2, q2 in ((1.0, 0.4, 3e-7, 0.9), (0.5, 0.3, 1e-7, 0.92), (1.0, 0.5, 5e-7, 0.88)):
+        seq = [e_star + c1 * q1 ** k - c2 * q2 ** k for k in range(3000)]
+        stops = {}
+        for rule in ("paper", "tail"):
+            k = 2
+            while not O.stop_check(seq[:k], tol, rule):
+                k += 1
+            stops[rule] = k - 1
+        err = lambda k: abs(seq[k] - e_star) / abs(e_star)
+        assert err(stops["paper"]) > 3 * tol
+        assert err(stops["tail"]) <= 1.05 * tol
+
+
+def test_tail_stop_rule_noise_floor_and_flat_sequences():
+    tol = 1e-9
+    # changes far below tolerance (the arithmetic's noise floor), of either sign: stop
+    assert O.stop_check([1.0, 0.5, 0.5 + 1e-13], tol, "tail")
+    assert O.stop_check([1.0, 0.5, 0.5 - 1e-13], tol, "tail")
+    assert O.stop_check([1.0, 0.5, 0.5], tol, "tail")
+    # a large rise is not convergence
+    assert not O.stop_check([1.0, 0.5, 0.6], tol, "tail")
+    # a turn below tolerance is not convergence either
+    assert not O.stop_check([0.5 + 3e-9, 0.5 + 1e-9, 0.5, 0.5 + 3e-10], tol, "tail")
+    # three checks give one ratio only: not yet
+    assert not O.stop_check([0.5 + 1e-9, 0.5 + 1e-10, 0.5 + 1e-11], tol, "tail")
+    assert O.stop_check([0.5 + 1e-10, 0.5], tol, "paper")
+    assert not O.stop_check([1.0, 0.5], -1.0, "paper")
+
+
 def test_solve_states_orders_energies_and_orthogonalises():
     n, a, m, dt = 6, 0.5, 1.0, 0.05
     V = aniso_ho(n, a)
