@@ -210,6 +210,16 @@ qfd_status qfd_get_stats(qfd_plan_t plan, int state, int64_t* steps_c64, int64_t
  * `capacity` entries into steps[] and E[] and sets *count to the total. */
 qfd_status qfd_get_history(qfd_plan_t plan, int state, int64_t* steps, double* E, int capacity, int* count);
 
+/* The decay-rate energy estimator at the last check of `state` in a solve:
+ * (1 - lambda) / dtau, with lambda the per-step norm ratio over the k steps
+ * since the last normalisation (k = ortho_every at a cadence step), from the
+ * squared norm N2 after those steps and the cadence's projections:
+ * lambda = N2^(1/(2k)).  The state decays as exp(-E tau) under Eq.
+ * (iter_proced), so at the fixed point this is the eigenvalue of the update
+ * (Sec. 2.2), next to the Rayleigh energy of qfd_energy.  NaN before the
+ * first check. */
+qfd_status qfd_get_decay(qfd_plan_t plan, int state, double* e_decay);
+
 /* Kernel timing: when enabled, every kernel launch of the plan is bracketed
  * by CUDA events on the plan's stream.  qfd_timing_query synchronises and
  * returns, for the pass kind (0 update-x, 1 forward-y, 2 z kinetic,

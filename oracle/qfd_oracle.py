@@ -329,23 +329,46 @@ class Problem:
             self.T = kinetic_symbol(self.n, self.a, self.mass, self.kinterm, self.rest_mass)
 
 
-def cadence(psi, prob: Problem, parity: int, lower):
-    """Parity projection, then Gram-Schmidt against the lower states, then normalisation."""
+def cadence_n2(psi, prob: Problem, parity: int, lower):
+    """Parity projection, then Gram-Schmidt against the lower states, then
+    normalisation.  Returns (normalised psi, squared norm before normalising)."""
     psi = parity_project(psi, parity, prob.centre)
     if lower:
         psi = gram_schmidt(psi, lower)
-    return normalize(psi)
+    n2 = norm2(psi)
+    return psi / np.sqrt(n2), n2
+
+
+def cadence(psi, prob: Problem, parity: int, lower):
+    """Parity projection, then Gram-Schmidt against the lower states, then normalisation."""
+    return cadence_n2(psi, prob, parity, lower)[0]
+
+
+def decay_energy(n2: float, k: int, dtau: float) -> float:
+    """The decay-rate energy estimator (1 - lambda) / dtau, with lambda the
+    per-step norm ratio ||psi_(t+1)|| / ||psi_t|| (Sec. 2.2: the state decays
+    as exp(-E tau)); n2 is the squared norm after k steps (and the cadence's
+    projections) from a normalised state, so lambda = n2^(1/(2k))."""
+    return (1.0 - n2 ** (0.5 / k)) / dtau
+
+
+def evolve_n2(psi, prob: Problem, nsteps: int, t0: int = 0, parity: int = 0, lower=()):
+    """evolve, also returning the squared norm before the last cadence's
+    normalisation (None when no cadence ran)."""
+    t = t0
+    n2 = None
+    for _ in range(nsteps):
+        psi = imaginary_time_step(psi, prob.V, prob.T, prob.dtau, prob.method)
+        t += 1
+        if t % prob.ortho_every == 0:
+            psi, n2 = cadence_n2(psi, prob, parity, lower)
+    return psi, t, n2
 
 
 def evolve(psi, prob: Problem, nsteps: int, t0: int = 0, parity: int = 0, lower=()):
     """Advance nsteps steps of Eq. (iter_proced) from step counter t0; after each
     step t with t % ortho_every == 0 apply the cadence.  Returns (psi, t)."""
-    t = t0
-    for _ in range(nsteps):
-        psi = imaginary_time_step(psi, prob.V, prob.T, prob.dtau, prob.method)
-        t += 1
-        if t % prob.ortho_every == 0:
-            psi = cadence(psi, prob, parity, lower)
+    psi, t, _ = evolve_n2(psi, prob, nsteps, t0, parity, lower)
     return psi, t
 
 
@@ -356,6 +379,7 @@ class StateResult:
     steps: int
     converged: bool
     history: list
+    e_decay: float = float("nan")  # decay-rate energy at the last check
 
 
 def stop_check(energies, tol: float, rule: str = "paper") -> bool:
@@ -396,15 +420,18 @@ def solve_state(psi0, prob: Problem, max_steps: int, tol: float, parity: int = 0
     energies = []
     hist = []
     converged = False
+    e_decay = float("nan")
     while t < max_steps:
-        psi, t = evolve(psi, prob, prob.check_every, t, parity, lower)
+        psi, t, n2 = evolve_n2(psi, prob, prob.check_every, t, parity, lower)
         e = energy(psi, prob.V, prob.T, prob.method)
+        if n2 is not None and t % prob.ortho_every == 0:
+            e_decay = decay_energy(n2, prob.ortho_every, prob.dtau)
         hist.append((t, e))
         energies.append(e)
         if stop_check(energies, tol, rule):
             converged = True
             break
-    return StateResult(e, normalize(psi), t, converged, hist)
+    return StateResult(e, normalize(psi), t, converged, hist, e_decay)
 
 
 def solve_states(psi0s, prob: Problem, max_steps: int, tol: float, parities=None, rule: str = "paper"):

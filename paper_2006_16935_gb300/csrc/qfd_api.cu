@@ -237,6 +237,7 @@ struct qfd_plan_s {
   std::vector<int> parity;
   std::vector<int64_t> steps16, steps32;
   std::vector<double> ebulk;
+  std::vector<double> edecay;  // decay-rate energy at the last check
   // energy at every check of the last solve, per state: (phase-local step, E)
   std::vector<std::vector<std::pair<int64_t, double>>> hist;
   int w_state = -1, w_stage = ST_NONE, w_phase = -1;
@@ -624,6 +625,10 @@ qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, boo
   if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
     return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
   pl->hist[s].push_back({pl->t[s], e});
+  {  // decay-rate energy over the steps since the last normalisation
+    const int64_t K = pl->p.ortho_every, k = pl->t[s] % K == 0 ? K : pl->t[s] % K;
+    pl->edecay[s] = -std::expm1(std::log(n2) * (0.5 / (double)k)) / pl->p.dtau;
+  }
   ++tr.checks;
   const double dk = tr.checks > 1 ? e - tr.e_prev : INFINITY;
   const double ae = std::fabs(e);
@@ -795,6 +800,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->steps16.assign(p.nstates, 0);
   pl->steps32.assign(p.nstates, 0);
   pl->ebulk.assign(p.nstates, NAN);
+  pl->edecay.assign(p.nstates, NAN);
   pl->hist.assign(p.nstates, {});
   pl->arith16 = (p.precision == QFD_DF64 || p.precision == QFD_C64_REFINE_DF) ? 2 : 0;
   pl->phase = uses32(p.precision) ? 1 : pl->arith16;
@@ -1119,6 +1125,14 @@ qfd_status qfd_get_stats(qfd_plan_t pl, int s, int64_t* steps_c64, int64_t* step
   if (steps_c64) *steps_c64 = pl->steps32[s];
   if (steps_c128) *steps_c128 = pl->steps16[s];
   if (e_bulk) *e_bulk = pl->ebulk[s];
+  return QFD_OK;
+}
+
+qfd_status qfd_get_decay(qfd_plan_t pl, int s, double* e_decay) {
+  qfd_status r = check_state(pl, s);
+  if (r != QFD_OK) return r;
+  if (!e_decay) return fail(pl, QFD_ERR_ARG, "null argument");
+  *e_decay = pl->edecay[s];
   return QFD_OK;
 }
 

@@ -104,6 +104,7 @@ def load():
         "qfd_set_limits": (I, [P, I64, D, D]),
         "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
+        "qfd_get_decay": (I, [P, I, ctypes.POINTER(D)]),
         "qfd_timing_enable": (I, [P, I]),
         "qfd_timing_reset": (I, [P]),
         "qfd_timing_query": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D)]),
@@ -279,6 +280,12 @@ class Plan:
         es = (ctypes.c_double * max(1, n))()
         self._check(self.lib.qfd_get_history(self.h, state, st, es, n, ctypes.byref(cnt)))
         return [(st[i], es[i]) for i in range(n)]
+
+    def decay_energy(self, state):
+        """(1 - lambda) / dtau at the last check of `state` (qfd_get_decay)."""
+        e = ctypes.c_double()
+        self._check(self.lib.qfd_get_decay(self.h, state, ctypes.byref(e)))
+        return e.value
 
     def stats(self, state):
         s64, s128, eb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()

@@ -186,12 +186,14 @@ def test_solve_parity_oscillator_32(qfdlib, kin, dt, prec):
         p.fill_psi_uniform(0, 1)
         es, steps, _ = p.solve_states(1)
         psi = p.get_psi(0)
+        e_decay = p.decay_energy(0)
     V = O.potential(n, a, "ho", (1.0,))
     prob = O.Problem(n, a, m, dt, kin, V, ortho_every=100, check_every=100)
     res = O.solve_state(inputs.uniform_psi(n, 1), prob, 2000, -1)
     assert steps[0] == res.steps == 2000
     assert abs(es[0] - res.energy) <= TOL_E * abs(res.energy)
     assert rel_l2(psi, res.psi) < TOL_PSI
+    assert abs(e_decay - res.e_decay) <= TOL_E * abs(res.e_decay)
 
 
 @pytest.mark.parametrize("prec", FP64_CLASS)
@@ -207,6 +209,7 @@ def test_solve_states_excited_with_parity(qfdlib, prec):
             p.fill_psi_uniform(s, 100 + s)
         es, steps, conv = p.solve_states(3, par)
         psis = [p.get_psi(s) for s in range(3)]
+        decays = [p.decay_energy(s) for s in range(3)]
     assert conv
     V = O.potential(n, a, "cornell", (0.3, 0.2))
     prob = O.Problem(n, a, m, dt, kin, V, ortho_every=10, check_every=50)
@@ -214,6 +217,8 @@ def test_solve_states_excited_with_parity(qfdlib, prec):
     for s in range(3):
         assert steps[s] == res[s].steps
         assert abs(es[s] - res[s].energy) <= TOL_E * abs(res[s].energy)
+        # decay-rate energy after the projections of the excited states
+        assert abs(decays[s] - res[s].e_decay) <= 1e-8 * abs(res[s].e_decay)
         assert rel_l2(psis[s], res[s].psi) < 1e-9
     # the even ground state lies lowest; the second even state may lie below the odd one
     assert es[0] < es[1] and es[0] < es[2]

@@ -378,6 +378,22 @@ def test_potential_values_by_hand():
 
 
 # ------------------------------------------------------------ solve loop ----
+@pytest.mark.parametrize("kin", [2, 3])
+def test_decay_energy_of_a_converged_solve_is_the_fixed_point_eigenvalue(kin):
+    # the norm decay over ortho_every steps of the converged state gives
+    # lambda^K; (1 - lambda) / dtau must then be the lowest eigenvalue of the
+    # dense H_K + ((1 + lambda) / 2) V (the fixed-point relation of Eq. (iter_proced))
+    n, a, m, dt = 6, 0.5, 1.0, 0.02
+    V = aniso_ho(n, a)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=5, check_every=20)
+    res = O.solve_state(rand_psi(n, 8), prob, max_steps=20000, tol=1e-14)
+    lam = 1.0 - dt * res.e_decay
+    w = np.linalg.eigvalsh(dense_HK(n, a, m, kin) + (1 + lam) / 2 * np.diag(V.ravel()))
+    assert res.e_decay == pytest.approx(w[0], rel=1e-10)
+    # and it differs from the Rayleigh energy by the O(dtau) iteration bias only
+    assert abs(res.e_decay - res.energy) < 0.05 * abs(res.energy)
+
+
 
 def test_solve_state_stop_rule_and_step_count():
     n, a, m, dt = 6, 0.5, 1.0, 0.05
