@@ -453,6 +453,12 @@ template <typename C, int PS, int T> struct AccLine {
 #ifndef QFD_YCOLS_MIN16
 #define QFD_YCOLS_MIN16 4
 #endif
+#ifndef QFD_ZG8
+#define QFD_ZG8 2
+#endif
+#ifndef QFD_ZG16
+#define QFD_ZG16 1
+#endif
 #ifndef QFD_YCOLS_MIN8
 #define QFD_YCOLS_MIN8 8
 #endif
@@ -487,7 +493,10 @@ template <class A, int N> struct Shape {
   static constexpr int LINES0 = (LTARGET / T) > 1 ? LTARGET / T : 1;
   static constexpr int LINES = LINES0 < N * N ? LINES0 : N * N;  // z-pass lines per CTA
   static constexpr int LINE_THREADS = T * LINES;
-  // one padding element per 128 bytes of a line keeps the exchanges conflict-free
+  // z-pass line groups per CTA (see k_zpass), when they divide the lines
+  static constexpr int ZG0 = WIDE ? QFD_ZG16 : QFD_ZG8;
+  static constexpr int ZG = (N * N / LINES) % ZG0 == 0 && N * N / LINES >= ZG0 ? ZG0 : 1;
+  // one padding element per 128 bytes of a line
   static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
   static constexpr int LPAD = N + (N >> PAD_SHIFT);
 };
@@ -568,6 +577,9 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
 // Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial when PARSEVAL),
 // inverse DFT_z.  The canonical layout is the same before and after a
 // transform, so the multiply sits in registers between the two transforms.
+// A CTA takes ZG groups of LINES consecutive lines in turn; the loads of the
+// next group are issued before the current group's transforms, so they are in
+// flight while it computes.
 template <class A, int N, bool PARSEVAL>
 __global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
 k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
@@ -578,25 +590,38 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int l = threadIdx.x / SH::T, t = threadIdx.x % SH::T;
-  const int64_t line = (int64_t)blockIdx.x * SH::LINES + l;  // = kx * N + ky
-  C* p = W + line * N;
+  const int64_t line0 = (int64_t)blockIdx.x * SH::LINES * SH::ZG + l;  // line = kx * N + ky
   C v[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = p[t + m * SH::T];
+  for (int m = 0; m < 8; ++m) v[m] = W[line0 * N + t + m * SH::T];
   static_assert(SH::T <= 32 || SH::LINES <= 15, "one named barrier per line");
   AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
-  fft_line<A, N, -1>(v, t, tw, acc);
-  const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
   double pt = 0.0;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
-    if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
-    v[m] = cscale(v[m], tk);
-  }
-  fft_line<A, N, +1>(v, t, tw, acc);
+  for (int g = 0; g < SH::ZG; ++g) {
+    const int64_t line = line0 + (int64_t)g * SH::LINES;
+    C* p = W + line * N;
+    C nx[8];
+    if (g + 1 < SH::ZG) {
 #pragma unroll
-  for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
+      for (int m = 0; m < 8; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
+    }
+    fft_line<A, N, -1>(v, t, tw, acc);
+    const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
+      if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
+      v[m] = cscale(v[m], tk);
+    }
+    fft_line<A, N, +1>(v, t, tw, acc);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
+    if (g + 1 < SH::ZG) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = nx[m];
+    }
+  }
   if constexpr (PARSEVAL) {
     double q[1] = {pt};
     block_reduce_store<1>(q, part);
@@ -788,17 +813,26 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
   // are lower states: conversions from FP64 run on the slow FP64 pipe)
   C cc[MAX_LOWER];
   if (k > 0) {
-    for (int j = 0; j < k; ++j) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
+#pragma unroll
+    for (int j = 0; j < MAX_LOWER; ++j)
+      if (j < k) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
   }
-  C v[8];
+  // every load of the state and of its reflection is issued before any use
+  C v[8], rv[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = src[base + (t + m * SH::T) * S];
+  if (parity) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) rv[m] = src[rbase + (int64_t)reflect1<N>(t + m * SH::T, offgrid) * S];
+  }
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int x = t + m * SH::T;
     const int64_t idx = base + x * S;
-    C p = src[idx];
-    if (parity) p = A::half_comb(p, src[rbase + (int64_t)reflect1<N>(x, offgrid) * S], parity);
+    C p = v[m];
+    if (parity) p = A::half_comb(p, rv[m], parity);
 #pragma unroll
     for (int j = 0; j < MAX_LOWER; ++j)
       if (j < k) p = csub(p, cmul(static_cast<const C*>(lower.p[j])[idx], cc[j]));

@@ -70,7 +70,7 @@ cudaError_t Launch<A, N>::zpass(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(C);
-  const int grid = (int)((int64_t)N * N / SH::LINES);
+  const int grid = (int)((int64_t)N * N / (SH::LINES * SH::ZG));
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<grid, SH::LINE_THREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (const typename A::T*)a.ktab, *a.kin,
