@@ -195,6 +195,24 @@ qfd_status qfd_energy(qfd_plan_t plan, int state, double* E, double* norm2);
  * max_steps, QFD_ERR_DIVERGED on a non-finite energy. */
 qfd_status qfd_solve_states(qfd_plan_t plan, int nstates, const int* parity, double* E_out, int64_t* steps_out);
 
+/* Excited states by the paper's snapshot overlaps (Sec. 2.2: the snapshots
+ * kept at every SNAPUPDATE): one evolution of state 0 from its stored initial
+ * state, with parity `parity` and the plan's tol / max_steps / stop rule,
+ * keeping normalised snapshots every snap_every steps (a positive multiple of
+ * ortho_every).  The ground state is the final state; excited state k
+ * (1 <= k < nout) is the k-th latest snapshot taken before the end, parity
+ * projected, Gram-Schmidt deflated against states 0..k-1 and normalised, in
+ * state slot k.  E_out[0..nout-1] receives the Rayleigh energies and
+ * *steps_out the evolution's steps.  nout is 1..3; the plan needs nout + 1
+ * state slots (snapshot buffers) for nout > 1 and a single-arithmetic
+ * precision (QFD_C128, QFD_C64, QFD_DF64).  QFD_ERR_STATE when fewer
+ * snapshots than excited states were taken.  How well the excited states are
+ * separated depends on the snapshot spacing against the inverse level gaps,
+ * as the paper discusses; the per-state Gram-Schmidt solve of
+ * qfd_solve_states converges each state instead. */
+qfd_status qfd_snapshot_states(qfd_plan_t plan, int nout, int parity, int64_t snap_every, double* E_out,
+                               int64_t* steps_out);
+
 /* Replaces the plan's max_steps, tol and tol_bulk (same meaning as in
  * qfd_params) for later qfd_solve_states calls. */
 qfd_status qfd_set_limits(qfd_plan_t plan, int64_t max_steps, double tol, double tol_bulk);

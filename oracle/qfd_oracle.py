@@ -16,7 +16,7 @@ Sections and equations cited below are those of the paper:
   Sec. 5.1  SNAPUPDATE (normalise + symmetrise cadence), TOLERANCE (stop rule)
   Sec. 5.3  hard-coded potentials (harmonic oscillator, Coulomb, Cornell)
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
   * energy estimator: Rayleigh quotient <psi|H_K + V|psi> / <psi|psi>
   * V_b = V, V_s = 0 (Sec. 5.1 recommends this)
   * relativistic term: rest_mass=1 keeps sqrt(p^2+M^2) as printed in Eq. (HK3);
@@ -25,7 +25,14 @@ Readings of points the paper leaves open (all listed in the design doc):
     or the paper's off-grid (N-1)/2 (reflection x -> N-1-x)
   * cadence: after every `ortho_every`-th step apply parity, then classical
     Gram-Schmidt against the lower states, then normalise; energy every
-    `check_every` steps; stop when |E_t - E_prev| <= tol * |E_t|
+    `check_every` steps; stop when |E_t - E_prev| <= tol * |E_t| (or, with the
+    optional tail rule, also when the geometric tail of the changes is within
+    tol)
+  * decay-rate energy: (1 - lambda) / dtau from the norm decay over the steps
+    since the last normalisation, after the cadence's projections
+  * snapshot-overlap excited states: snapshots after the cadence of every
+    snap_every-th step; excited estimate k = the k-th latest snapshot before
+    the end, deflated against the lower estimates
 
 Pins (tests/test_oracle_pins.py): DFT against a brute-force textbook 3D DFT,
 numpy.fft, deltas, plane waves and Parseval; H_K(2) against the periodic
@@ -35,7 +42,10 @@ waves with constant V; the converged iteration against dense eigen-solvers of
 independently assembled matrices (ground state, parity sector, Gram-Schmidt
 deflated state); the 3D oscillator levels 3/2 w and 5/2 w; the heavy-mass
 limit; parity and orthogonality invariants; the box-normalised hydrogen radii
-printed in Sec. 3.3 (observables).  No function here is unpinned.
+printed in Sec. 3.3 (observables); the tail stop rule on geometric and turning
+sequences; the decay-rate energy against the dense fixed-point eigenvalue; the
+snapshot-overlap states on a three-plane-wave evolution with known levels.
+No function here is unpinned.
 """
 from __future__ import annotations
 
@@ -432,6 +442,48 @@ def solve_state(psi0, prob: Problem, max_steps: int, tol: float, parity: int = 0
             converged = True
             break
     return StateResult(e, normalize(psi), t, converged, hist, e_decay)
+
+
+def snapshot_states(psi0, prob: Problem, max_steps: int, tol: float, snap_every: int, parity: int = 0,
+                    nout: int = 3, rule: str = "paper"):
+    """Excited states from snapshots of one evolution (Sec. 2.2).
+
+    The state is evolved as in solve_state; after the cadence of every step t
+    with t % snap_every == 0 the normalised state is kept as a snapshot.  The
+    ground-state estimate is the final state; the k-th excited estimate is the
+    k-th latest snapshot taken before the end, with the parity projection and
+    the components along the lower estimates removed, normalised."""
+    psi = cadence(psi0.astype(np.complex128), prob, parity, ())
+    t = 0
+    snaps = []  # (step, snapshot), newest first
+    energies, hist = [], []
+    converged = False
+    e = float("nan")
+    while t < max_steps:
+        for _ in range(prob.check_every):
+            psi = imaginary_time_step(psi, prob.V, prob.T, prob.dtau, prob.method)
+            t += 1
+            if t % prob.ortho_every == 0:
+                psi = cadence(psi, prob, parity, ())
+                if nout > 1 and t % snap_every == 0:
+                    snaps.insert(0, (t, psi.copy()))
+                    del snaps[nout:]
+        e = energy(psi, prob.V, prob.T, prob.method)
+        hist.append((t, e))
+        energies.append(e)
+        if stop_check(energies, tol, rule):
+            converged = True
+            break
+    states = [normalize(psi)]
+    sources = [p for (ts, p) in snaps if ts < t][:nout - 1]
+    if len(sources) < nout - 1:
+        raise ValueError("fewer snapshots than excited states")
+    out = [StateResult(e, states[0], t, converged, hist)]
+    for src in sources:
+        phi = cadence(src, prob, parity, tuple(states))
+        states.append(phi)
+        out.append(StateResult(energy(phi, prob.V, prob.T, prob.method), phi, t, converged, []))
+    return out
 
 
 def solve_states(psi0s, prob: Problem, max_steps: int, tol: float, parities=None, rule: str = "paper"):

@@ -240,6 +240,12 @@ struct qfd_plan_s {
   std::vector<double> edecay;  // decay-rate energy at the last check
   // energy at every check of the last solve, per state: (phase-local step, E)
   std::vector<std::vector<std::pair<int64_t, double>>> hist;
+  // snapshot-overlap excited states: while snap_every > 0, state slots
+  // 1..nsnap hold the latest snapshots of state 0, newest first, taken at the
+  // cadence every snap_every steps; snap_t[i] is the step of slot 1 + i
+  int64_t snap_every = 0;
+  int nsnap = 0;
+  std::vector<int64_t> snap_t;
   int w_state = -1, w_stage = ST_NONE, w_phase = -1;
   bool pending = false;
   int phase = 0;  // policy id of the current arithmetic
@@ -485,6 +491,24 @@ qfd_status cadence(qfd_plan_t pl, int s, int check) {
   return QFD_OK;
 }
 
+// Rotates the snapshot slots (the oldest buffer becomes the newest slot) and
+// copies the normalised state 0 into it.
+template <class A>
+qfd_status take_snapshot(qfd_plan_t pl) {
+  auto& sp = A::id == 1 ? pl->sp32 : pl->sp16;
+  char* oldest = sp[pl->nsnap];
+  for (int i = pl->nsnap; i > 1; --i) {
+    sp[i] = sp[i - 1];
+    pl->snap_t[i - 1] = pl->snap_t[i - 2];
+  }
+  sp[1] = oldest;
+  pl->snap_t[0] = pl->t[0];
+  QFD_RUN(PASS_OTHER, (k_scale_copy<A><<<grid_for(pl->n3), 256, 0, pl->st>>>(
+                           psi_of<A>(pl, 1), psi_of<A>(pl, 0), pl->n3, pl->pending ? pl->scal + SC_SCALE : nullptr),
+                       cudaGetLastError()));
+  return QFD_OK;
+}
+
 template <class A>
 qfd_status step_once(qfd_plan_t pl, int s, int check) {
   qfd_status r;
@@ -509,6 +533,8 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
   pl->t[s] += 1;
   if (pl->t[s] % pl->p.ortho_every == 0) {
     if ((r = cadence<A>(pl, s, check)) != QFD_OK) return r;
+    if (pl->snap_every > 0 && s == 0 && pl->t[s] % pl->snap_every == 0 && (r = take_snapshot<A>(pl)) != QFD_OK)
+      return r;
   } else if (check) {
     if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
   }
@@ -667,6 +693,50 @@ qfd_status solve_phase(qfd_plan_t pl, int s, double tol, int64_t max_steps, doub
   if ((r = finish_phase<A>(pl, s)) != QFD_OK) return r;
   *E_out = e;
   *steps = pl->t[s];
+  return QFD_OK;
+}
+
+// Snapshot-overlap excited states (Sec. 2.2): one evolution of state 0 to the
+// stop rule, snapshots every snap_every steps; the ground state is the final
+// state, excited state k the k-th latest snapshot taken before the end, parity
+// projected, Gram-Schmidt deflated against states 0..k-1 and normalised.
+template <class A>
+qfd_status snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap_every, double* E_out,
+                           int64_t* steps_out, bool* conv) {
+  const int K = nout > 1 ? nout : 0;
+  pl->nsnap = K;
+  pl->snap_t.assign(K, -1);
+  pl->snap_every = K ? snap_every : 0;
+  pl->parity[0] = parity;
+  pl->steps32[0] = pl->steps16[0] = 0;
+  pl->ebulk[0] = NAN;
+  pl->hist[0].clear();
+  double e = NAN;
+  int64_t steps = 0;
+  qfd_status r = solve_phase<A>(pl, 0, pl->p.tol, pl->p.max_steps, &e, &steps, conv);
+  pl->snap_every = 0;
+  if (r != QFD_OK) return r;
+  if (A::id == 1) pl->steps32[0] = steps;
+  else pl->steps16[0] = steps;
+  E_out[0] = e;
+  if (steps_out) *steps_out = steps;
+  // the sources, newest first: snapshots strictly before the end
+  auto& sp = A::id == 1 ? pl->sp32 : pl->sp16;
+  std::vector<char*> srcs, rest;
+  for (int i = 0; i < K; ++i)
+    ((pl->snap_t[i] >= 0 && pl->snap_t[i] < pl->t[0] && (int)srcs.size() < nout - 1) ? srcs : rest).push_back(sp[1 + i]);
+  if ((int)srcs.size() < nout - 1)
+    return fail(pl, QFD_ERR_STATE, "fewer snapshots than excited states: raise max_steps or lower snap_every");
+  for (int i = 0; i < K; ++i) sp[1 + i] = i < (int)srcs.size() ? srcs[i] : rest[i - srcs.size()];
+  for (int k = 1; k < nout; ++k) {
+    pl->parity[k] = parity;
+    pl->hist[k].clear();
+    pl->steps32[k] = pl->steps16[k] = 0;
+    double n2 = 0.0;
+    if ((r = cadence<A>(pl, k, 0)) != QFD_OK) return r;
+    if ((r = materialize<A>(pl, k)) != QFD_OK) return r;
+    if ((r = energy_full<A>(pl, k, &E_out[k], &n2)) != QFD_OK) return r;
+  }
   return QFD_OK;
 }
 
@@ -1107,6 +1177,28 @@ qfd_status qfd_solve_states(qfd_plan_t pl, int nstates, const int* parity, doubl
   }
   QFD_CK(cudaStreamSynchronize(pl->st));
   if (!all_conv) return fail(pl, QFD_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
+  return QFD_OK;
+}
+
+qfd_status qfd_snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap_every, double* E_out,
+                               int64_t* steps_out) {
+  if (!pl) return QFD_ERR_ARG;
+  if (!E_out) return fail(pl, QFD_ERR_ARG, "null argument");
+  if (nout < 1 || nout > 3 || (nout > 1 && pl->p.nstates < nout + 1))
+    return fail(pl, QFD_ERR_ARG, "nout must be 1..3 and the plan must hold nout + 1 states");
+  if (snap_every < 1 || snap_every % pl->p.ortho_every != 0)
+    return fail(pl, QFD_ERR_ARG, "snap_every must be a positive multiple of ortho_every");
+  if (parity < -1 || parity > 1) return fail(pl, QFD_ERR_ARG, "parity must be -1, 0 or 1");
+  if (refines(pl->p.precision)) return fail(pl, QFD_ERR_ARG, "snapshot states run in one arithmetic (no refinement)");
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before solving");
+  pl->phase = uses32(pl->p.precision) ? 1 : pl->arith16;
+  bool conv = false;
+  qfd_status r = with_policy(pl->phase, [&](auto pol) -> qfd_status {
+    return snapshot_states<decltype(pol)>(pl, nout, parity, snap_every, E_out, steps_out, &conv);
+  });
+  if (r != QFD_OK) return r;
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  if (pl->p.tol >= 0 && !conv) return fail(pl, QFD_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
   return QFD_OK;
 }
 

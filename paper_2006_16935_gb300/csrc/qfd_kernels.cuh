@@ -865,4 +865,13 @@ __global__ void k_scale(typename A::C* __restrict__ psi, int64_t n3, const doubl
     psi[i] = cscale(psi[i], fs);
 }
 
+// dst = src * f, f = *scale (1 when scale is null), in the policy's arithmetic.
+template <class A>
+__global__ void k_scale_copy(typename A::C* __restrict__ dst, const typename A::C* __restrict__ src, int64_t n3,
+                             const double* __restrict__ scale) {
+  const typename A::S fs = A::scalar(scale ? scale[0] : 1.0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = cscale(src[i], fs);
+}
+
 }  // namespace qfd

@@ -102,6 +102,7 @@ def load():
         "qfd_energy": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_set_limits": (I, [P, I64, D, D]),
+        "qfd_snapshot_states": (I, [P, I, I, I64, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
         "qfd_get_decay": (I, [P, I, ctypes.POINTER(D)]),
@@ -265,6 +266,16 @@ class Plan:
         ok = (OK, ERR_NOT_CONVERGED) if allow_unconverged else (OK,)
         st = self._check(self.lib.qfd_solve_states(self.h, nstates, par, es, steps), ok)
         return list(es), list(steps), st == OK
+
+    def snapshot_states(self, nout, parity=0, snap_every=None, allow_unconverged=False):
+        """Excited states from the snapshots of one evolution of state 0
+        (qfd_snapshot_states); returns (energies, steps, converged)."""
+        es = (ctypes.c_double * nout)()
+        steps = ctypes.c_int64()
+        ok = (OK, ERR_NOT_CONVERGED) if allow_unconverged else (OK,)
+        se = self.params.check_every if snap_every is None else snap_every
+        st = self._check(self.lib.qfd_snapshot_states(self.h, nout, parity, int(se), es, ctypes.byref(steps)), ok)
+        return list(es), steps.value, st == OK
 
     def set_limits(self, max_steps, tol, tol_bulk=None):
         tb = self.params.tol_bulk if tol_bulk is None else tol_bulk

@@ -472,6 +472,38 @@ def test_tail_stop_rule_noise_floor_and_flat_sequences():
     assert not O.stop_check([1.0, 0.5], -1.0, "paper")
 
 
+def test_snapshot_states_recover_plane_wave_levels():
+    """V = 0, psi0 = three plane waves: each step multiplies mode i by
+    r_i = 1 - dtau T_i (Eq. (iter_proced) with A = B = 1).  With snapshots 40
+    steps apart and the run ending at step 120, mode 1 is down to r_1^40 ~ 2.5e-2
+    relative to its weight one snapshot earlier and mode 2 is still present two
+    snapshots earlier, so the overlap procedure returns the three plane waves
+    and energies T(k_i) (Eq. HK2 on plane waves).  Snapshots taken too late
+    (spacing 80) lose the second excited state, as the paper warns."""
+    n, a, m, kin = 8, 1.0, 1.0, 2
+    V = np.zeros((n, n, n))
+    T = O.kinetic_symbol(n, a, m, kin)
+    modes = [(0, 0, 0), (1, 0, 0), (2, 0, 0)]
+    x = np.arange(n)
+    X1, X2, X3 = np.meshgrid(x, x, x, indexing="ij")
+    pws = [np.exp(2j * np.pi * (k1 * X1 + k2 * X2 + k3 * X3) / n) for (k1, k2, k3) in modes]
+    lev = [T[k] for k in modes]
+    assert lev == pytest.approx([0.0, 2 * math.sin(math.pi / 8) ** 2, 1.0], abs=1e-15)
+    prob = O.Problem(n, a, m, 0.3, kin, V, ortho_every=10, check_every=10)
+    psi0 = pws[0] + 0.7 * pws[1] + 0.4 * pws[2]
+    ovl = lambda r, i: abs(O.inner(r.psi, pws[i])) / np.sqrt(O.norm2(pws[i]))
+    res = O.snapshot_states(psi0, prob, max_steps=120, tol=-1, snap_every=40, nout=3)
+    for i in range(3):
+        assert ovl(res[i], i) == pytest.approx(1.0, abs=1e-9)
+        assert res[i].energy == pytest.approx(lev[i], abs=1e-9)
+    late = O.snapshot_states(psi0, prob, max_steps=240, tol=-1, snap_every=80, nout=3)
+    assert ovl(late[1], 1) == pytest.approx(1.0, abs=1e-12)
+    assert ovl(late[2], 2) < 0.5
+    # a run as long as one spacing leaves no snapshot before its end
+    with pytest.raises(ValueError):
+        O.snapshot_states(psi0, prob, max_steps=40, tol=-1, snap_every=40, nout=3)
+
+
 def test_solve_states_orders_energies_and_orthogonalises():
     n, a, m, dt = 6, 0.5, 1.0, 0.05
     V = aniso_ho(n, a)
