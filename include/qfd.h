@@ -55,8 +55,16 @@ typedef enum {
   QFD_ERR_STATE = -8          /* call out of order (e.g. stepping before a potential is set) */
 } qfd_status;
 
-/* Kinetic terms, numbered as the paper's KINTERM (Sec. 5.1). */
-enum { QFD_KIN_P2 = 1, QFD_KIN_SIN2 = 2, QFD_KIN_REL = 3 };
+/* Kinetic terms, numbered as the paper's KINTERM (Sec. 5.1).  QFD_KIN_FDTD is
+ * H_K(0) of Sec. 2.1, Eq. (HK0): the finite-difference Laplacian with
+ * Dirichlet boundaries (psi = 0 outside the lattice; every lattice site
+ * evolves), normalised as its momentum-space form, Eq.
+ * (HK0_momentum_space_1): H_K(0) psi = -(1/(2 M A^2)) sum over the three axes
+ * of [psi(x + e) + psi(x - e) - 2 psi(x)].  (The printed position-space form
+ * carries an extra factor 1/2.)  Its box is symmetric about the off-grid
+ * centre, so parity work with it should use QFD_CENTRE_OFFGRID.  The FFT
+ * terms use periodic boundaries. */
+enum { QFD_KIN_FDTD = 0, QFD_KIN_P2 = 1, QFD_KIN_SIN2 = 2, QFD_KIN_REL = 3 };
 /* Arithmetic of the steps (reductions end in FP64 in all of them):
  *  QFD_C128          complex128 storage, native FP64 arithmetic;
  *  QFD_C64           complex64 storage and FP32 arithmetic;

@@ -7,10 +7,11 @@ it and shares no code, table or constant generator with it.
 
 Everything is complex128 / float64 and follows the paper's notation:
 lattice of N points per axis, spacing A, mass M, time step EPS = dtau,
-kinetic term KINTERM in {1, 2, 3}.
+kinetic term KINTERM in {0, 1, 2, 3}.
 
 Sections and equations cited below are those of the paper:
-  Sec. 2.1  kinetic terms: Eq. (eigenmodes), Eqs. (HK1)-(HK3), FFT/IFFT definitions
+  Sec. 2.1  kinetic terms: Eq. (eigenmodes), Eqs. (HK1)-(HK3), FFT/IFFT definitions;
+            the finite-difference term H_K(0) with Dirichlet boundaries (Eq. HK0)
   Sec. 2.2  iterative procedure: Eq. (iter_proced) and the coefficients A, B
   Sec. 2.4  parity projection: Eq. (parity)
   Sec. 5.1  SNAPUPDATE (normalise + symmetrise cadence), TOLERANCE (stop rule)
@@ -146,13 +147,39 @@ def kinetic_symbol(n: int, a: float, mass: float, kinterm: int, rest_mass: int =
     raise ValueError(f"kinetic term {kinterm} is not an FFT kinetic term")
 
 
+class FdtdKinetic:
+    """H_K(0), the finite-difference kinetic term with Dirichlet boundaries
+    (Sec. 2.1, Eq. HK0), normalised as its momentum-space form (Eq.
+    HK0_momentum_space_1, (1/2M) sum_l (4/A^2) sin^2(k_l/2)), i.e.
+
+        H_K(0) Psi = -(1 / (2 M A^2)) sum_l [Psi(r + A e_l) + Psi(r - A e_l) - 2 Psi(r)],
+
+    with Psi = 0 outside the lattice (every lattice site evolves; the missing
+    neighbours of an edge site are zero)."""
+
+    def __init__(self, a: float, mass: float):
+        self.a, self.mass = a, mass
+
+    def __call__(self, psi: np.ndarray) -> np.ndarray:
+        p = np.pad(psi, 1)
+        lap = (p[2:, 1:-1, 1:-1] + p[:-2, 1:-1, 1:-1] + p[1:-1, 2:, 1:-1] + p[1:-1, :-2, 1:-1]
+               + p[1:-1, 1:-1, 2:] + p[1:-1, 1:-1, :-2] - 6.0 * psi)
+        return -lap / (2.0 * self.mass * self.a * self.a)
+
+
 def kinetic_max(n: int, a: float, mass: float, kinterm: int, rest_mass: int = 0) -> float:
-    """Largest eigenvalue of H_K on the lattice (max of T over the modes)."""
+    """Largest eigenvalue of H_K on the lattice (max of T over the modes); for
+    H_K(0) the bound 6 / (A^2 M) of its momentum-space form."""
+    if kinterm == 0:
+        return 6.0 / (a * a * mass)
     return float(np.max(kinetic_symbol(n, a, mass, kinterm, rest_mass)))
 
 
-def apply_kinetic(psi: np.ndarray, T: np.ndarray, method: str = "naive") -> np.ndarray:
-    """H_K Psi = (1/N^3) IFFT[T * FFT[Psi]]  (Eqs. HK1-HK3)."""
+def apply_kinetic(psi: np.ndarray, T, method: str = "naive") -> np.ndarray:
+    """H_K Psi = (1/N^3) IFFT[T * FFT[Psi]]  (Eqs. HK1-HK3); T may instead be
+    the finite-difference operator FdtdKinetic (Eq. HK0)."""
+    if callable(T):
+        return T(psi)
     n3 = psi.size
     return ifft3(T * fft3(psi, method), method) / n3
 
@@ -336,7 +363,8 @@ class Problem:
 
     def __post_init__(self):
         if self.T is None:
-            self.T = kinetic_symbol(self.n, self.a, self.mass, self.kinterm, self.rest_mass)
+            self.T = FdtdKinetic(self.a, self.mass) if self.kinterm == 0 else \
+                kinetic_symbol(self.n, self.a, self.mass, self.kinterm, self.rest_mass)
 
 
 def cadence_n2(psi, prob: Problem, parity: int, lower):

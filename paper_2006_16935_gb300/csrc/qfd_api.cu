@@ -195,6 +195,80 @@ __global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C*
     out[i] = AO::from_d2(AI::to_d2(in[i]));
 }
 
+// ------------------------------------------------ finite-difference H_K(0)
+// H_K(0) psi at site idx of the 2^lg-cube lattice with psi = 0 outside it
+// (Eq. HK0 with Dirichlet boundaries, normalised as its momentum-space form,
+// Eq. HK0_momentum_space_1): c (6 psi - the sum of the six neighbours) with
+// c = 1 / (2 M A^2).  `self` receives psi at idx.
+template <class A>
+__device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict__ psi, int64_t idx, int lg,
+                                                 typename A::S c, typename A::C& self) {
+  using C = typename A::C;
+  const int64_t n = (int64_t)1 << lg, n2 = n * n;
+  const int64_t z = idx & (n - 1), y = (idx >> lg) & (n - 1), x = idx >> (2 * lg);
+  const C zero{};
+  self = psi[idx];
+  C s = x > 0 ? psi[idx - n2] : zero;
+  s = cadd(s, x + 1 < n ? psi[idx + n2] : zero);
+  s = cadd(s, y > 0 ? psi[idx - n] : zero);
+  s = cadd(s, y + 1 < n ? psi[idx + n] : zero);
+  s = cadd(s, z > 0 ? psi[idx - 1] : zero);
+  s = cadd(s, z + 1 < n ? psi[idx + 1] : zero);
+  return cscale(csub(cscale(self, A::scalar(6.0)), s), c);
+}
+
+// One imaginary-time step of Eq. (iter_proced) with H_K(0): out = A psi -
+// B dtau H_K(0) psi (times the pending normalisation factor), partial sums per
+// STATS.  psi and out are different lattices (the stencil reads neighbours).
+template <class A, int STATS>
+__global__ void __launch_bounds__(256)
+k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__ out,
+              const typename A::K* __restrict__ coef, const double* __restrict__ V, const double* __restrict__ scale,
+              const float* __restrict__ scale_f, int lg, typename A::S c, double* __restrict__ part) {
+  using C = typename A::C;
+  const int64_t n3 = (int64_t)1 << (3 * lg);
+  const bool scaled = scale != nullptr;
+  typename A::S s{};
+  if (scaled) s = A::load_scale(scale, scale_f);
+  typename A::Acc nacc;
+  double n2 = 0.0, pv = 0.0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += (int64_t)gridDim.x * blockDim.x) {
+    C self;
+    const C hk = fdtd_hk<A>(psi, idx, lg, c, self);
+    C nw = A::update(self, hk, coef[idx]);
+    if (scaled) nw = cscale(nw, s);
+    out[idx] = nw;
+    if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
+    if constexpr (STATS == STATS_FULL) {
+      const double a2 = A::norm2_d(nw);
+      n2 += a2;
+      pv += V[idx] * a2;
+    }
+  }
+  if constexpr (STATS != STATS_NONE) {
+    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+    double q[2] = {n2, pv};
+    block_reduce_store<2>(q, part);
+  }
+}
+
+// Per-CTA partials of <psi|H_K(0)|psi> (FP64 accumulation).
+template <class A>
+__global__ void __launch_bounds__(256)
+k_fdtd_energy(const typename A::C* __restrict__ psi, int lg, typename A::S c, double* __restrict__ part) {
+  using C = typename A::C;
+  const int64_t n3 = (int64_t)1 << (3 * lg);
+  double e = 0.0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += (int64_t)gridDim.x * blockDim.x) {
+    C self;
+    const C hk = fdtd_hk<A>(psi, idx, lg, c, self);
+    const double2 u = A::to_d2(self), h = A::to_d2(hk);
+    e += u.x * h.x + u.y * h.y;
+  }
+  double q[1] = {e};
+  block_reduce_store<1>(q, part);
+}
+
 }  // namespace qfd
 
 // ================================================================== plan
@@ -232,6 +306,8 @@ struct qfd_plan_s {
   double* hscal = nullptr;  // pinned host copy of the scalars (+ the error flag)
   // host-side state
   KinParams kin{};
+  int lg = 0;           // n = 2^lg
+  double fdtd_c = 0.0;  // 1 / (2 M A^2) of H_K(0)
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
   std::vector<int64_t> t;
   std::vector<int> parity;
@@ -345,6 +421,11 @@ template <class A> typename A::C* spare_of(qfd_plan_t pl) {
 template <class A> void swap_spare(qfd_plan_t pl, int s) {
   if (A::id == 1) std::swap(pl->sp32[s], pl->spare32);
   else std::swap(pl->sp16[s], pl->spare16);
+}
+template <class A> typename A::S host_scalar(double x) {
+  if constexpr (A::id == 0) return x;
+  else if constexpr (A::id == 1) return (float)x;
+  else return host_split(x);
 }
 template <class A> const void* coef_of(qfd_plan_t pl) { return A::id == 1 ? (const void*)pl->coef32 : pl->coef16; }
 template <class A> const void* tw_of(qfd_plan_t pl) {
@@ -509,27 +590,69 @@ qfd_status take_snapshot(qfd_plan_t pl) {
   return QFD_OK;
 }
 
+// One H_K(0) step: the stencil update from the state into the spare lattice,
+// which then becomes the state (W is not used).
+template <class A>
+qfd_status fdtd_update(qfd_plan_t pl, int s, int stats) {
+  const double* scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
+  const typename A::S c = host_scalar<A>(pl->fdtd_c);
+  auto go = [&](auto kern) -> cudaError_t {
+    kern<<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), spare_of<A>(pl),
+                                        static_cast<const typename A::K*>(coef_of<A>(pl)), pl->V, scale, pl->scalf,
+                                        pl->lg, c, pl->partA);
+    return cudaGetLastError();
+  };
+  auto launch = [&]() -> cudaError_t {
+    if (stats == STATS_FULL) return go(k_fdtd_update<A, STATS_FULL>);
+    if (stats == STATS_NORM) return go(k_fdtd_update<A, STATS_NORM>);
+    return go(k_fdtd_update<A, STATS_NONE>);
+  };
+  QFD_RUN(PASS_UPDATE_X, launch());
+  swap_spare<A>(pl, s);
+  pl->nA = GS_BLOCKS;
+  pl->w_stage = ST_NONE;
+  return QFD_OK;
+}
+
+// <psi|H_K(0)|psi> of state s into the energy partials (the Parseval sum of
+// the FFT terms).
+template <class A>
+qfd_status fdtd_energy_partials(qfd_plan_t pl, int s) {
+  const typename A::S c = host_scalar<A>(pl->fdtd_c);
+  QFD_RUN(PASS_ZKIN, (k_fdtd_energy<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->lg, c, pl->partC),
+                      cudaGetLastError()));
+  pl->nC = GS_BLOCKS;
+  return QFD_OK;
+}
+
 template <class A>
 qfd_status step_once(qfd_plan_t pl, int s, int check) {
   qfd_status r;
-  if ((r = ensure_w<A>(pl, s)) != QFD_OK) return r;
-  if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) return r;
+  const bool fdtd = pl->p.kinetic == 0;
+  if (!fdtd) {
+    if ((r = ensure_w<A>(pl, s)) != QFD_OK) return r;
+    if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) return r;
+  }
   const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
   const bool proj = projects(pl, s);
   int stats = STATS_NONE;
   if (ortho_next) stats = proj ? STATS_NONE : (check ? STATS_FULL : STATS_NORM);
   else if (check) stats = STATS_FULL;
-  LaunchArgs a = base_args<A>(pl);
-  a.psi = psi_of<A>(pl, s);
-  a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
-  a.scale_f = pl->scalf;
-  a.part = pl->partA;
-  a.stats = stats;
-  int nb = 0;
-  QFD_RUN(PASS_UPDATE_X, launch_update_x<A>(a, &nb));
-  pl->nA = nb;
+  if (fdtd) {
+    if ((r = fdtd_update<A>(pl, s, stats)) != QFD_OK) return r;
+  } else {
+    LaunchArgs a = base_args<A>(pl);
+    a.psi = psi_of<A>(pl, s);
+    a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
+    a.scale_f = pl->scalf;
+    a.part = pl->partA;
+    a.stats = stats;
+    int nb = 0;
+    QFD_RUN(PASS_UPDATE_X, launch_update_x<A>(a, &nb));
+    pl->nA = nb;
+    pl->w_stage = ST_X;
+  }
   pl->pending = false;
-  pl->w_stage = ST_X;
   pl->t[s] += 1;
   if (pl->t[s] % pl->p.ortho_every == 0) {
     if ((r = cadence<A>(pl, s, check)) != QFD_OK) return r;
@@ -576,7 +699,16 @@ qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
   if ((r = pass_forward_x<A>(pl, psi_of<A>(pl, s), nullptr, false, STATS_FULL)) != QFD_OK) return r;
   mark_w<A>(pl, s, ST_X);
   if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
-  return energy_tail<A>(pl, E, n2);
+  if (pl->p.kinetic != 0) return energy_tail<A>(pl, E, n2);
+  // H_K(0): the kinetic expectation by the stencil instead of Parseval
+  if ((r = fdtd_energy_partials<A>(pl, s)) != QFD_OK) return r;
+  if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
+  double h[SC_COUNT];
+  QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
+  if ((r = check_kernel_errors(pl)) != QFD_OK) return r;
+  if (E) *E = h[SC_E];
+  if (n2) *n2 = h[SC_N2];
+  return QFD_OK;
 }
 
 // One state in one arithmetic is a phase: begin_phase (counter reset and the
@@ -607,8 +739,12 @@ qfd_status period_launch(qfd_plan_t pl, int s, double* host) {
   const int ce = pl->p.check_every;
   for (int j = 0; j < ce; ++j)
     if ((r = step_once<A>(pl, s, j == ce - 1)) != QFD_OK) return r;
-  if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
-  if ((r = advance_to_d<A>(pl, 1)) != QFD_OK) return r;
+  if (pl->p.kinetic == 0) {
+    if ((r = fdtd_energy_partials<A>(pl, s)) != QFD_OK) return r;
+  } else {
+    if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
+    if ((r = advance_to_d<A>(pl, 1)) != QFD_OK) return r;
+  }
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   QFD_CK(cudaMemcpyAsync(host, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, pl->st));
   QFD_CK(cudaMemcpyAsync(host + SC_COUNT, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
@@ -814,11 +950,11 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
     g_create_error = "n must be one of 8, 16, 32, 64, 128, 256, 512, 1024";
     return QFD_ERR_ARG;
   }
-  if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 1 || p.kinetic > 3 || p.nstates < 1 ||
+  if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 0 || p.kinetic > 3 || p.nstates < 1 ||
       p.nstates > MAX_LOWER || p.precision < 0 || p.precision > QFD_C64_REFINE_DF || p.ortho_every < 1 ||
       p.check_every < 1 || (p.centre != QFD_CENTRE_GRID && p.centre != QFD_CENTRE_OFFGRID) || (p.stop_rule != QFD_STOP_PAPER && p.stop_rule != QFD_STOP_TAIL) ||
       p.max_steps < 0 || (p.rest_mass != 0 && p.rest_mass != 1)) {
-    g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 1..3; nstates 1..8; precision 0..4; cadences >= 1)";
+    g_create_error = "invalid parameter (a, mass, dtau > 0; kinetic 0..3; nstates 1..8; precision 0..4; cadences >= 1)";
     return QFD_ERR_ARG;
   }
   const int64_t n = p.n;
@@ -865,6 +1001,8 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->p = p;
   pl->n3 = n * n * n;
   pl->kin = kin;
+  while (((int64_t)1 << pl->lg) < n) ++pl->lg;
+  pl->fdtd_c = 1.0 / (2.0 * p.mass * p.a * p.a);
   pl->t.assign(p.nstates, 0);
   pl->parity.assign(p.nstates, 0);
   pl->steps16.assign(p.nstates, 0);

@@ -40,7 +40,7 @@ def _plan_status(lib, **kw):
 
 
 @pytest.mark.parametrize("bad", [dict(n=48), dict(n=2048), dict(a=0.0), dict(mass=-1.0), dict(dtau=0.0),
-                                 dict(kinetic=0), dict(kinetic=4), dict(nstates=0), dict(nstates=9),
+                                 dict(kinetic=-1), dict(kinetic=4), dict(nstates=0), dict(nstates=9),
                                  dict(precision=5), dict(ortho_every=0), dict(check_every=0), dict(centre=2),
                                  dict(stop_rule=2), dict(rest_mass=2), dict(max_steps=-1)])
 def test_plan_rejects_bad_arguments(lib, bad):

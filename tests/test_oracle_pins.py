@@ -184,6 +184,9 @@ def kron3(m1):
 
 def dense_HK(n, a, m, kin, rest_mass=0):
     """Dense H_K assembled without the oracle's DFT code."""
+    if kin == 0:  # Dirichlet second difference: no wrap-around entries
+        d1 = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+        return kron3(d1) / (2 * m * a * a)
     l1 = 2 * np.eye(n) - np.roll(np.eye(n), 1, 0) - np.roll(np.eye(n), -1, 0)
     h2 = kron3(l1) / (2 * m * a * a)
     if kin == 2:
@@ -220,7 +223,7 @@ def converge(psi, prob, parity=0, lower=(), tol=1e-13, max_steps=20000):
     raise AssertionError("oracle iteration did not converge")
 
 
-@pytest.mark.parametrize("kin", [1, 2, 3])
+@pytest.mark.parametrize("kin", [0, 1, 2, 3])
 def test_fixed_point_matches_dense_eigensolver(kin):
     # (1 - lam) / dtau is the lowest eigenvalue of H_K + ((1 + lam) / 2) V and
     # psi its eigenvector (derived from Eq. (iter_proced) with the A, B of Sec. 2.2)
@@ -375,6 +378,28 @@ def test_potential_values_by_hand():
     assert O.potential(n, a, "ho")[5, 4, 3] == pytest.approx(0.5 * 0.02)
     # off-grid centre 3.5: site (0,0,0) has displacement -3.5 per axis
     assert O.potential(n, a, "ho", centre="offgrid")[0, 0, 0] == pytest.approx(0.5 * 3 * 0.35 ** 2)
+
+
+def test_fdtd_kinetic_on_dirichlet_sine_modes():
+    """H_K(0) (Eq. HK0, Dirichlet) has the sine modes prod_l sin(pi j_l (x_l + 1) / (N + 1))
+    as eigenvectors, with eigenvalue the momentum-space form of Eq.
+    (HK0_momentum_space_1), (1/2M) sum_l (4/A^2) sin^2(k_l/2), at k_l = pi j_l / (N + 1)
+    (the momentum form fixes the normalisation; the printed position-space
+    form carries an extra factor 1/2)."""
+    n, a, m = 7, 0.3, 1.7
+    x = np.arange(n)
+    op = O.FdtdKinetic(a, m)
+    for j in [(1, 1, 1), (2, 1, 3), (7, 5, 1), (4, 4, 4)]:
+        modes = [np.sin(np.pi * jl * (x + 1) / (n + 1)) for jl in j]
+        psi = np.einsum("i,j,k->ijk", *modes).astype(np.complex128)
+        k = [np.pi * jl / (n + 1) for jl in j]
+        lam = sum(4 / (a * a) * math.sin(kl / 2) ** 2 for kl in k) / (2 * m)
+        assert np.max(np.abs(op(psi) - lam * psi)) < 1e-12 * lam
+    # on any state it is the dense Dirichlet Laplacian assembled by hand
+    psi = rand_psi(n, 12)
+    assert np.max(np.abs(op(psi).ravel() - dense_HK(n, a, m, 0) @ psi.ravel())) < 1e-12
+    # and the bound used for the stability check holds
+    assert np.linalg.eigvalsh(dense_HK(n, a, m, 0)).max() < O.kinetic_max(n, a, m, 0)
 
 
 # ------------------------------------------------------------ solve loop ----
