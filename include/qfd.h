@@ -148,6 +148,19 @@ qfd_status qfd_set_potential(qfd_plan_t plan, const double* V, int on_device);
  * qfd_set_potential does. */
 qfd_status qfd_fill_potential(qfd_plan_t plan, int kind, const double* coeffs, int ncoeffs);
 
+/* Adds a smooth Gaussian random field to the plan's potential (the seeded
+ * stand-in for the paper's file-based potentials, Sec. 5.3): white noise
+ * (per site the two counter-mode uniforms u0, u1 of qfd_fill_psi_uniform's
+ * generator under `seed`, through Box-Muller: sqrt(-2 ln(1 - u0)) cos(2 pi u1)),
+ * filtered by exp(-k^2 corr^2 / 2) (corr in lattice units, at most 21; done
+ * as three periodic real-space Gaussian convolutions, which differ from the
+ * momentum-space filter by aliasing of order exp(-pi^2 corr^2 / 2), below
+ * 1e-16 for corr >= 2.8), then shifted and scaled
+ * to mean 0 and standard deviation `amplitude` over the lattice, and added to
+ * V; the update coefficients are derived again.  Uses the work lattice as
+ * scratch.  Needs a potential set first. */
+qfd_status qfd_add_random_field(qfd_plan_t plan, uint64_t seed, double corr, double amplitude);
+
 /* Copies the potential V the plan holds (N^3 doubles) into the caller's buffer. */
 qfd_status qfd_get_potential(qfd_plan_t plan, double* V, int on_device);
 
@@ -171,8 +184,11 @@ qfd_status qfd_get_psi(qfd_plan_t plan, int state, double* out, int on_device);
  * box-normalised average radius <rho>_box of Eq. (box_normalization);
  * out[3] <rho^2>, out[4..6] <x>, <y>, <z> over the full lattice (the UPDATE
  * observables of Sec. 5.1); out[7], out[8] the box-normalised weights of the
- * parity projections P+ and P- (Sec. 2.4, they sum to 1).  The first nout
- * (<= 9) values are written; 0 <= min_sep_edge < 1. */
+ * parity projections P+ and P- (Sec. 2.4, they sum to 1); out[9..11] those of
+ * the axis projections P-_{e_k}, k = 1, 2, 3, of Eq. (parity_axis) (odd under
+ * the reflection of axis k, even under that of the two others; normalised as
+ * projectors, 1/4 of the bracket).  The first nout (<= 12) values are
+ * written; 0 <= min_sep_edge < 1. */
 qfd_status qfd_observables(qfd_plan_t plan, int state, double min_sep_edge, double* out, int nout);
 
 /* Parity sector applied to `state` at every cadence (QFD_PAR_*). */
@@ -319,6 +335,9 @@ typedef struct {
   uint64_t seed;           /* state i starts from qfd_fill_psi_uniform(seed + i) */
   int64_t max_steps;       /* per state and phase */
   double tol, tol_bulk;
+  double grf_amplitude;    /* > 0: add qfd_add_random_field(grf_seed, grf_corr, grf_amplitude) */
+  double grf_corr;
+  uint64_t grf_seed;
 } qfd_request;
 
 typedef struct {

@@ -221,6 +221,25 @@ def reflect(psi: np.ndarray, centre: str = "grid") -> np.ndarray:
     return psi[np.ix_(idx, idx, idx)]
 
 
+def reflect_axes(psi: np.ndarray, axes, centre: str = "grid") -> np.ndarray:
+    """Psi with the coordinates of `axes` (a subset of 0, 1, 2) reflected about
+    the centre, the others kept."""
+    n = psi.shape[0]
+    flip = (n - np.arange(n)) % n if centre == "grid" else n - 1 - np.arange(n)
+    keep = np.arange(n)
+    ix = [flip if k in axes else keep for k in range(3)]
+    return psi[np.ix_(*ix)]
+
+
+def axis_parity_minus(psi: np.ndarray, k: int, centre: str = "grid") -> np.ndarray:
+    """P-_{e_k} of Eq. (parity_axis) (read with the missing comma restored),
+    normalised as a projector: (1/4) [psi(x) + psi with the two other axes
+    reflected - psi with axis k reflected - psi(-x)] (the printed 1/2 makes the
+    operator twice a projector)."""
+    others = tuple(j for j in range(3) if j != k)
+    return 0.25 * (psi + reflect_axes(psi, others, centre) - reflect_axes(psi, (k,), centre) - reflect(psi, centre))
+
+
 def parity_project(psi, parity: int, centre: str = "grid"):
     """Eq. (parity): P+- Psi(r) = (Psi(r) +- Psi(-r)) / 2; parity 0 leaves Psi alone."""
     if parity == 0:
@@ -318,7 +337,7 @@ def observables(psi, centre: str = "grid", min_sep_edge: float = 0.3) -> dict:
     |d_l| <= (1 - min_sep_edge) N / 2 on every axis; <rho>_box = sum over the box
     of rho |psi|^2 / sum over the box of |psi|^2 (Eq. (box_normalization));
     parity weights (Sec. 2.4): sum over the box of |P+- psi|^2, box-normalised,
-    so that w+ + w- = 1;
+    so that w+ + w- = 1, and of |P-_{e_k} psi|^2 for the three axes;
     UPDATE observables (Sec. 5.1): <x>, <y>, <z>, <rho^2> over the full lattice.
     """
     n = psi.shape[0]
@@ -333,12 +352,28 @@ def observables(psi, centre: str = "grid", min_sep_edge: float = 0.3) -> dict:
     refl = reflect(psi, centre)
     wp = (np.abs(0.5 * (psi + refl)) ** 2)[box].sum() / n_box
     wm = (np.abs(0.5 * (psi - refl)) ** 2)[box].sum() / n_box
+    wax = [(np.abs(axis_parity_minus(psi, k, centre)) ** 2)[box].sum() / n_box for k in range(3)]
     return {"norm2": float(n_full), "norm2_box": float(n_box),
             "rho_box": float((rho * p2)[box].sum() / n_box),
             "rho2": float((rho * rho * p2).sum() / n_full),
             "x": float((d1 * p2).sum() / n_full), "y": float((d2 * p2).sum() / n_full),
             "z": float((d3 * p2).sum() / n_full),
-            "w_plus": float(wp), "w_minus": float(wm)}
+            "w_plus": float(wp), "w_minus": float(wm),
+            "w_axis1": float(wax[0]), "w_axis2": float(wax[1]), "w_axis3": float(wax[2])}
+
+
+def random_field(noise: np.ndarray, corr: float, amplitude: float) -> np.ndarray:
+    """Smooth Gaussian random field from white noise (the seeded stand-in for
+    the paper's file-based potentials): multiply the noise by
+    exp(-k^2 corr^2 / 2) in momentum space (k per axis from Eq. (eigenmodes),
+    corr in lattice units), transform back, then shift and scale the result to
+    mean 0 and standard deviation `amplitude` over the lattice."""
+    n = noise.shape[0]
+    k = k_modes(n)
+    g = np.exp(-0.5 * corr * corr * k * k)
+    f = np.fft.ifftn(np.fft.fftn(noise) * g[:, None, None] * g[None, :, None] * g[None, None, :]).real
+    f = f - f.mean()
+    return amplitude * f / np.sqrt((f * f).mean())
 
 
 # --------------------------------------------------------------------------

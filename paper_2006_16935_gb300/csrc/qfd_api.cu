@@ -32,7 +32,7 @@ enum Stage { ST_NONE = 0, ST_X = 1, ST_XY = 2, ST_C = 3, ST_D = 4 };
 // device scalar slots
 enum { SC_SUMS = 0, SC_N2 = 40, SC_PV = 41, SC_PT = 42, SC_SCALE = 43, SC_E = 44, SC_COUNT = 64 };
 enum { OP_SUMS = 0, OP_NORM = 1, OP_N2PV = 2, OP_ENERGY = 3, OP_OBS = 4 };
-constexpr int NOBS = 9;
+constexpr int NOBS = 12;
 constexpr int GS_BLOCKS = 4 * 152;
 constexpr int FIN_THREADS = 1024;
 
@@ -81,7 +81,8 @@ k_finalize_op(const double* __restrict__ part, int nq, int count, double* __rest
       scal[SC_PT] = sums[0];
       scal[SC_E] = (sums[0] + scal[SC_PV]) / scal[SC_N2];
     } else if (op == OP_OBS) {
-      // sums: n2, n2_box, rho_box, rho^2, x, y, z, |P+ psi|^2_box, |P- psi|^2_box
+      // sums: n2, n2_box, rho_box, rho^2, x, y, z, |P+ psi|^2_box, |P- psi|^2_box,
+      // |P-_e1 psi|^2_box, |P-_e2 psi|^2_box, |P-_e3 psi|^2_box
       const double n2 = sums[0], nb = sums[1];
       scal[SC_SUMS + 0] = n2;
       scal[SC_SUMS + 1] = nb;
@@ -92,6 +93,9 @@ k_finalize_op(const double* __restrict__ part, int nq, int count, double* __rest
       scal[SC_SUMS + 6] = sums[6] / n2;
       scal[SC_SUMS + 7] = sums[7] / nb;
       scal[SC_SUMS + 8] = sums[8] / nb;
+      scal[SC_SUMS + 9] = sums[9] / nb;
+      scal[SC_SUMS + 10] = sums[10] / nb;
+      scal[SC_SUMS + 11] = sums[11] / nb;
     }
   }
 }
@@ -156,7 +160,10 @@ __global__ void k_fill_uniform(typename A::C* __restrict__ psi, int64_t n3, uint
 // Observables of Sec. 2.3 / 2.4 / 5.1 in lattice units (d = x - centre per
 // axis): partial sums of |psi|^2 (full and effective volume), rho |psi|^2 over
 // the effective volume (|d_l| <= half on every axis), rho^2 |psi|^2, d |psi|^2,
-// and |P+- psi|^2 over the effective volume, all in FP64.
+// and |P+- psi|^2 and |P-_{e_k} psi|^2 (k = 1, 2, 3) over the effective volume,
+// all in FP64.  P-_{e_k} of Eq. (parity_axis), normalised as a projector:
+// (1/4) [psi(x) + psi(F_other x) - psi(F_k x) - psi(-x)], F_k the reflection of
+// axis k and F_other that of the two other axes.
 template <class A>
 __global__ void __launch_bounds__(256)
 k_observables(const typename A::C* __restrict__ psi, int lg, int offgrid, double half, double* __restrict__ part) {
@@ -184,6 +191,15 @@ k_observables(const typename A::C* __restrict__ psi, int lg, int offgrid, double
       const double sx = 0.5 * (p.x + r.x), sy = 0.5 * (p.y + r.y), mx = 0.5 * (p.x - r.x), my = 0.5 * (p.y - r.y);
       acc[7] += sx * sx + sy * sy;
       acc[8] += mx * mx + my * my;
+      auto at = [&](int64_t X, int64_t Y, int64_t Z) { return A::to_d2(psi[(X << (2 * lg)) + (Y << lg) + Z]); };
+      const double2 f1 = at(rx, y, z), f2 = at(x, ry, z), f3 = at(x, y, rz);        // one axis reflected
+      const double2 g1 = at(x, ry, rz), g2 = at(rx, y, rz), g3 = at(rx, ry, z);     // the two others
+      const double2 fk[3] = {f1, f2, f3}, gk[3] = {g1, g2, g3};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double ax = 0.25 * (p.x + gk[k].x - fk[k].x - r.x), ay = 0.25 * (p.y + gk[k].y - fk[k].y - r.y);
+        acc[9 + k] += ax * ax + ay * ay;
+      }
     }
   }
   block_reduce_store<NOBS>(acc, part);
@@ -267,6 +283,58 @@ k_fdtd_energy(const typename A::C* __restrict__ psi, int lg, typename A::S c, do
   }
   double q[1] = {e};
   block_reduce_store<1>(q, part);
+}
+
+// ------------------------------------------------- Gaussian random fields
+// White noise: per site the two counter-mode uniforms of k_fill_uniform
+// (u in [0, 1)) through the Box-Muller transform, sqrt(-2 ln(1 - u0)) cos(2 pi u1).
+__global__ void k_grf_noise(double* __restrict__ f, int64_t n3, uint64_t seed) {
+  const uint64_t base = seed * 0x9E3779B97F4A7C15ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t z0 = splitmix64(base ^ (uint64_t)(2 * i)), z1 = splitmix64(base ^ (uint64_t)(2 * i + 1));
+    const double u0 = (double)(z0 >> 11) * 0x1.0p-53, u1 = (double)(z1 >> 11) * 0x1.0p-53;
+    f[i] = sqrt(-2.0 * log(1.0 - u0)) * cospi(2.0 * u1);
+  }
+}
+
+// Taps exp(-j^2 / (2 c^2)), j = -r..r, of a real-space Gaussian.
+constexpr int GRF_MAX_R = 200;
+struct GrfTaps {
+  double g[2 * GRF_MAX_R + 1];
+  int r;
+};
+
+// Periodic convolution along one axis (stride 2^(lg * (2 - axis))): taps
+// wrapping past the lattice add up, which is the periodic sum of the Gaussian.
+__global__ void k_grf_conv(const double* __restrict__ in, double* __restrict__ out, int lg, int axis, GrfTaps taps) {
+  const int64_t n = (int64_t)1 << lg, n3 = n * n * n;
+  const int sh = lg * (2 - axis);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = (i >> sh) & (n - 1), base = i - (c << sh);
+    double acc = 0.0;
+    for (int j = -taps.r; j <= taps.r; ++j) acc += taps.g[j + taps.r] * in[base + (((c + j) & (n - 1)) << sh)];
+    out[i] = acc;
+  }
+}
+
+// Per-CTA partial sums of f and f^2.
+__global__ void __launch_bounds__(256) k_grf_moments(const double* __restrict__ f, int64_t n3, double* __restrict__ part) {
+  double q[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    q[0] += f[i];
+    q[1] += f[i] * f[i];
+  }
+  block_reduce_store<2>(q, part);
+}
+
+// V += amplitude (f - mean) / std, with the sums of f and f^2 in sums[0..1].
+__global__ void k_grf_add(double* __restrict__ V, const double* __restrict__ f, int64_t n3,
+                          const double* __restrict__ sums, double amplitude) {
+  const double mean = sums[0] / (double)n3;
+  const double var = sums[1] / (double)n3 - mean * mean;
+  const double s = amplitude / sqrt(var);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    V[i] += s * (f[i] - mean);
 }
 
 }  // namespace qfd
@@ -1137,6 +1205,33 @@ qfd_status qfd_fill_potential(qfd_plan_t pl, int kind, const double* coeffs, int
   return derive_coefficients(pl);
 }
 
+qfd_status qfd_add_random_field(qfd_plan_t pl, uint64_t seed, double corr, double amplitude) {
+  if (!pl) return QFD_ERR_ARG;
+  if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "set a potential before adding a random field");
+  if (!(corr > 0) || !(amplitude >= 0))
+    return fail(pl, QFD_ERR_ARG, "corr > 0 and amplitude >= 0 required");
+  GrfTaps taps{};
+  taps.r = (int)std::ceil(corr * std::sqrt(2.0 * std::log(1e18)));
+  if (taps.r > GRF_MAX_R) return fail(pl, QFD_ERR_ARG, "corr too large (at most 21 lattice units)");
+  for (int j = -taps.r; j <= taps.r; ++j) taps.g[j + taps.r] = std::exp(-(double)j * j / (2.0 * corr * corr));
+  // the work lattice holds the two real scratch fields
+  double* f0 = reinterpret_cast<double*>(pl->W);
+  double* f1 = f0 + pl->n3;
+  pl->w_stage = ST_NONE;
+  pl->w_state = -1;
+  const int g = grid_for(pl->n3);
+  QFD_RUN(PASS_OTHER, (k_grf_noise<<<g, 256, 0, pl->st>>>(f0, pl->n3, seed), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, pl->lg, 0, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f1, f0, pl->lg, 1, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, pl->lg, 2, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_moments<<<GS_BLOCKS, 256, 0, pl->st>>>(f1, pl->n3, pl->partG), cudaGetLastError()));
+  qfd_status r = finalize(pl, pl->partG, 2, GS_BLOCKS, OP_SUMS);
+  if (r != QFD_OK) return r;
+  QFD_RUN(PASS_OTHER, (k_grf_add<<<g, 256, 0, pl->st>>>(pl->V, f1, pl->n3, pl->scal + SC_SUMS, amplitude),
+                       cudaGetLastError()));
+  return derive_coefficients(pl);
+}
+
 qfd_status qfd_get_potential(qfd_plan_t pl, double* V, int on_device) {
   if (!pl || !V) return fail(pl, QFD_ERR_ARG, "null argument");
   if (!pl->has_pot) return fail(pl, QFD_ERR_STATE, "no potential set");
@@ -1422,7 +1517,7 @@ qfd_status qfd_sync(qfd_plan_t pl) {
 }  // extern "C"
 
 // ================================================================ server
-static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 144 && sizeof(qfd_result) == 232 &&
+static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 168 && sizeof(qfd_result) == 232 &&
                   sizeof(qfd_server_params) == 32,
               "C ABI struct layouts are fixed (the Python binding mirrors them)");
 // Continuous batching of solve requests: requests wait in FIFO order and are
@@ -1583,6 +1678,8 @@ qfd_status admit(qfd_server_t sv) {
     if (r == QFD_OK) {
       const double c[2] = {m->req.pot_coeffs[0], m->req.pot_coeffs[1]};
       r = qfd_fill_potential(m->plan, m->req.potential, c, 2);
+      if (r == QFD_OK && m->req.grf_amplitude > 0)
+        r = qfd_add_random_field(m->plan, m->req.grf_seed, m->req.grf_corr, m->req.grf_amplitude);
       for (int s = 0; r == QFD_OK && s < m->req.nstates; ++s) r = qfd_fill_psi_uniform(m->plan, s, m->req.seed + s);
       if (r == QFD_OK) r = start_state(m, 0);
     }

@@ -17,6 +17,11 @@ counter mode:
     value = 2*u - 1                       in [-1, 1)   (exact in binary64)
 
 with site = (x*N + y)*N + z the row-major index and part 0 for Re, 1 for Im.
+
+Gaussian white noise (for the random-field potentials): the same two uniforms
+u0, u1 of a site (parts 0 and 1 above, as u in [0, 1)) through the Box-Muller
+transform (Box and Muller, Ann. Math. Statist. 29, 1958):
+    g = sqrt(-2 ln(1 - u0)) cos(2 pi u1).
 """
 from __future__ import annotations
 
@@ -68,3 +73,20 @@ def plane_wave_mix(n: int, seed: int, modes: int = 4):
     idx[0] = [n // 2, n // 2, n // 2]  # always include the Nyquist corner
     amp = rng.uniform(-1, 1, modes) + 1j * rng.uniform(-1, 1, modes)
     return idx.astype(np.int64), amp
+
+
+def uniform01(seed: int, counters: np.ndarray) -> np.ndarray:
+    """U[0, 1) doubles (multiples of 2**-53) for the given uint64 counters."""
+    with np.errstate(over="ignore"):
+        base = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * GOLDEN_GAMMA
+    z = splitmix64(base ^ counters.astype(np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def gaussian_noise(n: int, seed: int) -> np.ndarray:
+    """Seeded float64 lattice [n, n, n] of i.i.d. N(0, 1) values (Box-Muller on
+    the counter-mode uniforms of parts 0 and 1 of every site)."""
+    site = np.arange(n * n * n, dtype=np.uint64)
+    u0 = uniform01(seed, 2 * site)
+    u1 = uniform01(seed, 2 * site + np.uint64(1))
+    return (np.sqrt(-2.0 * np.log(1.0 - u0)) * np.cos(2.0 * np.pi * u1)).reshape(n, n, n)

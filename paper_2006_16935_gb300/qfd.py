@@ -59,7 +59,8 @@ class Request(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("potential", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("pot_coeffs", ctypes.c_double * 2),
                 ("centre", ctypes.c_int32), ("parity", ctypes.c_int32 * 8), ("seed", ctypes.c_uint64),
-                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double)]
+                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double), ("tol_bulk", ctypes.c_double),
+                ("grf_amplitude", ctypes.c_double), ("grf_corr", ctypes.c_double), ("grf_seed", ctypes.c_uint64)]
 
 
 class Result(ctypes.Structure):
@@ -93,6 +94,7 @@ def load():
         "qfd_set_potential": (I, [P, P, I]),
         "qfd_fill_potential": (I, [P, I, ctypes.POINTER(D), I]),
         "qfd_get_potential": (I, [P, P, I]),
+        "qfd_add_random_field": (I, [P, ctypes.c_uint64, D, D]),
         "qfd_set_psi": (I, [P, I, P, I]),
         "qfd_fill_psi_uniform": (I, [P, I, ctypes.c_uint64]),
         "qfd_get_psi": (I, [P, I, P, I]),
@@ -218,6 +220,10 @@ class Plan:
         c = (ctypes.c_double * max(1, len(coeffs)))(*coeffs)
         self._check(self.lib.qfd_fill_potential(self.h, POTENTIAL[kind], c, len(coeffs)))
 
+    def add_random_field(self, seed, corr, amplitude):
+        """qfd_add_random_field: V += seeded Gaussian random field (corr in lattice units)."""
+        self._check(self.lib.qfd_add_random_field(self.h, int(seed), float(corr), float(amplitude)))
+
     def get_potential(self, out=None):
         if out is None:
             out = np.empty(self.shape, np.float64)
@@ -246,9 +252,10 @@ class Plan:
 
     def observables(self, state=0, min_sep_edge=0.3):
         """dict of the observables of qfd_observables (lattice units)."""
-        out = (ctypes.c_double * 9)()
-        self._check(self.lib.qfd_observables(self.h, state, float(min_sep_edge), out, 9))
-        keys = ["norm2", "norm2_box", "rho_box", "rho2", "x", "y", "z", "w_plus", "w_minus"]
+        out = (ctypes.c_double * 12)()
+        self._check(self.lib.qfd_observables(self.h, state, float(min_sep_edge), out, 12))
+        keys = ["norm2", "norm2_box", "rho_box", "rho2", "x", "y", "z", "w_plus", "w_minus",
+                "w_axis1", "w_axis2", "w_axis3"]
         return dict(zip(keys, list(out)))
 
     def step(self, state, nsteps):
@@ -329,8 +336,9 @@ class Plan:
 
 def make_request(n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision="c128", potential="ho",
                  pot_coeffs=(1.0, 0.0), centre="grid", parity=None, seed=1, max_steps=100000, tol=1e-9,
-                 tol_bulk=1e-10, stop_rule="paper"):
-    """A qfd_request structure from keyword arguments."""
+                 tol_bulk=1e-10, stop_rule="paper", grf=None):
+    """A qfd_request structure from keyword arguments; grf = (seed, corr,
+    amplitude) adds a random field to the potential."""
     r = Request(n=n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=rest_mass, nstates=nstates,
                 precision=PRECISION[precision], potential=POTENTIAL[potential], stop_rule=STOP_RULE[stop_rule],
                 centre=CENTRE[centre], seed=seed,
@@ -338,6 +346,8 @@ def make_request(n, a, mass, dtau, kinetic, *, rest_mass=0, nstates=1, precision
     r.pot_coeffs[0], r.pot_coeffs[1] = (list(pot_coeffs) + [0.0, 0.0])[:2]
     for i, v in enumerate(parity or [0] * nstates):
         r.parity[i] = v
+    if grf is not None:
+        r.grf_seed, r.grf_corr, r.grf_amplitude = int(grf[0]), float(grf[1]), float(grf[2])
     return r
 
 

@@ -61,8 +61,34 @@ def poisson_stream(count: int, *, rate: float = 20.0, seed: int = 5, sizes=SIZES
     return out
 
 
+def batch_stream(count: int, *, seed: int = 4, sizes=(64, 128), a: float = 0.1, courant: float = 0.5,
+                 tol: float = 1e-9, grf_corr: float = 4.0, grf_amplitude: float = 0.05, max_steps: int = 400000):
+    """`count` independent solves, all present at time 0: n uniform over
+    `sizes`; Cornell V = -alpha/r + sigma r with alpha U[0.1,0.5], sigma
+    U[0.1,0.3], plus a seeded Gaussian random field (correlation length
+    grf_corr lattice units, standard deviation grf_amplitude); kinetic term
+    uniform over H_K(1..3); mass U[1,5]; 1-3 states without parity (the random
+    field breaks the reflection symmetry); spacing `a`; dtau = courant * 2 /
+    max T(k); tol under the tail rule."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(np.asarray(sizes)))
+        kinetic = int(rng.integers(1, 4))
+        mass = float(rng.uniform(1.0, 5.0))
+        nstates = int(rng.integers(1, 4))
+        alpha = float(rng.uniform(0.1, 0.5))
+        sigma = float(rng.uniform(0.1, 0.3))
+        dtau = courant * 2.0 / kinetic_max(kinetic, a, mass, 0)
+        out.append((0.0, dict(n=n, a=a, mass=mass, dtau=dtau, kinetic=kinetic, rest_mass=0, nstates=nstates,
+                              potential="cornell", pot_coeffs=(alpha, sigma), seed=2000 + 10 * i, tol=tol,
+                              tol_bulk=1e-10, stop_rule="tail", max_steps=max_steps,
+                              grf=(7000 + i, grf_corr, grf_amplitude))))
+    return out
+
+
 def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: int = 100, ortho_every: int = 10,
-          use_graphs: bool = True, stream_handle=None):
+          use_graphs: bool = True, stream_handle=None, max_active: int = 0):
     """Offers `stream` (from poisson_stream) to a server in real time: each
     request is submitted once the server clock passes its arrival time; the
     loop polls until every result is back.  Returns (records, server stats);
@@ -71,7 +97,7 @@ def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: i
     recs = [None] * len(stream)
     ids = {}
     with qfd.Server(budget_bytes, check_every=check_every, ortho_every=ortho_every, use_graphs=use_graphs,
-                    stream=stream_handle) as sv:
+                    stream=stream_handle, max_active=max_active) as sv:
         t0 = sv.clock()
         nxt = 0
         got = 0

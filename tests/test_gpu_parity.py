@@ -395,3 +395,29 @@ def test_observables_match_oracle(qfdlib, prec, centre):
     ref = O.observables(psi, centre, 0.3)
     for k, v in ref.items():
         assert got[k] == pytest.approx(v, rel=1e-12, abs=1e-12), k
+
+
+@pytest.mark.parametrize("n,corr", [(32, 4.0), (64, 4.0), (64, 3.0)])
+def test_random_field_matches_oracle(qfdlib, n, corr):
+    # Cornell plus a seeded Gaussian random field of amplitude 0.05
+    with Q.Plan(n, 0.1, 1.0, 1e-4, 2) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        p.add_random_field(17, corr, 0.05)
+        V = p.get_potential()
+    ref = O.potential(n, 0.1, "cornell", (0.3, 0.2)) + O.random_field(inputs.gaussian_noise(n, 17), corr, 0.05)
+    assert np.max(np.abs(V - ref)) < 1e-12
+
+
+def test_random_field_potential_solve_matches_oracle(qfdlib):
+    n, a, m, kin = 16, 0.3, 1.2, 2
+    dt = stable_dt(n, a, m, kin, 0.5)
+    with Q.Plan(n, a, m, dt, kin, ortho_every=10, check_every=50, max_steps=20000, tol=1e-10) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        p.add_random_field(5, 4.0, 0.05)
+        p.fill_psi_uniform(0, 9)
+        es, steps, _ = p.solve_states(1)
+    V = O.potential(n, a, "cornell", (0.3, 0.2)) + O.random_field(inputs.gaussian_noise(n, 5), 4.0, 0.05)
+    res = O.solve_state(inputs.uniform_psi(n, 9), O.Problem(n, a, m, dt, kin, V, ortho_every=10, check_every=50),
+                        20000, 1e-10)
+    assert steps[0] == res.steps
+    assert abs(es[0] - res.energy) <= TOL_E * abs(res.energy)

@@ -85,6 +85,6 @@ def test_binding_struct_sizes_match_the_header():
     import ctypes
 
     assert ctypes.sizeof(qfd.QfdParams) == 96
-    assert ctypes.sizeof(qfd.Request) == 144 and qfd.Request.pot_coeffs.offset == 56
+    assert ctypes.sizeof(qfd.Request) == 168 and qfd.Request.pot_coeffs.offset == 56
     assert ctypes.sizeof(qfd.Result) == 232
     assert ctypes.sizeof(qfd.ServerParams) == 32

@@ -605,3 +605,67 @@ def test_observable_invariants():
     assert (ob["x"], ob["y"], ob["z"]) == pytest.approx(shift, abs=1e-9)
     assert ob["rho2"] == pytest.approx(sum(v * v for v in shift) + 3 * s * s, rel=1e-9)
     assert ob["norm2"] == pytest.approx(ob["norm2_box"], rel=1e-12)
+
+
+def test_axis_parity_projections():
+    """P-_{e_k} (Eq. parity_axis) separates the p-wave magnetic substates: on
+    x_j f(r) it is 1 for j = k and 0 otherwise, it is a projector, and the
+    three axis weights of an s-wave vanish."""
+    n = 16
+    for centre in ("grid", "offgrid"):
+        d = O.displacement(n, centre)
+        d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+        f = np.exp(-(d1 ** 2 + d2 ** 2 + d3 ** 2) / 4.0)  # negligible on the self-mapped edge plane
+        for j, dj in enumerate((d1, d2, d3)):
+            p = (dj * f).astype(complex)
+            ob = O.observables(p, centre, 0.0)
+            for k in range(3):
+                want = 1.0 if k == j else 0.0
+                assert ob[f"w_axis{k + 1}"] == pytest.approx(want, abs=1e-11)
+        s_wave = O.observables(f.astype(complex), centre, 0.0)
+        assert max(s_wave[f"w_axis{k + 1}"] for k in range(3)) < 1e-28
+        psi = rand_psi(n, 51)
+        for k in range(3):
+            q = O.axis_parity_minus(psi, k, centre)
+            assert np.max(np.abs(O.axis_parity_minus(q, k, centre) - q)) < 1e-14
+            # its range lies inside the P- sector
+            assert np.max(np.abs(O.parity_project(q, -1, centre) - q)) < 1e-14
+
+
+def test_random_field_of_a_delta_is_the_periodic_gaussian():
+    """The momentum-space filter exp(-k^2 c^2 / 2) of a unit impulse is, by
+    Poisson summation, the periodic sum of real-space Gaussians
+    exp(-(x + m N)^2 / (2 c^2)) per axis (aliasing ~ exp(-pi^2 c^2 / 2), here
+    e^-79); after the shift to mean 0 and the scaling to the amplitude the two
+    agree to rounding."""
+    n, c, amp = 32, 4.0, 0.05
+    delta = np.zeros((n, n, n))
+    delta[3, 17, 30] = 1.0
+    got = O.random_field(delta, c, amp)
+    x = np.arange(n)
+
+    def per_axis(x0):
+        d = x - x0
+        return sum(np.exp(-((d + m * n) ** 2) / (2 * c * c)) for m in range(-3, 4))
+
+    h = np.einsum("i,j,k->ijk", per_axis(3), per_axis(17), per_axis(30))
+    h = h - h.mean()
+    h = amp * h / np.sqrt((h * h).mean())
+    assert np.max(np.abs(got - h)) < 1e-12 * amp
+
+
+def test_random_field_normalisation_and_noise_statistics():
+    noise = inputs.gaussian_noise(64, 4)
+    assert abs(noise.mean()) < 0.01 and abs(noise.var() - 1.0) < 0.01
+    # the first value by hand from the published definitions
+    u0 = inputs.uniform01(4, np.array([0], dtype=np.uint64))[0]
+    u1 = inputs.uniform01(4, np.array([1], dtype=np.uint64))[0]
+    assert noise[0, 0, 0] == math.sqrt(-2 * math.log(1 - u0)) * math.cos(2 * math.pi * u1)
+    f = O.random_field(noise, 4.0, 0.05)
+    assert abs(f.mean()) < 1e-15 and math.sqrt((f * f).mean()) == pytest.approx(0.05, rel=1e-14)
+    # a smooth field: neighbouring sites are strongly correlated (Gaussian of
+    # width c sqrt 2 in the covariance: exp(-1 / (4 c^2)) ~ 0.98 at one site)
+    corr = (f * np.roll(f, 1, axis=2)).mean() / (f * f).mean()
+    assert corr == pytest.approx(math.exp(-1 / 64), abs=0.01)
+    assert np.max(np.abs(O.random_field(3 * noise, 4.0, 0.05) - f)) < 1e-15
+
