@@ -254,6 +254,16 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
     return plan, ms, steps[0], es[0], launches, per_pass
 
 
+# DRAM read + write bytes per site of the dominant kernel, from one ncu capture
+# of a 256^3 launch of the same kernel (`--set full`, profile_step driver);
+# traffic grows with the sites, so a 512^3 launch moves 512^3 times this
+DRAM_BYTES_PER_SITE = {
+    ("c128", "update_x"): (806.0e6 + 484.0e6) / 256 ** 3,
+    ("df64", "update_x"): (805.0e6 + 484.0e6) / 256 ** 3,
+    ("c64", "update_x"): (403.0e6 + 215.0e6) / 256 ** 3,
+}
+
+
 def roofline_for(prec, per_pass, peaks):
     dom = max(per_pass, key=lambda k: per_pass[k]["total_ms"])
     cnt, tot = per_pass[dom]["launches"], per_pass[dom]["total_ms"]
@@ -277,7 +287,11 @@ def roofline_for(prec, per_pass, peaks):
     else:
         r = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
              "peak_source": "hbm_gbs of MEASURED_PEAKS.json (of measured)"}
-    r.update({"kernel": dom, "traffic": None, "avg_launch_ms": 1e3 * avg_s,
+    per_site = DRAM_BYTES_PER_SITE.get((prec, dom))
+    r.update({"kernel": dom, "traffic": per_site * sites if per_site else None,
+              "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 256^3 launch, "
+                                "scaled by the sites" if per_site else None,
+              "avg_launch_ms": 1e3 * avg_s,
               "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
               "hbm_gbs_achieved": hbm, "hbm_frac": hbm_frac, "alu_tflops_achieved": alu,
               "share_of_step": tot / sum(v["total_ms"] for v in per_pass.values())})

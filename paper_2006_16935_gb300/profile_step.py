@@ -21,7 +21,9 @@ def main(argv=None):
     ap.add_argument("--parity", type=int, default=1)
     ap.add_argument("--kinetic", type=int, default=2)
     args = ap.parse_args(argv)
-    with qfd.Plan(args.n, 0.05, 1.0, 5e-4, args.kinetic, precision=args.precision, ortho_every=2) as p:
+    centre = "offgrid" if args.kinetic == 0 else "grid"  # the Dirichlet box of H_K(0) is symmetric off-grid
+    with qfd.Plan(args.n, 0.05, 1.0, 5e-4, args.kinetic, precision=args.precision, ortho_every=2,
+                  centre=centre) as p:
         p.fill_potential("softcoul", (0.01,))
         p.fill_psi_uniform(0, 3)
         p.set_parity(0, args.parity)
