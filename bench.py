@@ -230,6 +230,7 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
                   check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP * max(1, args.warmup), tol=-1,
                   stream=stream.cuda_stream)
     plan.fill_potential(*POT)
+    plan.tuning = plan.autotune()  # launch shapes of the y and z passes
     plan.fill_psi_uniform(0, SEED)
     es, _, _ = plan.solve_states(1, [1])  # warm-up: W bench steps
     plan.set_limits(STEPS_PER_BENCH_STEP * args.steps, -1)
@@ -310,6 +311,7 @@ def e2e_rate(torch, Q, args, prec, dev):
                   check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP, tol=-1,
                   stream=stream.cuda_stream)
     plan.fill_potential(*POT)
+    plan.autotune()
     for _ in range(max(1, args.warmup)):
         plan.set_psi(0, host)
         plan.solve_states(1, [1])
@@ -351,6 +353,7 @@ def run_qfd(args):
         dist.barrier()
     plan, ms, steps, energy, launches, per_pass = time_precision(torch, Q, args, prec, dev, True)
     clk = clocks.stop()
+    tuning = {prec: plan.tuning}
     plan.close()
     ms = max_over_ranks(ms, dev)
     total_units = float(N) ** 3 * steps * world
@@ -361,6 +364,7 @@ def run_qfd(args):
     others = {}
     for other in [p for p in ("c128", "df64", "c64") if p != prec]:
         pl_o, ms_o, steps_o, e_o, _, per_pass_o = time_precision(torch, Q, args, other, dev, True)
+        tuning[other] = pl_o.tuning
         pl_o.close()
         others[other] = {"value": float(N) ** 3 * steps_o / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
                          "energy_at_end": e_o, "roofline": roofline_for(other, per_pass_o, peaks),
@@ -383,6 +387,7 @@ def run_qfd(args):
         "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass.items()},
         "peaks_source": peak_src,
         "other_precisions": others,
+        "autotune_ms": tuning,
     }
     if world == 1 and not args.no_cpu_baseline:
         if mem_available_gb() > 24:
@@ -418,6 +423,7 @@ def full_solves(torch, Q, dev, which, ms_step_c128=None):
         plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=10, check_every=100, max_steps=400000,
                       tol=1e-9, tol_bulk=1e-10, stream=stream.cuda_stream)
         plan.fill_potential(*POT)
+        plan.autotune()
         plan.fill_psi_uniform(0, SEED)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()

@@ -237,6 +237,25 @@ qfd_status qfd_solve_states(qfd_plan_t plan, int nstates, const int* parity, dou
 qfd_status qfd_snapshot_states(qfd_plan_t plan, int nout, int parity, int64_t snap_every, double* E_out,
                                int64_t* steps_out);
 
+/* Launch-shape autotuner (a tuning of this implementation; the paper has no
+ * counterpart).  For every arithmetic the plan uses, times the y passes with
+ * tiles of the default width and of twice that width, and the z pass with
+ * one and with two line groups per CTA, on the work lattice (5 launches each
+ * after 2 warm-ups), and keeps the faster of each for later launches.  The
+ * choices change how work is tiled, not the arithmetic of any line: results
+ * agree to rounding whatever is chosen (complex128 / complex64 kernels may
+ * differ in where the compiler fuses a multiply-add; double-float ones are
+ * bit-identical).  ms_out (NULL or 12 doubles): per
+ * policy (0 complex128, 1 complex64, 2 double-float) the median times of
+ * y-default, y-wide, z-1, z-2 in ms (NaN for unused policies).  Synchronises;
+ * the work lattice is recomputed at the next step. */
+qfd_status qfd_autotune(qfd_plan_t plan, double* ms_out);
+
+/* Sets the launch shapes of one policy (0 complex128, 1 complex64, 2
+ * double-float) by hand: y_variant 0 default width, 1 twice it; z_variant
+ * -1 the policy's default grouping, 0 one line group, 1 two. */
+qfd_status qfd_set_tuning(qfd_plan_t plan, int policy, int y_variant, int z_variant);
+
 /* Replaces the plan's max_steps, tol and tol_bulk (same meaning as in
  * qfd_params) for later qfd_solve_states calls. */
 qfd_status qfd_set_limits(qfd_plan_t plan, int64_t max_steps, double tol, double tol_bulk);

@@ -374,6 +374,8 @@ struct qfd_plan_s {
   double* hscal = nullptr;  // pinned host copy of the scalars (+ the error flag)
   // host-side state
   KinParams kin{};
+  int tune_vy[3] = {0, 0, 0};     // launch shapes per policy id (autotuner; see LaunchArgs)
+  int tune_vz[3] = {-1, -1, -1};
   int lg = 0;           // n = 2^lg
   double fdtd_c = 0.0;  // 1 / (2 M A^2) of H_K(0)
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
@@ -523,6 +525,8 @@ LaunchArgs base_args(qfd_plan_t pl) {
   a.V = pl->V;
   a.err = pl->errflag;
   a.stream = pl->st;
+  a.vy = pl->tune_vy[A::id];
+  a.vz = pl->tune_vz[A::id];
   return a;
 }
 
@@ -941,6 +945,53 @@ qfd_status snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap_eve
     if ((r = materialize<A>(pl, k)) != QFD_OK) return r;
     if ((r = energy_full<A>(pl, k, &E_out[k], &n2)) != QFD_OK) return r;
   }
+  return QFD_OK;
+}
+
+// Median time (ms) of `reps` launches of f on the plan's stream after `warm`.
+template <class F>
+qfd_status time_launch(qfd_plan_t pl, F&& f, int warm, int reps, double* ms) {
+  cudaEvent_t e0, e1;
+  QFD_CK(cudaEventCreate(&e0));
+  QFD_CK(cudaEventCreate(&e1));
+  std::vector<double> t;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < warm + reps && err == cudaSuccess; ++i) {
+    cudaEventRecord(e0, pl->st);
+    err = f();
+    cudaEventRecord(e1, pl->st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float m = 0.f;
+    if (err == cudaSuccess && i >= warm && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess) t.push_back(m);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(pl, QFD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
+  std::sort(t.begin(), t.end());
+  *ms = t.empty() ? INFINITY : t[t.size() / 2];
+  return QFD_OK;
+}
+
+// Times both y-tile widths and both z-pass groupings of policy A on the work
+// lattice and keeps the faster of each.
+template <class A>
+qfd_status autotune_policy(qfd_plan_t pl, double* ms) {
+  qfd_status r;
+  QFD_CK(cudaMemsetAsync(pl->W, 0, (size_t)pl->n3 * sizeof(double2), pl->st));
+  for (int v = 0; v < 2; ++v) {
+    LaunchArgs a = base_args<A>(pl);
+    a.vy = v;
+    if ((r = time_launch(pl, [&]() { return launch_fft_y<A>(a, -1); }, 2, 5, &ms[v])) != QFD_OK) return r;
+  }
+  for (int v = 0; v < 2; ++v) {
+    LaunchArgs a = base_args<A>(pl);
+    a.vz = v;
+    a.stats = 0;
+    a.part = pl->partC;
+    if ((r = time_launch(pl, [&]() { return launch_zpass<A>(a, nullptr); }, 2, 5, &ms[2 + v])) != QFD_OK) return r;
+  }
+  pl->tune_vy[A::id] = ms[1] < ms[0] ? 1 : 0;
+  pl->tune_vz[A::id] = ms[3] < ms[2] ? 1 : 0;
   return QFD_OK;
 }
 
@@ -1432,6 +1483,30 @@ qfd_status qfd_snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap
   if (r != QFD_OK) return r;
   QFD_CK(cudaStreamSynchronize(pl->st));
   if (pl->p.tol >= 0 && !conv) return fail(pl, QFD_ERR_NOT_CONVERGED, "max_steps reached before the tolerance");
+  return QFD_OK;
+}
+
+qfd_status qfd_autotune(qfd_plan_t pl, double* ms_out) {
+  if (!pl) return QFD_ERR_ARG;
+  double ms[12];
+  for (double& m : ms) m = NAN;
+  QFD_CK(cudaStreamSynchronize(pl->st));
+  qfd_status r = QFD_OK;
+  if (uses32(pl->p.precision) && (r = autotune_policy<F32>(pl, ms + 4)) != QFD_OK) return r;
+  if (pl->psi16 && pl->arith16 == 0 && (r = autotune_policy<F64>(pl, ms + 0)) != QFD_OK) return r;
+  if (pl->psi16 && pl->arith16 == 2 && (r = autotune_policy<DF>(pl, ms + 8)) != QFD_OK) return r;
+  pl->w_stage = ST_NONE;  // W was used as the timing lattice
+  pl->w_state = -1;
+  if (ms_out) std::memcpy(ms_out, ms, sizeof(ms));
+  return QFD_OK;
+}
+
+qfd_status qfd_set_tuning(qfd_plan_t pl, int policy, int y_variant, int z_variant) {
+  if (!pl) return QFD_ERR_ARG;
+  if (policy < 0 || policy > 2 || y_variant < 0 || y_variant > 1 || z_variant < -1 || z_variant > 1)
+    return fail(pl, QFD_ERR_ARG, "policy 0..2, y_variant 0..1, z_variant -1..1");
+  pl->tune_vy[policy] = y_variant;
+  pl->tune_vz[policy] = z_variant;
   return QFD_OK;
 }
 

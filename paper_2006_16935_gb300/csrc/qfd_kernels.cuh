@@ -496,6 +496,10 @@ template <class A, int N> struct Shape {
   // z-pass line groups per CTA (see k_zpass), when they divide the lines
   static constexpr int ZG0 = WIDE ? QFD_ZG16 : QFD_ZG8;
   static constexpr int ZG = (N * N / LINES) % ZG0 == 0 && N * N / LINES >= ZG0 ? ZG0 : 1;
+  // the autotuner's alternatives: y tiles twice as wide (within 1024 threads
+  // and N columns), z-pass line groups 1 or 2
+  static constexpr int YCOLS2 = 2 * YCOLS * T <= 1024 && 2 * YCOLS <= N ? 2 * YCOLS : YCOLS;
+  static constexpr int ZG2 = (N * N / LINES) % 2 == 0 && N * N / LINES >= 2 ? 2 : 1;
   // one padding element per 128 bytes of a line
   static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
   static constexpr int LPAD = N + (N >> PAD_SHIFT);
@@ -554,21 +558,23 @@ enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 // Pass B / D (and the plain x transform): in-place strided line FFT over tiles
 // of COLS contiguous columns.  Tile id ->
 // base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
-template <class A, int N, int DIR>
-__global__ void __launch_bounds__(Shape<A, N>::YTHREADS)
+// YC (the tile width) is a launch-shape choice of the autotuner; the
+// arithmetic of every column is the same for all widths.
+template <class A, int N, int DIR, int YC = Shape<A, N>::YCOLS>
+__global__ void __launch_bounds__(N / 8 * YC)
 k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
               int64_t outer_stride) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int col = threadIdx.x % SH::YCOLS, t = threadIdx.x / SH::YCOLS;
+  const int col = threadIdx.x % YC, t = threadIdx.x / YC;
   const int64_t base = (int64_t)(blockIdx.x / tiles_inner) * outer_stride +
-                       (int64_t)(blockIdx.x % tiles_inner) * SH::YCOLS + col;
+                       (int64_t)(blockIdx.x % tiles_inner) * YC + col;
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
-  AccTile<C, SH::YCOLS, SH::YPITCH> acc{sm, col};
+  AccTile<C, YC, YC> acc{sm, col};
   fft_line<A, N, DIR>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < 8; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
@@ -580,7 +586,7 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
 // A CTA takes ZG groups of LINES consecutive lines in turn; the loads of the
 // next group are issued before the current group's transforms, so they are in
 // flight while it computes.
-template <class A, int N, bool PARSEVAL>
+template <class A, int N, bool PARSEVAL, int ZG = Shape<A, N>::ZG>
 __global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
 k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
         KinParams kp, double* __restrict__ part) {
@@ -590,7 +596,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int l = threadIdx.x / SH::T, t = threadIdx.x % SH::T;
-  const int64_t line0 = (int64_t)blockIdx.x * SH::LINES * SH::ZG + l;  // line = kx * N + ky
+  const int64_t line0 = (int64_t)blockIdx.x * SH::LINES * ZG + l;  // line = kx * N + ky
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = W[line0 * N + t + m * SH::T];
@@ -598,11 +604,11 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
   double pt = 0.0;
 #pragma unroll
-  for (int g = 0; g < SH::ZG; ++g) {
+  for (int g = 0; g < ZG; ++g) {
     const int64_t line = line0 + (int64_t)g * SH::LINES;
     C* p = W + line * N;
     C nx[8];
-    if (g + 1 < SH::ZG) {
+    if (g + 1 < ZG) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
     }
@@ -617,7 +623,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
     fft_line<A, N, +1>(v, t, tw, acc);
 #pragma unroll
     for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
-    if (g + 1 < SH::ZG) {
+    if (g + 1 < ZG) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = nx[m];
     }

@@ -54,6 +54,10 @@ struct LaunchArgs {
   int offgrid = 0;             // reflection about the off-grid centre
   const double* sums = nullptr;  // overlaps (2 doubles per lower state)
   void* dst = nullptr;         // projected state output
+  // launch shapes (autotuner): y tiles of the default width (0) or twice it
+  // (1); z-pass line groups of the policy default (-1), 1 (0) or 2 (1)
+  int vy = 0;
+  int vz = -1;
 };
 
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the

@@ -52,16 +52,20 @@ template <class A, int N>
 cudaError_t Launch<A, N>::fft_y(const LaunchArgs& a, int dir) {
   using C = typename A::C;
   using SH = Shape<A, N>;
-  const size_t smem = (size_t)N * SH::YPITCH * sizeof(C);
-  const int tiles_inner = N / SH::YCOLS;
-  const int grid = N * tiles_inner;
-  auto go = [&](auto kern) {
+  auto go = [&](auto kern, int yc) {
+    const size_t smem = (size_t)N * yc * sizeof(C);
+    const int tiles_inner = N / yc;
     ensure_smem(kern, smem);
-    kern<<<grid, SH::YTHREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
-                                                      (int64_t)N * N);
+    kern<<<N * tiles_inner, N / 8 * yc, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
+                                                          (int64_t)N * N);
   };
-  if (dir < 0) go(k_fft_strided<A, N, -1>);
-  else go(k_fft_strided<A, N, +1>);
+  if (a.vy == 1) {
+    if (dir < 0) go(k_fft_strided<A, N, -1, SH::YCOLS2>, SH::YCOLS2);
+    else go(k_fft_strided<A, N, +1, SH::YCOLS2>, SH::YCOLS2);
+  } else {
+    if (dir < 0) go(k_fft_strided<A, N, -1>, SH::YCOLS);
+    else go(k_fft_strided<A, N, +1>, SH::YCOLS);
+  }
   return cudaGetLastError();
 }
 
@@ -70,14 +74,24 @@ cudaError_t Launch<A, N>::zpass(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(C);
-  const int grid = (int)((int64_t)N * N / (SH::LINES * SH::ZG));
+  // z-pass line groups: the policy's default, or the autotuner's 1 / 2
+  const int zg = a.vz == 0 ? 1 : a.vz == 1 ? SH::ZG2 : SH::ZG;
+  const int grid = (int)((int64_t)N * N / (SH::LINES * zg));
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<grid, SH::LINE_THREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (const typename A::T*)a.ktab, *a.kin,
                                                       a.part);
   };
-  if (a.stats) go(k_zpass<A, N, true>);
-  else go(k_zpass<A, N, false>);
+  if (zg == 1) {
+    if (a.stats) go(k_zpass<A, N, true, 1>);
+    else go(k_zpass<A, N, false, 1>);
+  } else if (zg == SH::ZG2) {
+    if (a.stats) go(k_zpass<A, N, true, SH::ZG2>);
+    else go(k_zpass<A, N, false, SH::ZG2>);
+  } else {
+    if (a.stats) go(k_zpass<A, N, true>);
+    else go(k_zpass<A, N, false>);
+  }
   if (nblocks) *nblocks = grid;
   return cudaGetLastError();
 }

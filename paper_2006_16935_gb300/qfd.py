@@ -104,6 +104,8 @@ def load():
         "qfd_energy": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_set_limits": (I, [P, I64, D, D]),
+        "qfd_autotune": (I, [P, ctypes.POINTER(D)]),
+        "qfd_set_tuning": (I, [P, I, I, I]),
         "qfd_snapshot_states": (I, [P, I, I, I64, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
@@ -283,6 +285,20 @@ class Plan:
         se = self.params.check_every if snap_every is None else snap_every
         st = self._check(self.lib.qfd_snapshot_states(self.h, nout, parity, int(se), es, ctypes.byref(steps)), ok)
         return list(es), steps.value, st == OK
+
+    def autotune(self):
+        """qfd_autotune; returns {policy: {"y": [default, wide], "z": [1 group, 2 groups]}} in ms."""
+        ms = (ctypes.c_double * 12)()
+        self._check(self.lib.qfd_autotune(self.h, ms))
+        out = {}
+        for pid, name in enumerate(("c128", "c64", "df64")):
+            v = list(ms[4 * pid:4 * pid + 4])
+            if not all(x != x for x in v):
+                out[name] = {"y": v[:2], "z": v[2:]}
+        return out
+
+    def set_tuning(self, policy, y_variant, z_variant):
+        self._check(self.lib.qfd_set_tuning(self.h, int(policy), int(y_variant), int(z_variant)))
 
     def set_limits(self, max_steps, tol, tol_bulk=None):
         tb = self.params.tol_bulk if tol_bulk is None else tol_bulk
