@@ -483,7 +483,7 @@ def serve_section(torch, Q, dev, count, sizes, precisions):
     return out
 
 
-def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df"):
+def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_steps=50000):
     """The batched workload: `count` independent solves (n uniform over
     `sizes`, Cornell + seeded random field, random kinetic term, mass
     U[1,5], 1-3 states, complex64 bulk + double-float refinement to 1e-9 under
@@ -492,8 +492,9 @@ def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df"):
     at a time (max_active = 1)."""
     from paper_2006_16935_gb300 import serve as S
 
-    stream = S.batch_stream(count, sizes=sizes)
+    stream = S.batch_stream(count, sizes=sizes, max_steps=max_steps)
     out = {"solves": count, "sizes": list(sizes), "spacing_a": stream[0][1]["a"], "tol": 1e-9,
+           "max_steps_per_state_and_phase": max_steps,
            "stop_rule": "tail", "precision": precision,
            "potential": "Cornell + Gaussian random field (corr 4 lattice units, std 0.05)", "modes": {}}
     energies = {}
@@ -521,7 +522,8 @@ def run_batch_only(args):
     build.build_library()
     clocks = ClockSampler(local)
     clocks.start()
-    sec = batch_section(torch, Q, dev, args.batch, [int(x) for x in args.batch_sizes.split(",")])
+    sec = batch_section(torch, Q, dev, args.batch, [int(x) for x in args.batch_sizes.split(",")],
+                        max_steps=args.batch_max_steps)
     clk = clocks.stop()
     if rank == 0:
         line = {"metric": "batch: solves/s of independent solves submitted together",
@@ -576,6 +578,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="solves of the batched workload (with --batch-only)")
     ap.add_argument("--batch-sizes", default="64,128")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched workload")
+    ap.add_argument("--batch-max-steps", type=int, default=50000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

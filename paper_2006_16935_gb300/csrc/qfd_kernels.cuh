@@ -349,7 +349,10 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
 // One Stockham stage on the register-resident canonical set v[m] = x[t + m N/8].
 // Butterfly b = t + u N/8 (u < 8/RAD) takes x[b + r N/RAD] = v[u + r (8/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
-template <class A, int N, int RAD, int NS, int DIR, bool LAST>
+// TWC: the twiddles of a stage from one sincospif and products of powers
+// instead of table loads (complex64 only; the z-pass, where the table loads
+// of its two transforms compete with its shared-memory exchanges).
+template <class A, int N, int RAD, int NS, int DIR, bool LAST, bool TWC = false>
 __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw) {
   using C = typename A::C;
   constexpr int NB = 8 / RAD;
@@ -361,10 +364,23 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, cons
     if (NS > 1) {
       const int b = t + u * (N / 8);
       const int e0 = (b % NS) * (N / (NS * RAD));
+      if constexpr (TWC && A::id == 1) {
+        // w = exp(-2 pi i e0 / N) from sincospif, its powers by products
+        // (a few ulp of FP32, like the rounding of the transform itself)
+        float sn, cs;
+        sincospif(-2.0f * (float)e0 / (float)N, &sn, &cs);
+        C w[8];
+        w[1] = C{cs, sn};
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        const C w = A::ldtw(&tw[e0 * r]);
-        x[r] = DIR < 0 ? cmul(x[r], w) : cmulc(x[r], w);
+        for (int r = 2; r < RAD; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) x[r] = DIR < 0 ? cmul(x[r], w[r]) : cmulc(x[r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const C w = A::ldtw(&tw[e0 * r]);
+          x[r] = DIR < 0 ? cmul(x[r], w) : cmulc(x[r], w);
+        }
       }
     }
     if (RAD == 8) dft8<DIR>(x);
@@ -392,23 +408,23 @@ __device__ __forceinline__ void stage_exchange(C (&v)[8], int t, Acc& acc) {
   acc.sync();
 }
 
-template <class A, int N, int DIR, int I, class Acc>
+template <class A, int N, int DIR, int I, bool TWC, class Acc>
 __device__ __forceinline__ void fft_stages(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
                                            Acc& acc) {
   if constexpr (I < FftPlan<N>::S) {
     constexpr int RAD = FftPlan<N>::radix(I);
     constexpr int NS = FftPlan<N>::ns(I);
-    stage_compute<A, N, RAD, NS, DIR, I + 1 == FftPlan<N>::S>(v, t, tw);
+    stage_compute<A, N, RAD, NS, DIR, I + 1 == FftPlan<N>::S, TWC>(v, t, tw);
     if constexpr (I + 1 < FftPlan<N>::S) stage_exchange<typename A::C, N, RAD, NS>(v, t, acc);
-    fft_stages<A, N, DIR, I + 1>(v, t, tw, acc);
+    fft_stages<A, N, DIR, I + 1, TWC>(v, t, tw, acc);
   }
 }
 
 // Unnormalised length-N DFT, sign DIR, canonical layout in and out.
-template <class A, int N, int DIR, class Acc>
+template <class A, int N, int DIR, class Acc, bool TWC = false>
 __device__ __forceinline__ void fft_line(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
                                          Acc& acc) {
-  fft_stages<A, N, DIR, 0>(v, t, tw, acc);
+  fft_stages<A, N, DIR, 0, TWC>(v, t, tw, acc);
 }
 
 // Shared-memory views. Tile of CW columns of a strided axis: [pos][col] with a
@@ -612,7 +628,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 #pragma unroll
       for (int m = 0; m < 8; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
     }
-    fft_line<A, N, -1>(v, t, tw, acc);
+    fft_line<A, N, -1, decltype(acc), true>(v, t, tw, acc);
     const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -620,7 +636,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
       if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
       v[m] = cscale(v[m], tk);
     }
-    fft_line<A, N, +1>(v, t, tw, acc);
+    fft_line<A, N, +1, decltype(acc), true>(v, t, tw, acc);
 #pragma unroll
     for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
     if (g + 1 < ZG) {
