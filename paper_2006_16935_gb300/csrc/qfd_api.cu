@@ -125,16 +125,25 @@ __global__ void k_potential(double* __restrict__ V, int64_t n, double a, int kin
 
 // Update coefficients of Sec. 2.2 from V, per arithmetic: FP64 {A, B dtau};
 // FP32 and double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64.
-__global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double2* __restrict__ c64,
-                       dfc* __restrict__ cdf, float2* __restrict__ c32, int* __restrict__ bad) {
+// fdtd_c > 0 (H_K(0) plans, c = 1 / (2 M A^2)): the coefficients take the
+// stencil's diagonal in, so that the update applied to the neighbour sum S
+// gives A psi - B dtau c (6 psi - S) = (A - 6 c B dtau) psi + c B dtau S.
+__global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double fdtd_c,
+                       double2* __restrict__ c64, dfc* __restrict__ cdf, float2* __restrict__ c32,
+                       int* __restrict__ bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i];
     const double h = 0.5 * dtau * v;
     const double den = 1.0 + h;
     if (!(den > 0.0) || !isfinite(v)) atomicOr(bad, 1);
     const double A = (1.0 - h) / den, B = 1.0 / den;
-    const double g1 = B * dtau, g2 = dtau * v * B;
-    if (c64) c64[i] = double2{A, g1};
+    double a64 = A, g1 = B * dtau, g2 = dtau * v * B;
+    if (fdtd_c > 0.0) {
+      a64 = (1.0 - h - 6.0 * fdtd_c * dtau) / den;  // A - 6 c B dtau
+      g2 = dtau * (v + 6.0 * fdtd_c) * B;            // (1 - A) + 6 c B dtau
+      g1 = -fdtd_c * g1;                             // -c B dtau
+    }
+    if (c64) c64[i] = double2{a64, g1};
     if (cdf) cdf[i] = dfc{dsplit(g1), dsplit(g2)};
     if (c32) c32[i] = float2{(float)g1, (float)g2};
   }
@@ -217,8 +226,8 @@ __global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C*
 // Eq. HK0_momentum_space_1): c (6 psi - the sum of the six neighbours) with
 // c = 1 / (2 M A^2).  `self` receives psi at idx.
 template <class A>
-__device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict__ psi, int64_t idx, int lg,
-                                                 typename A::S c, typename A::C& self) {
+__device__ __forceinline__ typename A::C fdtd_sum(const typename A::C* __restrict__ psi, int64_t idx, int lg,
+                                                  typename A::C& self) {
   using C = typename A::C;
   const int64_t n = (int64_t)1 << lg, n2 = n * n;
   const int64_t z = idx & (n - 1), y = (idx >> lg) & (n - 1), x = idx >> (2 * lg);
@@ -230,12 +239,20 @@ __device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict
   s = cadd(s, y + 1 < n ? psi[idx + n] : zero);
   s = cadd(s, z > 0 ? psi[idx - 1] : zero);
   s = cadd(s, z + 1 < n ? psi[idx + 1] : zero);
+  return s;
+}
+template <class A>
+__device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict__ psi, int64_t idx, int lg,
+                                                 typename A::S c, typename A::C& self) {
+  const typename A::C s = fdtd_sum<A>(psi, idx, lg, self);
   return cscale(csub(cscale(self, A::scalar(6.0)), s), c);
 }
 
 // One imaginary-time step of Eq. (iter_proced) with H_K(0): out = A psi -
 // B dtau H_K(0) psi (times the pending normalisation factor), partial sums per
-// STATS.  psi and out are different lattices (the stencil reads neighbours).
+// STATS.  The coefficients of H_K(0) plans hold the stencil's diagonal (see
+// k_coef), so the update takes the neighbour sum.  psi and out are different
+// lattices (the stencil reads neighbours).
 template <class A, int STATS>
 __global__ void __launch_bounds__(256)
 k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__ out,
@@ -250,8 +267,8 @@ k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__
   double n2 = 0.0, pv = 0.0;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += (int64_t)gridDim.x * blockDim.x) {
     C self;
-    const C hk = fdtd_hk<A>(psi, idx, lg, c, self);
-    C nw = A::update(self, hk, coef[idx]);
+    const C sum = fdtd_sum<A>(psi, idx, lg, self);
+    C nw = A::update(self, sum, coef[idx]);
     if (scaled) nw = cscale(nw, s);
     out[idx] = nw;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
@@ -1022,8 +1039,9 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
   QFD_CK(cudaMemsetAsync(pl->flag, 0, sizeof(int), pl->st));
   double2* c64 = (pl->coef16 && pl->arith16 == 0) ? (double2*)pl->coef16 : nullptr;
   dfc* cdf = (pl->coef16 && pl->arith16 == 2) ? (dfc*)pl->coef16 : nullptr;
-  QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau, c64, cdf, pl->coef32,
-                                                                     pl->flag),
+  QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau,
+                                                                     pl->p.kinetic == 0 ? pl->fdtd_c : 0.0, c64,
+                                                                     cdf, pl->coef32, pl->flag),
                        cudaGetLastError()));
   int bad = 0;
   QFD_CK(cudaMemcpyAsync(&bad, pl->flag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
