@@ -576,7 +576,7 @@ def main():
     ap.add_argument("--serve-precisions", default="c64_refine_df,df64")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving sample")
     ap.add_argument("--batch", type=int, default=0, help="solves of the batched workload (with --batch-only)")
-    ap.add_argument("--batch-sizes", default="64,128")
+    ap.add_argument("--batch-sizes", default="64,96,128,192")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched workload")
     ap.add_argument("--batch-max-steps", type=int, default=50000)
     args = ap.parse_args()

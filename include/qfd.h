@@ -106,7 +106,7 @@ enum { QFD_POT_ZERO = 0, QFD_POT_HO = 1, QFD_POT_CORNELL = 2, QFD_POT_COULOMB = 
 enum { QFD_STOP_PAPER = 0, QFD_STOP_TAIL = 1 };
 
 typedef struct {
-  int64_t n;            /* lattice points per axis (NUM) */
+  int64_t n;            /* lattice points per axis (NUM): 8, 16, 32, 64, 96, 128, 192, 256, 512 or 1024 */
   double a;             /* lattice spacing A (> 0) */
   double mass;          /* mass M (> 0) */
   double dtau;          /* imaginary time step EPS (> 0) */

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqfd.so")
 POLICIES = ["DF", "F64", "F32"]  # slowest first
-SIZES = [1024, 512, 256, 128, 64, 32, 16, 8]
+SIZES = [1024, 512, 256, 192, 128, 96, 64, 32, 16, 8]
 UNITS = ([("qfd_inst.cu", f"inst_{p}_{n}", ["-DQFD_POLICY=" + p, f"-DQFD_N={n}"]) for p in POLICIES for n in SIZES]
          + [("qfd_api.cu", "api", []), ("qfd_noalloc.cu", "noalloc", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -166,6 +166,29 @@ __global__ void k_fill_uniform(typename A::C* __restrict__ psi, int64_t n3, uint
   }
 }
 
+// Site index <-> (x, y, z) of an n^3 lattice ([x][y][z], z fastest): shifts
+// and masks when n = 2^lg (lg >= 0), divisions otherwise (n = 96, 192).
+struct Lat {
+  int64_t n;
+  int lg;
+};
+__device__ __forceinline__ void lat_xyz(Lat L, int64_t i, int64_t& x, int64_t& y, int64_t& z) {
+  if (L.lg >= 0) {
+    z = i & (L.n - 1);
+    y = (i >> L.lg) & (L.n - 1);
+    x = i >> (2 * L.lg);
+  } else {
+    z = i % L.n;
+    const int64_t q = i / L.n;
+    y = q % L.n;
+    x = q / L.n;
+  }
+}
+__device__ __forceinline__ int64_t lat_idx(Lat L, int64_t x, int64_t y, int64_t z) { return (x * L.n + y) * L.n + z; }
+__device__ __forceinline__ int64_t lat_wrap(Lat L, int64_t c) {
+  return L.lg >= 0 ? (c & (L.n - 1)) : ((c % L.n) + L.n) % L.n;
+}
+
 // Observables of Sec. 2.3 / 2.4 / 5.1 in lattice units (d = x - centre per
 // axis): partial sums of |psi|^2 (full and effective volume), rho |psi|^2 over
 // the effective volume (|d_l| <= half on every axis), rho^2 |psi|^2, d |psi|^2,
@@ -175,17 +198,18 @@ __global__ void k_fill_uniform(typename A::C* __restrict__ psi, int64_t n3, uint
 // axis k and F_other that of the two other axes.
 template <class A>
 __global__ void __launch_bounds__(256)
-k_observables(const typename A::C* __restrict__ psi, int lg, int offgrid, double half, double* __restrict__ part) {
-  const int64_t n = (int64_t)1 << lg, n3 = n * n * n;
+k_observables(const typename A::C* __restrict__ psi, Lat L, int offgrid, double half, double* __restrict__ part) {
+  const int64_t n = L.n, n3 = n * n * n;
   const double cen = offgrid ? 0.5 * (double)(n - 1) : (double)(n / 2);
   double acc[NOBS];
 #pragma unroll
   for (int q = 0; q < NOBS; ++q) acc[q] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t z = i & (n - 1), y = (i >> lg) & (n - 1), x = i >> (2 * lg);
-    const int64_t rx = offgrid ? n - 1 - x : (n - x) & (n - 1), ry = offgrid ? n - 1 - y : (n - y) & (n - 1),
-                  rz = offgrid ? n - 1 - z : (n - z) & (n - 1);
-    const double2 p = A::to_d2(psi[i]), r = A::to_d2(psi[(rx << (2 * lg)) + (ry << lg) + rz]);
+    int64_t x, y, z;
+    lat_xyz(L, i, x, y, z);
+    const int64_t rx = offgrid ? n - 1 - x : lat_wrap(L, n - x), ry = offgrid ? n - 1 - y : lat_wrap(L, n - y),
+                  rz = offgrid ? n - 1 - z : lat_wrap(L, n - z);
+    const double2 p = A::to_d2(psi[i]), r = A::to_d2(psi[lat_idx(L, rx, ry, rz)]);
     const double dx = (double)x - cen, dy = (double)y - cen, dz = (double)z - cen;
     const double rho2 = dx * dx + dy * dy + dz * dz;
     const double a2 = p.x * p.x + p.y * p.y;
@@ -200,7 +224,7 @@ k_observables(const typename A::C* __restrict__ psi, int lg, int offgrid, double
       const double sx = 0.5 * (p.x + r.x), sy = 0.5 * (p.y + r.y), mx = 0.5 * (p.x - r.x), my = 0.5 * (p.y - r.y);
       acc[7] += sx * sx + sy * sy;
       acc[8] += mx * mx + my * my;
-      auto at = [&](int64_t X, int64_t Y, int64_t Z) { return A::to_d2(psi[(X << (2 * lg)) + (Y << lg) + Z]); };
+      auto at = [&](int64_t X, int64_t Y, int64_t Z) { return A::to_d2(psi[lat_idx(L, X, Y, Z)]); };
       const double2 f1 = at(rx, y, z), f2 = at(x, ry, z), f3 = at(x, y, rz);        // one axis reflected
       const double2 g1 = at(x, ry, rz), g2 = at(rx, y, rz), g3 = at(rx, ry, z);     // the two others
       const double2 fk[3] = {f1, f2, f3}, gk[3] = {g1, g2, g3};
@@ -221,16 +245,17 @@ __global__ void k_convert(const typename AI::C* __restrict__ in, typename AO::C*
 }
 
 // ------------------------------------------------ finite-difference H_K(0)
-// H_K(0) psi at site idx of the 2^lg-cube lattice with psi = 0 outside it
+// H_K(0) psi at site idx of the n^3 lattice with psi = 0 outside it
 // (Eq. HK0 with Dirichlet boundaries, normalised as its momentum-space form,
 // Eq. HK0_momentum_space_1): c (6 psi - the sum of the six neighbours) with
 // c = 1 / (2 M A^2).  `self` receives psi at idx.
 template <class A>
-__device__ __forceinline__ typename A::C fdtd_sum(const typename A::C* __restrict__ psi, int64_t idx, int lg,
+__device__ __forceinline__ typename A::C fdtd_sum(const typename A::C* __restrict__ psi, int64_t idx, Lat L,
                                                   typename A::C& self) {
   using C = typename A::C;
-  const int64_t n = (int64_t)1 << lg, n2 = n * n;
-  const int64_t z = idx & (n - 1), y = (idx >> lg) & (n - 1), x = idx >> (2 * lg);
+  const int64_t n = L.n, n2 = n * n;
+  int64_t x, y, z;
+  lat_xyz(L, idx, x, y, z);
   const C zero{};
   self = psi[idx];
   C s = x > 0 ? psi[idx - n2] : zero;
@@ -242,9 +267,9 @@ __device__ __forceinline__ typename A::C fdtd_sum(const typename A::C* __restric
   return s;
 }
 template <class A>
-__device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict__ psi, int64_t idx, int lg,
+__device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict__ psi, int64_t idx, Lat L,
                                                  typename A::S c, typename A::C& self) {
-  const typename A::C s = fdtd_sum<A>(psi, idx, lg, self);
+  const typename A::C s = fdtd_sum<A>(psi, idx, L, self);
   return cscale(csub(cscale(self, A::scalar(6.0)), s), c);
 }
 
@@ -257,9 +282,9 @@ template <class A, int STATS>
 __global__ void __launch_bounds__(256)
 k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__ out,
               const typename A::K* __restrict__ coef, const double* __restrict__ V, const double* __restrict__ scale,
-              const float* __restrict__ scale_f, int lg, typename A::S c, double* __restrict__ part) {
+              const float* __restrict__ scale_f, Lat L, double* __restrict__ part) {
   using C = typename A::C;
-  const int64_t n3 = (int64_t)1 << (3 * lg);
+  const int64_t n3 = L.n * L.n * L.n;
   const bool scaled = scale != nullptr;
   typename A::S s{};
   if (scaled) s = A::load_scale(scale, scale_f);
@@ -271,7 +296,7 @@ k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__
 #pragma unroll U
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += (int64_t)gridDim.x * blockDim.x) {
     C self;
-    const C sum = fdtd_sum<A>(psi, idx, lg, self);
+    const C sum = fdtd_sum<A>(psi, idx, L, self);
     C nw = A::update(self, sum, coef[idx]);
     if (scaled) nw = cscale(nw, s);
     out[idx] = nw;
@@ -292,13 +317,13 @@ k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__
 // Per-CTA partials of <psi|H_K(0)|psi> (FP64 accumulation).
 template <class A>
 __global__ void __launch_bounds__(256)
-k_fdtd_energy(const typename A::C* __restrict__ psi, int lg, typename A::S c, double* __restrict__ part) {
+k_fdtd_energy(const typename A::C* __restrict__ psi, Lat L, typename A::S c, double* __restrict__ part) {
   using C = typename A::C;
-  const int64_t n3 = (int64_t)1 << (3 * lg);
+  const int64_t n3 = L.n * L.n * L.n;
   double e = 0.0;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n3; idx += (int64_t)gridDim.x * blockDim.x) {
     C self;
-    const C hk = fdtd_hk<A>(psi, idx, lg, c, self);
+    const C hk = fdtd_hk<A>(psi, idx, L, c, self);
     const double2 u = A::to_d2(self), h = A::to_d2(hk);
     e += u.x * h.x + u.y * h.y;
   }
@@ -325,15 +350,17 @@ struct GrfTaps {
   int r;
 };
 
-// Periodic convolution along one axis (stride 2^(lg * (2 - axis))): taps
-// wrapping past the lattice add up, which is the periodic sum of the Gaussian.
-__global__ void k_grf_conv(const double* __restrict__ in, double* __restrict__ out, int lg, int axis, GrfTaps taps) {
-  const int64_t n = (int64_t)1 << lg, n3 = n * n * n;
-  const int sh = lg * (2 - axis);
+// Periodic convolution along one axis (0: x, 1: y, 2: z): taps wrapping past
+// the lattice add up, which is the periodic sum of the Gaussian.
+__global__ void k_grf_conv(const double* __restrict__ in, double* __restrict__ out, Lat L, int axis, GrfTaps taps) {
+  const int64_t n = L.n, n3 = n * n * n;
+  const int64_t stride = axis == 0 ? n * n : axis == 1 ? n : 1;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = (i >> sh) & (n - 1), base = i - (c << sh);
+    int64_t xyz[3];
+    lat_xyz(L, i, xyz[0], xyz[1], xyz[2]);
+    const int64_t c = xyz[axis], base = i - c * stride;
     double acc = 0.0;
-    for (int j = -taps.r; j <= taps.r; ++j) acc += taps.g[j + taps.r] * in[base + (((c + j) & (n - 1)) << sh)];
+    for (int j = -taps.r; j <= taps.r; ++j) acc += taps.g[j + taps.r] * in[base + lat_wrap(L, c + j) * stride];
     out[i] = acc;
   }
 }
@@ -397,7 +424,7 @@ struct qfd_plan_s {
   KinParams kin{};
   int tune_vy[3] = {0, 0, 0};     // launch shapes per policy id (autotuner; see LaunchArgs)
   int tune_vz[3] = {-1, -1, -1};
-  int lg = 0;           // n = 2^lg
+  int lg = -1;          // n = 2^lg, or -1 (n = 96, 192)
   double fdtd_c = 0.0;  // 1 / (2 M A^2) of H_K(0)
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
   std::vector<int64_t> t;
@@ -688,11 +715,10 @@ qfd_status take_snapshot(qfd_plan_t pl) {
 template <class A>
 qfd_status fdtd_update(qfd_plan_t pl, int s, int stats) {
   const double* scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
-  const typename A::S c = host_scalar<A>(pl->fdtd_c);
   auto go = [&](auto kern) -> cudaError_t {
     kern<<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), spare_of<A>(pl),
                                         static_cast<const typename A::K*>(coef_of<A>(pl)), pl->V, scale, pl->scalf,
-                                        pl->lg, c, pl->partA);
+                                        Lat{pl->p.n, pl->lg}, pl->partA);
     return cudaGetLastError();
   };
   auto launch = [&]() -> cudaError_t {
@@ -712,7 +738,7 @@ qfd_status fdtd_update(qfd_plan_t pl, int s, int stats) {
 template <class A>
 qfd_status fdtd_energy_partials(qfd_plan_t pl, int s) {
   const typename A::S c = host_scalar<A>(pl->fdtd_c);
-  QFD_RUN(PASS_ZKIN, (k_fdtd_energy<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), pl->lg, c, pl->partC),
+  QFD_RUN(PASS_ZKIN, (k_fdtd_energy<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), Lat{pl->p.n, pl->lg}, c, pl->partC),
                       cudaGetLastError()));
   pl->nC = GS_BLOCKS;
   return QFD_OK;
@@ -1088,7 +1114,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   }
   const qfd_params& p = *params;
   if (!supported_n(p.n)) {
-    g_create_error = "n must be one of 8, 16, 32, 64, 128, 256, 512, 1024";
+    g_create_error = "n must be one of 8, 16, 32, 64, 96, 128, 192, 256, 512, 1024";
     return QFD_ERR_ARG;
   }
   if (!(p.a > 0) || !(p.mass > 0) || !(p.dtau > 0) || p.kinetic < 0 || p.kinetic > 3 || p.nstates < 1 ||
@@ -1142,7 +1168,9 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->p = p;
   pl->n3 = n * n * n;
   pl->kin = kin;
-  while (((int64_t)1 << pl->lg) < n) ++pl->lg;
+  if ((n & (n - 1)) == 0)
+    for (pl->lg = 0; ((int64_t)1 << pl->lg) < n; ++pl->lg) {
+    }
   pl->fdtd_c = 1.0 / (2.0 * p.mass * p.a * p.a);
   pl->t.assign(p.nstates, 0);
   pl->parity.assign(p.nstates, 0);
@@ -1294,9 +1322,9 @@ qfd_status qfd_add_random_field(qfd_plan_t pl, uint64_t seed, double corr, doubl
   pl->w_state = -1;
   const int g = grid_for(pl->n3);
   QFD_RUN(PASS_OTHER, (k_grf_noise<<<g, 256, 0, pl->st>>>(f0, pl->n3, seed), cudaGetLastError()));
-  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, pl->lg, 0, taps), cudaGetLastError()));
-  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f1, f0, pl->lg, 1, taps), cudaGetLastError()));
-  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, pl->lg, 2, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, Lat{pl->p.n, pl->lg}, 0, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f1, f0, Lat{pl->p.n, pl->lg}, 1, taps), cudaGetLastError()));
+  QFD_RUN(PASS_OTHER, (k_grf_conv<<<g, 256, 0, pl->st>>>(f0, f1, Lat{pl->p.n, pl->lg}, 2, taps), cudaGetLastError()));
   QFD_RUN(PASS_OTHER, (k_grf_moments<<<GS_BLOCKS, 256, 0, pl->st>>>(f1, pl->n3, pl->partG), cudaGetLastError()));
   qfd_status r = finalize(pl, pl->partG, 2, GS_BLOCKS, OP_SUMS);
   if (r != QFD_OK) return r;
@@ -1389,15 +1417,14 @@ qfd_status qfd_observables(qfd_plan_t pl, int s, double min_sep_edge, double* ou
   if (r != QFD_OK) return r;
   if (!out || nout < 1 || !(min_sep_edge >= 0.0) || !(min_sep_edge < 1.0))
     return fail(pl, QFD_ERR_ARG, "need an output buffer and 0 <= min_sep_edge < 1");
-  int lg = 0;
-  while (((int64_t)1 << lg) < pl->p.n) ++lg;
+  const Lat lat{pl->p.n, pl->lg};
   const double half = (1.0 - min_sep_edge) * (double)pl->p.n / 2.0;
   const int offgrid = pl->p.centre == QFD_CENTRE_OFFGRID;
   r = with_policy(pl->phase, [&](auto pol) -> qfd_status {
     using A = decltype(pol);
     qfd_status q = materialize<A>(pl, s);
     if (q != QFD_OK) return q;
-    QFD_RUN(PASS_OTHER, (k_observables<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), lg, offgrid, half, pl->partG),
+    QFD_RUN(PASS_OTHER, (k_observables<A><<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), lat, offgrid, half, pl->partG),
                          cudaGetLastError()));
     return finalize(pl, pl->partG, NOBS, GS_BLOCKS, OP_OBS);
   });
@@ -2029,6 +2056,7 @@ qfd_status qfd_server_stats(qfd_server_t sv, int* waiting, int* active, double* 
 
 namespace qfd {
 bool supported_n(int64_t n) {
-  return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+  return n == 8 || n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 ||
+         n == 1024;
 }
 }  // namespace qfd

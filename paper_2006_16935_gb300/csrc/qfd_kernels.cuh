@@ -305,15 +305,27 @@ struct DF {
 // ============================================================ FFT planning
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// N = 2^p: floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
+// E elements per thread and the radix schedule of a length-N transform.
+// N = 2^p: E = 8; floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
+// N = 12 * 2^p (96, 192): E = 12; one radix-12 stage, then floor(p/2) radix-4
+// stages and a radix-2 stage when p is odd (every radix divides E).
 template <int N> struct FftPlan {
-  static constexpr int P = ilog2c(N);
-  static constexpr int Q = P / 3;
-  static constexpr int REM = P % 3;
-  static constexpr int S = Q + (REM ? 1 : 0);
-  __host__ __device__ static constexpr int radix(int i) { return i < Q ? 8 : (REM == 1 ? 2 : 4); }
+  static constexpr bool R3 = N % 3 == 0;
+  static constexpr int E = R3 ? 12 : 8;
+  static constexpr int P = ilog2c(R3 ? N / 12 : N);
+  static constexpr int Q = R3 ? P / 2 : P / 3;
+  static constexpr int REM = R3 ? P % 2 : P % 3;
+  static constexpr int S = R3 ? 1 + Q + REM : Q + (REM ? 1 : 0);
+  __host__ __device__ static constexpr int radix(int i) {
+    return R3 ? (i == 0 ? 12 : (i <= Q ? 4 : 2)) : (i < Q ? 8 : (REM == 1 ? 2 : 4));
+  }
   __host__ __device__ static constexpr int ns(int i) { return i == 0 ? 1 : ns(i - 1) * radix(i - 1); }
 };
+
+// Complex constants in the representation of C.
+__device__ __forceinline__ double2 cconst(double re, double im, double2) { return double2{re, im}; }
+__device__ __forceinline__ float2 cconst(double re, double im, float2) { return float2{(float)re, (float)im}; }
+__device__ __forceinline__ dfc cconst(double re, double im, dfc) { return dfc{dsplit(re), dsplit(im)}; }
 
 template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
   C t = a;
@@ -327,6 +339,45 @@ template <int DIR, typename C> __device__ __forceinline__ void dft4(C& x0, C& x1
   x2 = csub_l(s0, s1);
   x1 = cadd_l(d0, d1);
   x3 = csub_l(d0, d1);
+}
+// DFT-3 with w = exp(DIR 2 pi i / 3): X0 = a + s, X1,2 = a - s/2 -+ DIR i (sqrt3/2) (b - c),
+// s = b + c (normalised sums; used by the radix-12 butterfly only).
+template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a, C& b, C& c) {
+  const C s = cadd(b, c), d = csub(b, c);
+  const C m = csub(a, cmul(s, cconst(0.5, 0.0, C{})));
+  const C r = mul_i<DIR>(cmul(d, cconst(0.86602540378443864676, 0.0, C{})));
+  a = cadd(a, s);
+  b = cadd(m, r);
+  c = csub(m, r);
+}
+// DFT-12 as 3 x 4 (Cooley-Tukey): DFT-3 over x[n2 + 4 n1] for each n2, the
+// factors w12^(n2 k1), DFT-4 over n2 for each k1; X[k1 + 3 k2].
+template <int DIR, typename C> __device__ __forceinline__ void dft12(C* x) {
+  C y[4][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C a = x[n2], b = x[n2 + 4], c = x[n2 + 8];
+    dft3<DIR>(a, b, c);
+    y[n2][0] = a;
+    y[n2][1] = b;
+    y[n2][2] = c;
+  }
+  const double h = 0.5, r3 = 0.86602540378443864676, sg = DIR > 0 ? 1.0 : -1.0;
+  y[1][1] = cmul(y[1][1], cconst(r3, sg * h, C{}));   // w12^1
+  y[1][2] = cmul(y[1][2], cconst(h, sg * r3, C{}));   // w12^2
+  y[2][1] = cmul(y[2][1], cconst(h, sg * r3, C{}));   // w12^2
+  y[2][2] = cmul(y[2][2], cconst(-h, sg * r3, C{}));  // w12^4
+  y[3][1] = mul_i<DIR>(y[3][1]);                      // w12^3
+  y[3][2] = cmul(y[3][2], cconst(-1.0, 0.0, C{}));    // w12^6
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C a = y[0][k1], b = y[1][k1], c = y[2][k1], d = y[3][k1];
+    dft4<DIR>(a, b, c, d);
+    x[k1] = a;
+    x[k1 + 3] = b;
+    x[k1 + 6] = c;
+    x[k1 + 9] = d;
+  }
 }
 template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
@@ -353,23 +404,25 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
 // instead of table loads (complex64 only; the z-pass, where the table loads
 // of its two transforms compete with its shared-memory exchanges).
 template <class A, int N, int RAD, int NS, int DIR, bool LAST, bool TWC = false>
-__device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw) {
+__device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N>::E], int t,
+                                              const typename A::C* __restrict__ tw) {
   using C = typename A::C;
-  constexpr int NB = 8 / RAD;
+  constexpr int E = FftPlan<N>::E;
+  constexpr int NB = E / RAD;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     C x[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) x[r] = v[u + r * NB];
     if (NS > 1) {
-      const int b = t + u * (N / 8);
+      const int b = t + u * (N / E);
       const int e0 = (b % NS) * (N / (NS * RAD));
       if constexpr (TWC && A::id == 1) {
         // w = exp(-2 pi i e0 / N) from sincospif, its powers by products
         // (a few ulp of FP32, like the rounding of the transform itself)
         float sn, cs;
         sincospif(-2.0f * (float)e0 / (float)N, &sn, &cs);
-        C w[8];
+        C w[RAD];
         w[1] = C{cs, sn};
 #pragma unroll
         for (int r = 2; r < RAD; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
@@ -383,6 +436,7 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, cons
         }
       }
     }
+    if constexpr (RAD == 12) dft12<DIR>(x);
     if (RAD == 8) dft8<DIR>(x);
     if (RAD == 4) dft4<DIR>(x[0], x[1], x[2], x[3]);
     if (RAD == 2) dft2<DIR>(x[0], x[1]);
@@ -393,23 +447,24 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[8], int t, cons
 
 // Writes stage outputs to their Stockham positions, then reads the canonical set.
 template <typename C, int N, int RAD, int NS, class Acc>
-__device__ __forceinline__ void stage_exchange(C (&v)[8], int t, Acc& acc) {
-  constexpr int NB = 8 / RAD;
+__device__ __forceinline__ void stage_exchange(C (&v)[FftPlan<N>::E], int t, Acc& acc) {
+  constexpr int E = FftPlan<N>::E;
+  constexpr int NB = E / RAD;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
-    const int b = t + u * (N / 8);
+    const int b = t + u * (N / E);
     const int base = (b / NS) * NS * RAD + (b % NS);
 #pragma unroll
     for (int r = 0; r < RAD; ++r) acc.at(base + r * NS) = v[u + r * NB];
   }
   acc.sync();
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = acc.at(t + m * (N / 8));
+  for (int m = 0; m < E; ++m) v[m] = acc.at(t + m * (N / E));
   acc.sync();
 }
 
 template <class A, int N, int DIR, int I, bool TWC, class Acc>
-__device__ __forceinline__ void fft_stages(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
+__device__ __forceinline__ void fft_stages(typename A::C (&v)[FftPlan<N>::E], int t, const typename A::C* __restrict__ tw,
                                            Acc& acc) {
   if constexpr (I < FftPlan<N>::S) {
     constexpr int RAD = FftPlan<N>::radix(I);
@@ -422,7 +477,7 @@ __device__ __forceinline__ void fft_stages(typename A::C (&v)[8], int t, const t
 
 // Unnormalised length-N DFT, sign DIR, canonical layout in and out.
 template <class A, int N, int DIR, class Acc, bool TWC = false>
-__device__ __forceinline__ void fft_line(typename A::C (&v)[8], int t, const typename A::C* __restrict__ tw,
+__device__ __forceinline__ void fft_line(typename A::C (&v)[FftPlan<N>::E], int t, const typename A::C* __restrict__ tw,
                                          Acc& acc) {
   fft_stages<A, N, DIR, 0, TWC>(v, t, tw, acc);
 }
@@ -491,14 +546,15 @@ template <typename C, int PS, int T> struct AccLine {
 #define QFD_LINE_TARGET8 128
 #endif
 template <int N, int CMIN> struct TileCols {
-  static constexpr int T = N / 8;
+  static constexpr int T = N / FftPlan<N>::E;
   static constexpr int C0 = (QFD_TILE_TARGET / T > CMIN) ? QFD_TILE_TARGET / T : CMIN;
   static constexpr int C1 = C0 < 1024 / T ? C0 : 1024 / T;
   static constexpr int value = C1 < N ? C1 : N;
 };
 template <class A, int N> struct Shape {
   static constexpr bool WIDE = sizeof(typename A::C) >= 16;
-  static constexpr int T = N / 8;  // threads per line
+  static constexpr int E = FftPlan<N>::E;  // elements per thread
+  static constexpr int T = N / E;          // threads per line
   static constexpr int XCOLS = TileCols<N, WIDE ? QFD_XCOLS_MIN16 : QFD_XCOLS_MIN8>::value;
   static constexpr int YCOLS = TileCols<N, WIDE ? QFD_YCOLS_MIN16 : QFD_YCOLS_MIN8>::value;
   static constexpr int XTHREADS = T * XCOLS;
@@ -514,7 +570,8 @@ template <class A, int N> struct Shape {
   static constexpr int ZG = (N * N / LINES) % ZG0 == 0 && N * N / LINES >= ZG0 ? ZG0 : 1;
   // the autotuner's alternatives: y tiles twice as wide (within 1024 threads
   // and N columns), z-pass line groups 1 or 2
-  static constexpr int YCOLS2 = 2 * YCOLS * T <= 1024 && 2 * YCOLS <= N ? 2 * YCOLS : YCOLS;
+  static constexpr int YCOLS2 = 2 * YCOLS * T <= 1024 && N % (2 * YCOLS) == 0 ? 2 * YCOLS : YCOLS;
+  static_assert(N % YCOLS == 0 && (N * N) % XCOLS == 0, "tiles must divide the lattice");
   static constexpr int ZG2 = (N * N / LINES) % 2 == 0 && N * N / LINES >= 2 ? 2 : 1;
   // one padding element per 128 bytes of a line
   static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
@@ -577,7 +634,7 @@ enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 // YC (the tile width) is a launch-shape choice of the autotuner; the
 // arithmetic of every column is the same for all widths.
 template <class A, int N, int DIR, int YC = Shape<A, N>::YCOLS>
-__global__ void __launch_bounds__(N / 8 * YC)
+__global__ void __launch_bounds__(N / FftPlan<N>::E * YC)
 k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
               int64_t outer_stride) {
   using C = typename A::C;
@@ -587,13 +644,13 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
   const int col = threadIdx.x % YC, t = threadIdx.x / YC;
   const int64_t base = (int64_t)(blockIdx.x / tiles_inner) * outer_stride +
                        (int64_t)(blockIdx.x % tiles_inner) * YC + col;
-  C v[8];
+  C v[SH::E];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
+  for (int m = 0; m < SH::E; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
   AccTile<C, YC, YC> acc{sm, col};
   fft_line<A, N, DIR>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
+  for (int m = 0; m < SH::E; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
 }
 
 // Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial when PARSEVAL),
@@ -613,9 +670,9 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   C* sm = reinterpret_cast<C*>(smraw);
   const int l = threadIdx.x / SH::T, t = threadIdx.x % SH::T;
   const int64_t line0 = (int64_t)blockIdx.x * SH::LINES * ZG + l;  // line = kx * N + ky
-  C v[8];
+  C v[SH::E];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = W[line0 * N + t + m * SH::T];
+  for (int m = 0; m < SH::E; ++m) v[m] = W[line0 * N + t + m * SH::T];
   static_assert(SH::T <= 32 || SH::LINES <= 15, "one named barrier per line");
   AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
   double pt = 0.0;
@@ -623,25 +680,25 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   for (int g = 0; g < ZG; ++g) {
     const int64_t line = line0 + (int64_t)g * SH::LINES;
     C* p = W + line * N;
-    C nx[8];
+    C nx[SH::E];
     if (g + 1 < ZG) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
+      for (int m = 0; m < SH::E; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
     }
     fft_line<A, N, -1, decltype(acc), true>(v, t, tw, acc);
     const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < SH::E; ++m) {
       const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
       if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
       v[m] = cscale(v[m], tk);
     }
     fft_line<A, N, +1, decltype(acc), true>(v, t, tw, acc);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) p[t + m * SH::T] = v[m];
+    for (int m = 0; m < SH::E; ++m) p[t + m * SH::T] = v[m];
     if (g + 1 < ZG) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) v[m] = nx[m];
+      for (int m = 0; m < SH::E; ++m) v[m] = nx[m];
     }
   }
   if constexpr (PARSEVAL) {
@@ -672,15 +729,15 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   // coefficients) are loaded before the inverse transform so that their
   // latency overlaps it
   constexpr bool EARLY_K = sizeof(C) == 8 || QFD_EARLY_COEF16;
-  C v[8], ps[8];
-  K cf[EARLY_K ? 8 : 1];
+  C v[SH::E], ps[SH::E];
+  K cf[EARLY_K ? SH::E : 1];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = W[base + (t + m * SH::T) * S];
+  for (int m = 0; m < SH::E; ++m) v[m] = W[base + (t + m * SH::T) * S];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
+  for (int m = 0; m < SH::E; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
   if constexpr (EARLY_K) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) cf[m] = coef[base + (t + m * SH::T) * S];
+    for (int m = 0; m < SH::E; ++m) cf[m] = coef[base + (t + m * SH::T) * S];
   }
   AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, +1>(v, t, tw, acc);
@@ -690,7 +747,7 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < SH::E; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
     C nw;
     if constexpr (EARLY_K) nw = A::update(ps[m], v[m], cf[m]);
@@ -707,7 +764,7 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   }
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
+  for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS != STATS_NONE) {
     if constexpr (STATS == STATS_NORM) n2 = nacc.value();
     double q[2] = {n2, pv};
@@ -733,11 +790,11 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   const bool scaled = scale != nullptr;
   typename A::S s{};
   if (scaled) s = A::load_scale(scale, scale_f);
-  C v[8];
+  C v[SH::E];
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < SH::E; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
     C x = src[idx];
     if (scaled) x = cscale(x, s);
@@ -751,12 +808,12 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   }
   if (psi_out) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) psi_out[base + (t + m * SH::T) * S] = v[m];
+    for (int m = 0; m < SH::E; ++m) psi_out[base + (t + m * SH::T) * S] = v[m];
   }
   AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
+  for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS != STATS_NONE) {
     if constexpr (STATS == STATS_NORM) n2 = nacc.value();
     double q[2] = {n2, pv};
@@ -776,7 +833,7 @@ struct LowerPtrs {
 // grid centre x -> (N - x) mod N, off-grid centre x -> N - 1 - x.
 template <int N>
 __device__ __forceinline__ int reflect1(int x, int offgrid) {
-  return offgrid ? N - 1 - x : (N - x) & (N - 1);
+  return offgrid ? N - 1 - x : (N - x) % N;
 }
 
 // Overlaps <phi_j | P psi> for j < k (P the parity projector of Eq. (parity),
@@ -787,14 +844,13 @@ __global__ void __launch_bounds__(256)
 k_gs_dots(const typename A::C* __restrict__ psi, LowerPtrs lower, int k, int parity, int offgrid,
           double* __restrict__ part) {
   using C = typename A::C;
-  constexpr int LG = ilog2c(N);
   constexpr int64_t N3 = (int64_t)N * N * N;
   typename A::Dot acc[MAX_LOWER];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N3; i += (int64_t)gridDim.x * blockDim.x) {
     C p = psi[i];
     if (parity) {
-      const int z = (int)(i & (N - 1)), y = (int)((i >> LG) & (N - 1)), x = (int)(i >> (2 * LG));
-      const int64_t ri = ((int64_t)reflect1<N>(x, offgrid) << (2 * LG)) + ((int64_t)reflect1<N>(y, offgrid) << LG) +
+      const int z = (int)(i % N), y = (int)((i / N) % N), x = (int)(i / ((int64_t)N * N));
+      const int64_t ri = ((int64_t)reflect1<N>(x, offgrid) * N + reflect1<N>(y, offgrid)) * N +
                          reflect1<N>(z, offgrid);
       p = A::half_comb(p, psi[ri], parity);
     }
@@ -840,17 +896,17 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
       if (j < k) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
   }
   // every load of the state and of its reflection is issued before any use
-  C v[8], rv[8];
+  C v[SH::E], rv[SH::E];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = src[base + (t + m * SH::T) * S];
+  for (int m = 0; m < SH::E; ++m) v[m] = src[base + (t + m * SH::T) * S];
   if (parity) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) rv[m] = src[rbase + (int64_t)reflect1<N>(t + m * SH::T, offgrid) * S];
+    for (int m = 0; m < SH::E; ++m) rv[m] = src[rbase + (int64_t)reflect1<N>(t + m * SH::T, offgrid) * S];
   }
   typename A::Acc nacc;
   double n2 = 0.0, pv = 0.0;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < SH::E; ++m) {
     const int x = t + m * SH::T;
     const int64_t idx = base + x * S;
     C p = v[m];
@@ -870,7 +926,7 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
   AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) W[base + (t + m * SH::T) * S] = v[m];
+  for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS != STATS_NONE) {
     if constexpr (STATS == STATS_NORM) n2 = nacc.value();
     double q[2] = {n2, pv};

@@ -83,7 +83,9 @@ inline cudaError_t dispatch_n(int64_t n, F&& f) {
     case 16: return f(Tag<16>());
     case 32: return f(Tag<32>());
     case 64: return f(Tag<64>());
+    case 96: return f(Tag<96>());
     case 128: return f(Tag<128>());
+    case 192: return f(Tag<192>());
     case 256: return f(Tag<256>());
     case 512: return f(Tag<512>());
     case 1024: return f(Tag<1024>());

@@ -7,9 +7,12 @@
 
 namespace qfd {
 
+// Opts in to more than the default 48 KB of shared memory per CTA when the
+// dynamic part, together with the kernels' static reduction buffers (a few
+// KB), could exceed it.
 template <class K>
 static void ensure_smem(K kern, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 40 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <class A, int N>
@@ -56,7 +59,7 @@ cudaError_t Launch<A, N>::fft_y(const LaunchArgs& a, int dir) {
     const size_t smem = (size_t)N * yc * sizeof(C);
     const int tiles_inner = N / yc;
     ensure_smem(kern, smem);
-    kern<<<N * tiles_inner, N / 8 * yc, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
+    kern<<<N * tiles_inner, SH::T * yc, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
                                                           (int64_t)N * N);
   };
   if (a.vy == 1) {

@@ -61,7 +61,7 @@ def poisson_stream(count: int, *, rate: float = 20.0, seed: int = 5, sizes=SIZES
     return out
 
 
-def batch_stream(count: int, *, seed: int = 4, sizes=(64, 128), a: float = 0.1, courant: float = 0.5,
+def batch_stream(count: int, *, seed: int = 4, sizes=(64, 96, 128, 192), a: float = 0.1, courant: float = 0.5,
                  tol: float = 1e-9, grf_corr: float = 4.0, grf_amplitude: float = 0.05, max_steps: int = 400000):
     """`count` independent solves, all present at time 0: n uniform over
     `sizes`; Cornell V = -alpha/r + sigma r with alpha U[0.1,0.5], sigma

@@ -82,7 +82,7 @@ def test_potential_fill_matches_oracle(qfdlib, kind, coeffs, centre):
 @pytest.mark.parametrize("prec", FP64_CLASS)
 @pytest.mark.parametrize("nsteps", [10, 12])
 @pytest.mark.parametrize("kin", [1, 2, 3])
-@pytest.mark.parametrize("n", [8, 16, 32, 64])
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 96])
 def test_step_parity_fp64_class(qfdlib, n, kin, nsteps, prec):
     a, m = 0.1, 1.3
     dt = stable_dt(n, a, m, kin)
@@ -163,7 +163,7 @@ def test_parity_sector_is_kept_by_steps(qfdlib, centre, parity):
 
 @pytest.mark.parametrize("prec", FP64_CLASS)
 @pytest.mark.parametrize("kin", [1, 2, 3])
-@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("n", [16, 64, 96])
 def test_energy_parity(qfdlib, n, kin, prec):
     a, m = 0.1, 1.0
     V = O.potential(n, a, "softcoul", (0.01,))
@@ -323,7 +323,7 @@ def test_snapshot_states_argument_errors(qfdlib):
 # ------------------------------------------------------------- complex64 ----
 
 @pytest.mark.parametrize("kin", [1, 2, 3])
-@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("n", [16, 64, 96])
 def test_step_parity_c64(qfdlib, n, kin):
     a, m = 0.1, 1.3
     dt = stable_dt(n, a, m, kin)
@@ -421,3 +421,69 @@ def test_random_field_potential_solve_matches_oracle(qfdlib):
                         20000, 1e-10)
     assert steps[0] == res.steps
     assert abs(es[0] - res.energy) <= TOL_E * abs(res.energy)
+
+
+# ------------------------------------------------- radix-12 lattices (96, 192)
+
+@pytest.mark.parametrize("prec", FP64_CLASS + ["c64"])
+def test_radix12_lattice_projection_observables_and_fields(qfdlib, prec):
+    # N = 96 (12 elements per thread, radix 12-4-2): parity projection with
+    # Gram-Schmidt, the observables and a random field at a lattice that is
+    # not a power of two
+    n, a, m, kin = 96, 0.1, 1.5, 3
+    dt = stable_dt(n, a, m, kin)
+    V = O.potential(n, a, "cornell", (0.3, 0.2)) + O.random_field(inputs.gaussian_noise(n, 3), 4.0, 0.05)
+    phi0 = O.normalize(inputs.uniform_psi(n, 1))
+    psi = inputs.uniform_psi(n, 2)
+    if prec == "df64":
+        phi0 = df_round(phi0)
+    with Q.Plan(n, a, m, dt, kin, nstates=2, ortho_every=3, precision=prec) as p:
+        p.fill_potential("cornell", (0.3, 0.2))
+        p.add_random_field(3, 4.0, 0.05)
+        assert np.max(np.abs(p.get_potential() - V)) < 1e-12
+        p.set_psi(0, phi0)
+        p.set_psi(1, psi)
+        p.set_parity(1, -1)
+        p.step(1, 6)
+        got = p.get_psi(1)
+        lower = p.get_psi(0)
+        ob = p.observables(1, 0.3)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=3)
+    ref, _ = O.evolve(psi, prob, 6, parity=-1, lower=(lower,))
+    assert rel_l2(got, ref) < (TOL_PSI if prec != "c64" else 2e-6)
+    want = O.observables(got, "grid", 0.3)
+    for k, v in want.items():
+        assert ob[k] == pytest.approx(v, rel=1e-12, abs=1e-12), k
+
+
+@pytest.mark.parametrize("prec", FP64_CLASS)
+def test_radix12_192_steps_match_library_oracle(qfdlib, prec):
+    n, a, m, kin = 192, 0.05, 1.0, 2
+    dt = stable_dt(n, a, m, kin)
+    V = O.potential(n, a, "softcoul", (0.01,))
+    psi0 = inputs.uniform_psi(n, 8)
+    with Q.Plan(n, a, m, dt, kin, ortho_every=4, precision=prec) as p:
+        p.set_potential(V)
+        p.set_psi(0, psi0)
+        p.step(0, 6)
+        got = p.get_psi(0)
+        e, _ = p.energy(0)
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=4, method="library")
+    ref, _ = O.evolve(psi0, prob, 6)
+    assert rel_l2(got, ref) < TOL_PSI
+    e_ref = O.energy(ref, V, prob.T, "library")
+    assert abs(e - e_ref) <= TOL_E * abs(e_ref)
+
+
+def test_radix12_fdtd_step(qfdlib):
+    n, a, m = 96, 0.1, 1.3
+    dt = 0.9 / O.kinetic_max(n, a, m, 0)
+    V = O.potential(n, a, "ho", (1.0,), "offgrid")
+    psi0 = inputs.uniform_psi(n, 5)
+    with Q.Plan(n, a, m, dt, 0, ortho_every=5, centre="offgrid") as p:
+        p.set_potential(V)
+        p.set_psi(0, psi0)
+        p.step(0, 10)
+        got = p.get_psi(0)
+    ref, _ = O.evolve(psi0, O.Problem(n, a, m, dt, 0, V, ortho_every=5, centre="offgrid"), 10)
+    assert rel_l2(got, ref) < TOL_PSI
