@@ -85,3 +85,28 @@ def test_short_requests_overtake_a_long_one(qfdlib):
         assert res[i]["status"] == 0
         assert res[i]["t_admit"] < res[lid]["t_done"]
         assert res[i]["t_done"] < res[lid]["t_done"]
+
+
+def test_server_serves_fdtd_radix12_and_random_field_requests(qfdlib):
+    """Requests with the finite-difference kinetic term, a 96^3 (radix-12)
+    lattice and a random-field potential give the numbers of the same solve
+    through a plan."""
+    reqs = [
+        dict(n=16, a=0.35, mass=1.5, dtau=0.0075, kinetic=0, nstates=2, precision="df64", potential="cornell",
+             pot_coeffs=(0.3, 0.2), centre="offgrid", parity=[1, -1], seed=31, tol=1e-9, max_steps=20000),
+        dict(n=96, a=0.2, mass=2.0, dtau=0.01, kinetic=2, nstates=1, precision="c64_refine_df", potential="ho",
+             pot_coeffs=(1.0, 0.0), seed=32, tol=1e-9, max_steps=40000, grf=(5, 4.0, 0.05)),
+    ]
+    mix, _ = run_server(reqs)
+    for req, got in zip(reqs, mix):
+        assert got["status"] == 0
+        kw = dict(nstates=req["nstates"], precision=req["precision"], ortho_every=ORTHO, check_every=CHECK,
+                  max_steps=req["max_steps"], tol=req["tol"], tol_bulk=1e-10, centre=req.get("centre", "grid"))
+        with Q.Plan(req["n"], req["a"], req["mass"], req["dtau"], req["kinetic"], **kw) as p:
+            p.fill_potential(req["potential"], req["pot_coeffs"])
+            if "grf" in req:
+                p.add_random_field(*req["grf"])
+            for s in range(req["nstates"]):
+                p.fill_psi_uniform(s, req["seed"] + s)
+            es, steps, _ = p.solve_states(req["nstates"], req.get("parity"))
+        assert got["energy"] == es and got["steps"] == steps
