@@ -401,8 +401,9 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
 // Butterfly b = t + u N/8 (u < 8/RAD) takes x[b + r N/RAD] = v[u + r (8/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
 // TWC: the twiddles of a stage from one sincospif and products of powers
-// instead of table loads (complex64 only; the z-pass, where the table loads
-// of its two transforms compete with its shared-memory exchanges).
+// instead of table loads (complex64 only; used where the table loads compete
+// with the shared-memory exchanges for the L1 pipe: the z-pass and the
+// inverse y pass).
 template <class A, int N, int RAD, int NS, int DIR, bool LAST, bool TWC = false>
 __device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N>::E], int t,
                                               const typename A::C* __restrict__ tw) {
@@ -648,7 +649,9 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
   AccTile<C, YC, YC> acc{sm, col};
-  fft_line<A, N, DIR>(v, t, tw, acc);
+  // complex64 inverse y pass: computed twiddles (measured faster there; the
+  // forward y pass is faster with the table)
+  fft_line<A, N, DIR, decltype(acc), (DIR > 0)>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
 }
