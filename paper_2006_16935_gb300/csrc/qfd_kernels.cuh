@@ -876,7 +876,9 @@ k_gs_dots(const typename A::C* __restrict__ psi, LowerPtrs lower, int k, int par
 // is written to dst (a different buffer than src: other CTAs still read the
 // reflected sites of src) and its forward DFT_x to W; partials per STATS of
 // psi'.  The normalisation is applied by the next pass A.
-template <class A, int N, int STATS>
+// LOWER: whether there are lower states (k > 0); the parity-only instance
+// carries no Gram-Schmidt code at all.
+template <class A, int N, int STATS, bool LOWER = true>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double* __restrict__ sums, int k, int parity,
             int offgrid, typename A::C* __restrict__ dst, typename A::C* __restrict__ W, const double* __restrict__ V,
@@ -893,7 +895,7 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
   // the overlaps in the policy's representation (converted only when there
   // are lower states: conversions from FP64 run on the slow FP64 pipe)
   C cc[MAX_LOWER];
-  if (k > 0) {
+  if (LOWER && k > 0) {
 #pragma unroll
     for (int j = 0; j < MAX_LOWER; ++j)
       if (j < k) cc[j] = A::from_d2(double2{sums[2 * j], sums[2 * j + 1]});
@@ -916,7 +918,7 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
     if (parity) p = A::half_comb(p, rv[m], parity);
 #pragma unroll
     for (int j = 0; j < MAX_LOWER; ++j)
-      if (j < k) p = csub(p, cmul(static_cast<const C*>(lower.p[j])[idx], cc[j]));
+      if (LOWER && j < k) p = csub(p, cmul(static_cast<const C*>(lower.p[j])[idx], cc[j]));
     dst[idx] = p;
     v[m] = p;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(p);

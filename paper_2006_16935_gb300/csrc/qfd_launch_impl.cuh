@@ -112,8 +112,13 @@ cudaError_t Launch<A, N>::project_x(const LaunchArgs& a, int* nblocks) {
     kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, lp, a.sums, a.k, a.parity, a.offgrid,
                                                       (C*)a.dst, (C*)a.W, a.V, (const C*)a.tw, a.part);
   };
-  if (a.stats == STATS_FULL) go(k_project_x<A, N, STATS_FULL>);
-  else go(k_project_x<A, N, STATS_NORM>);
+  if (a.k > 0) {
+    if (a.stats == STATS_FULL) go(k_project_x<A, N, STATS_FULL, true>);
+    else go(k_project_x<A, N, STATS_NORM, true>);
+  } else {
+    if (a.stats == STATS_FULL) go(k_project_x<A, N, STATS_FULL, false>);
+    else go(k_project_x<A, N, STATS_NORM, false>);
+  }
   if (nblocks) *nblocks = grid;
   return cudaGetLastError();
 }
