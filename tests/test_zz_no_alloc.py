@@ -17,6 +17,7 @@ CASES = [  # n, a, mass, kinetic, rest_mass, potential, seed
     (32, 0.1, 1.0, 2, 0, ("softcoul", (0.01,)), 5),
     (64, 0.05, 1.5, 3, 0, ("cornell", (0.3, 0.2)), 6),
     (128, 0.05, 2.0, 1, 0, ("ho", (1.0,)), 7),
+    (96, 0.1, 1.2, 2, 0, ("cornell", (0.3, 0.2)), 8),  # radix-12 transforms
 ]
 
 
@@ -32,7 +33,7 @@ def test_noalloc_energy_matches_plan_energy(qfdlib):
     import torch
 
     refs = [plan_energy(*c) for c in CASES]
-    order = [0, 1, 2, 0]  # two different calls in a row, then a repeat
+    order = [0, 1, 3, 2, 0]  # different calls in a row, then a repeat
     for i in order:
         n, a, mass, kin, rest, _, _ = CASES[i]
         e_ref, n2_ref, psi, V = refs[i]
