@@ -43,3 +43,17 @@ def test_summary_of_records():
     assert s["p50_s"] == 1.0 and s["p99_s"] == 1.0 and s["requests"] == 10 and s["ok"] == 10
     assert math.isclose(s["makespan_s"], 1.9) and math.isclose(s["solves_per_s"], 10 / 1.9)
     assert math.isclose(s["site_updates_per_s"], 10 * 64 ** 3 * 100 / 1.9)
+
+
+def test_batch_stream_is_seeded_and_shaped():
+    a = serve.batch_stream(64)
+    assert a == serve.batch_stream(64)
+    assert all(t == 0.0 for t, _ in a)
+    sizes = {r["n"] for _, r in a}
+    assert sizes == {64, 96, 128, 192}
+    for _, r in a:
+        assert r["a"] == 0.1 and r["stop_rule"] == "tail" and "parity" not in r
+        seed, corr, amp = r["grf"]
+        assert corr == 4.0 and amp == 0.05
+        assert abs(r["dtau"] * serve.kinetic_max(r["kinetic"], r["a"], r["mass"], 0) - 1.0) < 1e-12
+    assert len({r["grf"][0] for _, r in a}) == 64  # one field per solve
