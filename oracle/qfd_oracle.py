@@ -136,6 +136,17 @@ def kinetic_symbol(n: int, a: float, mass: float, kinterm: int, rest_mass: int =
     """
     k = k_modes(n)
     k1, k2, k3 = np.meshgrid(k, k, k, indexing="ij")
+    return _symbol(k1, k2, k3, a, mass, kinterm, rest_mass)
+
+
+def kinetic_symbol_at(n: int, a: float, mass: float, kinterm: int, idx: np.ndarray, rest_mass: int = 0) -> np.ndarray:
+    """T(k) at the DFT index triples idx[:, 0..2] (the same formulas as
+    kinetic_symbol, without building the whole N^3 table)."""
+    k = k_modes(n)
+    return _symbol(k[idx[:, 0]], k[idx[:, 1]], k[idx[:, 2]], a, mass, kinterm, rest_mass)
+
+
+def _symbol(k1, k2, k3, a, mass, kinterm, rest_mass):
     if kinterm == 1:
         return (k1 ** 2 + k2 ** 2 + k3 ** 2) / (2.0 * a * a * mass)
     s = 4.0 * (np.sin(k1 / 2) ** 2 + np.sin(k2 / 2) ** 2 + np.sin(k3 / 2) ** 2)

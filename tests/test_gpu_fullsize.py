@@ -72,3 +72,40 @@ def test_random_state_steps_256_against_library_fft_oracle(qfdlib, prec, tol):
     prob = O.Problem(n, a, m, dt, kin, V, ortho_every=2, method="library")
     ref, _ = O.evolve(psi0, prob, 3, parity=1)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("df64", 1e-11), ("c64", 3e-6)])
+def test_plane_wave_step_1024(qfdlib, prec, tol):
+    # the largest lattice: 2^30 sites (17 GB per 16-byte lattice).  psi is built
+    # on the device with torch (slab by slab) and read back on the device; V = 0,
+    # so one step maps a plane wave to (1 - dtau T(k)) times itself
+    import torch
+
+    n, a, m, kin, dt = 1024, 0.05, 1.0, 2, 2.5e-4
+    idx, amp = inputs.plane_wave_mix(n, 6, modes=3)
+    dev = torch.device("cuda")
+    x = torch.arange(n, device=dev, dtype=torch.float64)
+    psi = torch.zeros((n, n, n), dtype=torch.complex128, device=dev)
+    for (i1, i2, i3), c in zip(idx, amp):
+        e = [torch.exp(2j * np.pi * int(i) * x / n) for i in (i1, i2, i3)]
+        yz = e[1][:, None] * e[2][None, :]
+        for s0 in range(0, n, 128):
+            psi[s0:s0 + 128] += complex(c) * e[0][s0:s0 + 128, None, None] * yz[None, :, :]
+        del yz
+    with Q.Plan(n, a, m, dt, kin, precision=prec, ortho_every=1000) as p:
+        p.fill_potential("zero", ())
+        p.set_psi(0, psi.view(-1))
+        p.step(0, 1)
+        p.get_psi(0, psi.view(-1))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    sites = rng.integers(0, n, size=(4096, 3))
+    sites[0] = [n - 1, n - 1, n - 1]
+    got = psi[sites[:, 0], sites[:, 1], sites[:, 2]].cpu().numpy()
+    del psi
+    T = O.kinetic_symbol_at(n, a, m, kin, idx)
+    phase = np.exp(2j * np.pi * (sites @ idx.T) / n)
+    expect = phase @ (amp * (1.0 - dt * T))
+    err = np.max(np.abs(got - expect)) / np.max(np.abs(expect))
+    assert err < tol
+

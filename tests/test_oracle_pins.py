@@ -669,3 +669,13 @@ def test_random_field_normalisation_and_noise_statistics():
     assert corr == pytest.approx(math.exp(-1 / 64), abs=0.01)
     assert np.max(np.abs(O.random_field(3 * noise, 4.0, 0.05) - f)) < 1e-15
 
+
+def test_kinetic_symbol_at_indices_is_the_table():
+    n = 12
+    idx = np.array([[0, 0, 0], [6, 6, 6], [1, 11, 5], [3, 7, 2]])
+    for kin in (1, 2, 3):
+        for rest in (0, 1):
+            T = O.kinetic_symbol(n, 0.3, 1.7, kin, rest)
+            got = O.kinetic_symbol_at(n, 0.3, 1.7, kin, idx, rest)
+            assert np.array_equal(got, T[idx[:, 0], idx[:, 1], idx[:, 2]])
+
