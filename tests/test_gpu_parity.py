@@ -487,3 +487,47 @@ def test_radix12_fdtd_step(qfdlib):
         got = p.get_psi(0)
     ref, _ = O.evolve(psi0, O.Problem(n, a, m, dt, 0, V, ortho_every=5, centre="offgrid"), 10)
     assert rel_l2(got, ref) < TOL_PSI
+
+
+# ------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("prec", FP64_CLASS)
+def test_eight_states_the_largest_stack(qfdlib, prec):
+    # the deepest Gram-Schmidt: state 7 deflated against seven lower states
+    n, a, m, kin = 8, 0.5, 1.0, 2
+    dt = stable_dt(n, a, m, kin, 0.5)
+    V = aniso_potential(n, a)
+    with Q.Plan(n, a, m, dt, kin, nstates=8, ortho_every=5, check_every=25, max_steps=40000, tol=1e-10,
+                precision=prec) as p:
+        p.set_potential(V)
+        for s in range(8):
+            p.fill_psi_uniform(s, 300 + s)
+        es, steps, conv = p.solve_states(8)
+        psis = [p.get_psi(s) for s in range(8)]
+    prob = O.Problem(n, a, m, dt, kin, V, ortho_every=5, check_every=25)
+    res = O.solve_states([inputs.uniform_psi(n, 300 + s) for s in range(8)], prob, 40000, 1e-10)
+    for s in range(8):
+        assert steps[s] == res[s].steps
+        assert abs(es[s] - res[s].energy) <= TOL_E * abs(res[s].energy)
+    gram = np.array([[O.inner(psis[i], psis[j]) for j in range(8)] for i in range(8)])
+    assert np.max(np.abs(gram - np.eye(8))) < 1e-12
+
+
+def aniso_potential(n, a):
+    # anisotropic oscillator: no degenerate levels among the lowest eight
+    d = O.displacement(n)
+    d1, d2, d3 = np.meshgrid(d, d, d, indexing="ij")
+    return 0.5 * a * a * (1.0 * d1 ** 2 + 2.3 * d2 ** 2 + 5.1 * d3 ** 2)
+
+
+def test_zero_steps_and_tiny_cases(qfdlib):
+    n = 8
+    psi = inputs.uniform_psi(n, 3)
+    with Q.Plan(n, 0.5, 1.0, 0.01, 2, max_steps=0) as p:
+        p.fill_potential("ho", (1.0,))
+        p.set_psi(0, psi)
+        p.step(0, 0)  # no steps: the state is untouched
+        assert np.array_equal(p.get_psi(0), psi)
+        with pytest.raises(Q.QfdError) as ei:  # max_steps 0: no check, not converged
+            p.solve_states(1)
+        assert ei.value.status == Q.ERR_NOT_CONVERGED

@@ -110,3 +110,11 @@ def test_server_serves_fdtd_radix12_and_random_field_requests(qfdlib):
                 p.fill_psi_uniform(s, req["seed"] + s)
             es, steps, _ = p.solve_states(req["nstates"], req.get("parity"))
         assert got["energy"] == es and got["steps"] == steps
+
+
+def test_request_that_never_fits_ends_with_oom(qfdlib):
+    big = dict(REQS[1], n=64)
+    budget = 0.5 * Q.plan_bytes(64, big["precision"], big["nstates"])
+    res, _ = run_server([big, REQS[3]], budget=max(budget, 1.5 * Q.plan_bytes(8, "c64_refine", 3)))
+    assert res[0]["status"] == Q.ERR_OOM
+    assert res[1]["status"] == 0
