@@ -307,8 +307,8 @@ k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__
       pv += V[idx] * a2;
     }
   }
-  if constexpr (STATS != STATS_NONE) {
-    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+  if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
+  if constexpr (STATS == STATS_FULL) {
     double q[2] = {n2, pv};
     block_reduce_store<2>(q, part);
   }

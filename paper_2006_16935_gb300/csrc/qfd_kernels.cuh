@@ -621,6 +621,49 @@ __device__ __forceinline__ void block_reduce_store(double (&val)[NQ], double* __
   }
 }
 
+// The STATS_NORM partial of a CTA (part[blockIdx.x], with 0 for the second
+// quantity at part[gridDim.x + blockIdx.x]).  For the FP32-pipe policies the
+// per-thread exact double-float sums are reduced in double-float and turned
+// into FP64 once per CTA: FP64 instructions issue at a small fraction of the
+// FP32 rate on this GPU, and a per-thread conversion and FP64 shuffle tree
+// cost as much as a thread's share of a transform.
+template <class A>
+__device__ __forceinline__ void norm_reduce_store(const typename A::Acc& acc, double* __restrict__ part) {
+  if constexpr (A::id == 0) {
+    double q[2] = {acc.value(), 0.0};
+    block_reduce_store<2>(q, part);
+  } else {
+    __shared__ df red[32];
+    df s = acc.s;
+    if (blockDim.x < 32) {
+      red[threadIdx.x] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)blockDim.x; ++i) s = dadd(s, red[i]);
+        part[blockIdx.x] = dval(s);
+        part[gridDim.x + blockIdx.x] = 0.0;
+      }
+      return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+      s = lane < nw ? red[lane] : df{0.f, 0.f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
+      if (lane == 0) {
+        part[blockIdx.x] = dval(s);
+        part[gridDim.x + blockIdx.x] = 0.0;
+      }
+    }
+  }
+}
+
 // Partial-sum modes of the passes that write psi (pass A and forward x):
 //   STATS_NONE  no reduction (the common step)
 //   STATS_NORM  sum |psi|^2 (steps that end in a normalisation)
@@ -768,8 +811,8 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
-  if constexpr (STATS != STATS_NONE) {
-    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+  if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
+  if constexpr (STATS == STATS_FULL) {
     double q[2] = {n2, pv};
     block_reduce_store<2>(q, part);
   }
@@ -817,8 +860,8 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
-  if constexpr (STATS != STATS_NONE) {
-    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+  if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
+  if constexpr (STATS == STATS_FULL) {
     double q[2] = {n2, pv};
     block_reduce_store<2>(q, part);
   }
@@ -932,8 +975,8 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
-  if constexpr (STATS != STATS_NONE) {
-    if constexpr (STATS == STATS_NORM) n2 = nacc.value();
+  if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
+  if constexpr (STATS == STATS_FULL) {
     double q[2] = {n2, pv};
     block_reduce_store<2>(q, part);
   }
