@@ -124,13 +124,15 @@ __global__ void k_potential(double* __restrict__ V, int64_t n, double a, int kin
 }
 
 // Update coefficients of Sec. 2.2 from V, per arithmetic: FP64 {A, B dtau};
-// FP32 and double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64.
+// FP32 and double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64;
+// and, for plans with an FP32-pipe arithmetic, V split into double-float
+// pairs (the energy sums of those arithmetics read it).
 // fdtd_c > 0 (H_K(0) plans, c = 1 / (2 M A^2)): the coefficients take the
 // stencil's diagonal in, so that the update applied to the neighbour sum S
 // gives A psi - B dtau c (6 psi - S) = (A - 6 c B dtau) psi + c B dtau S.
 __global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double fdtd_c,
                        double2* __restrict__ c64, dfc* __restrict__ cdf, float2* __restrict__ c32,
-                       int* __restrict__ bad) {
+                       df* __restrict__ vdf, int* __restrict__ bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i];
     const double h = 0.5 * dtau * v;
@@ -146,6 +148,7 @@ __global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, do
     if (c64) c64[i] = double2{a64, g1};
     if (cdf) cdf[i] = dfc{dsplit(g1), dsplit(g2)};
     if (c32) c32[i] = float2{(float)g1, (float)g2};
+    if (vdf) vdf[i] = dsplit(v);
   }
 }
 
@@ -281,15 +284,15 @@ __device__ __forceinline__ typename A::C fdtd_hk(const typename A::C* __restrict
 template <class A, int STATS>
 __global__ void __launch_bounds__(256)
 k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__ out,
-              const typename A::K* __restrict__ coef, const double* __restrict__ V, const double* __restrict__ scale,
-              const float* __restrict__ scale_f, Lat L, double* __restrict__ part) {
+              const typename A::K* __restrict__ coef, const typename A::VT* __restrict__ V,
+              const double* __restrict__ scale, const float* __restrict__ scale_f, Lat L, double* __restrict__ part) {
   using C = typename A::C;
   const int64_t n3 = L.n * L.n * L.n;
   const bool scaled = scale != nullptr;
   typename A::S s{};
   if (scaled) s = A::load_scale(scale, scale_f);
   typename A::Acc nacc;
-  double n2 = 0.0, pv = 0.0;
+  typename A::Full facc;
   // sites per thread unrolled in the stencil loop (measured at 512^3: four
   // for the 16-byte arithmetics, one for complex64)
   constexpr int U = A::id == 1 ? 1 : 4;
@@ -301,17 +304,10 @@ k_fdtd_update(const typename A::C* __restrict__ psi, typename A::C* __restrict__
     if (scaled) nw = cscale(nw, s);
     out[idx] = nw;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
-    if constexpr (STATS == STATS_FULL) {
-      const double a2 = A::norm2_d(nw);
-      n2 += a2;
-      pv += V[idx] * a2;
-    }
+    if constexpr (STATS == STATS_FULL) facc.add(nw, V[idx]);
   }
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
-  if constexpr (STATS == STATS_FULL) {
-    double q[2] = {n2, pv};
-    block_reduce_store<2>(q, part);
-  }
+  if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }
 
 // Per-CTA partials of <psi|H_K(0)|psi> (FP64 accumulation).
@@ -405,6 +401,7 @@ struct qfd_plan_s {
   void* coef16 = nullptr;   // F64 {A, B dtau} or DF {B dtau, 1 - A}
   float2* coef32 = nullptr;
   double* V = nullptr;
+  df* Vdf = nullptr;        // V as double-float pairs (plans with an FP32-pipe arithmetic)
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   dfc* twdf = nullptr;
@@ -545,6 +542,11 @@ template <class A> typename A::S host_scalar(double x) {
   else if constexpr (A::id == 1) return (float)x;
   else return host_split(x);
 }
+// V as the policy's energy sums read it (FP64, or the double-float copy)
+template <class A> const typename A::VT* v_of(qfd_plan_t pl) {
+  if constexpr (A::id == 0) return pl->V;
+  else return pl->Vdf;
+}
 template <class A> const void* coef_of(qfd_plan_t pl) { return A::id == 1 ? (const void*)pl->coef32 : pl->coef16; }
 template <class A> const void* tw_of(qfd_plan_t pl) {
   return A::id == 0 ? (const void*)pl->tw64 : A::id == 1 ? (const void*)pl->tw32 : (const void*)pl->twdf;
@@ -570,7 +572,7 @@ LaunchArgs base_args(qfd_plan_t pl) {
   a.ktab = ktab_of<A>(pl);
   a.kin = &pl->kin;
   a.coef = coef_of<A>(pl);
-  a.V = pl->V;
+  a.V = v_of<A>(pl);
   a.err = pl->errflag;
   a.stream = pl->st;
   a.vy = pl->tune_vy[A::id];
@@ -717,7 +719,7 @@ qfd_status fdtd_update(qfd_plan_t pl, int s, int stats) {
   const double* scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
   auto go = [&](auto kern) -> cudaError_t {
     kern<<<GS_BLOCKS, 256, 0, pl->st>>>(psi_of<A>(pl, s), spare_of<A>(pl),
-                                        static_cast<const typename A::K*>(coef_of<A>(pl)), pl->V, scale, pl->scalf,
+                                        static_cast<const typename A::K*>(coef_of<A>(pl)), v_of<A>(pl), scale, pl->scalf,
                                         Lat{pl->p.n, pl->lg}, pl->partA);
     return cudaGetLastError();
   };
@@ -1071,7 +1073,7 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
   dfc* cdf = (pl->coef16 && pl->arith16 == 2) ? (dfc*)pl->coef16 : nullptr;
   QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau,
                                                                      pl->p.kinetic == 0 ? pl->fdtd_c : 0.0, c64,
-                                                                     cdf, pl->coef32, pl->flag),
+                                                                     cdf, pl->coef32, pl->Vdf, pl->flag),
                        cudaGetLastError()));
   int bad = 0;
   QFD_CK(cudaMemcpyAsync(&bad, pl->flag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
@@ -1086,6 +1088,8 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
 
 bool uses16(int precision) { return precision != QFD_C64; }
 bool uses32(int precision);
+// any arithmetic on the FP32 pipe (complex64 or double-float)
+bool uses_vdf(int precision) { return precision != QFD_C128; }
 // Device bytes a plan with these parameters allocates (lattices, tables, partials).
 size_t plan_device_bytes(const qfd_params& p) {
   const size_t n = (size_t)p.n, n3 = n * n * n;
@@ -1094,6 +1098,7 @@ size_t plan_device_bytes(const qfd_params& p) {
   size_t b = n3 * 16 + n3 * 8 + n * (16 + 8 + 16 + 8 + 4 + 8) + npart * 8 * (3 + 2 * MAX_LOWER) + 1024;
   if (uses16(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 16;
   if (uses32(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 8;
+  if (uses_vdf(p.precision)) b += n3 * sizeof(df);
   return b;
 }
 bool uses32(int precision) {
@@ -1226,6 +1231,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
     allocs.push_back({(void**)&pl->psi32, (size_t)(p.nstates + 1) * n3 * sizeof(float2)});
     allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
   }
+  if (uses_vdf(p.precision)) allocs.push_back({(void**)&pl->Vdf, (size_t)n3 * sizeof(df)});
   for (auto& a : allocs) {
     if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -1274,7 +1280,7 @@ void qfd_destroy(qfd_plan_t pl) {
   if (pl->st) cudaStreamSynchronize(pl->st);
   void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
                   pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
-                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->errflag};
+                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->errflag, pl->Vdf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (pl->hscal) cudaFreeHost(pl->hscal);

@@ -166,6 +166,7 @@ struct F64 {
   using K = double2;  // update coefficients {A, B dtau}
   using T = double;   // per-axis kinetic table entry
   using S = double;   // scalar
+  using VT = double;  // potential as read by the energy partials
   static constexpr int id = 0;
   static __device__ __forceinline__ C ldtw(const C* p) { return __ldg(p); }
   static __device__ __forceinline__ T kadd(T a, T b) { return a + b; }
@@ -201,6 +202,18 @@ struct F64 {
     }
     __device__ __forceinline__ double2 value() const { return double2{re, im}; }
   };
+  struct Full {  // sums of |psi|^2 and V |psi|^2
+    double n2 = 0.0, pv = 0.0;
+    __device__ __forceinline__ void add(C v, VT vv) {
+      const double a2 = v.x * v.x + v.y * v.y;
+      n2 += a2;
+      pv += vv * a2;
+    }
+  };
+  struct Pars {  // Parseval sum of T |psi~|^2
+    double pt = 0.0;
+    __device__ __forceinline__ void add(T tk, C v) { pt += tk * (v.x * v.x + v.y * v.y); }
+  };
 };
 
 struct F32 {
@@ -208,6 +221,7 @@ struct F32 {
   using K = float2;  // {B dtau, 1 - A}
   using T = float;
   using S = float;
+  using VT = df;     // the double-float copy of V
   static constexpr int id = 1;
   static __device__ __forceinline__ C ldtw(const C* p) { return __ldg(p); }
   static __device__ __forceinline__ T kadd(T a, T b) { return a + b; }
@@ -245,6 +259,21 @@ struct F32 {
     }
     __device__ __forceinline__ double2 value() const { return double2{dval(re), dval(im)}; }
   };
+  // energy partials in double-float on the FP32 pipe (exact squares)
+  struct Full {
+    df n2{0.f, 0.f}, pv{0.f, 0.f};
+    __device__ __forceinline__ void add(C v, VT vv) {
+      const df a2 = dadd(two_prod(v.x, v.x), two_prod(v.y, v.y));
+      n2 = dadd(n2, a2);
+      pv = dadd(pv, dmul(a2, vv));
+    }
+  };
+  struct Pars {
+    df pt{0.f, 0.f};
+    __device__ __forceinline__ void add(T tk, C v) {
+      pt = dadd(pt, dmul(dadd(two_prod(v.x, v.x), two_prod(v.y, v.y)), df{tk, 0.f}));
+    }
+  };
 };
 
 struct DF {
@@ -252,6 +281,7 @@ struct DF {
   using K = dfc;  // {B dtau, 1 - A} as double-float pairs
   using T = df;
   using S = df;
+  using VT = df;  // the double-float copy of V
   static constexpr int id = 2;
   static __device__ __forceinline__ C ldtw(const C* p) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
@@ -299,6 +329,20 @@ struct DF {
       s = dadd(s, fast_two_sum(t.h, e));
     }
     __device__ __forceinline__ double value() const { return dval(s); }
+  };
+  // energy partials in double-float (|v|^2 as in Acc, products by dmul)
+  static __device__ __forceinline__ df norm2_df(C v) { return dadd(dmul(v.x, v.x), dmul(v.y, v.y)); }
+  struct Full {
+    df n2{0.f, 0.f}, pv{0.f, 0.f};
+    __device__ __forceinline__ void add(C v, VT vv) {
+      const df a2 = norm2_df(v);
+      n2 = dadd(n2, a2);
+      pv = dadd(pv, dmul(a2, vv));
+    }
+  };
+  struct Pars {
+    df pt{0.f, 0.f};
+    __device__ __forceinline__ void add(T tk, C v) { pt = dadd(pt, dmul(norm2_df(v), tk)); }
   };
 };
 
@@ -621,6 +665,49 @@ __device__ __forceinline__ void block_reduce_store(double (&val)[NQ], double* __
   }
 }
 
+// Block sum of NQ double-float values in double-float, stored as FP64
+// partials part[q * nblocks + blockIdx.x] (one conversion per CTA).  Same
+// shape as block_reduce_store: serial in thread order below 32 threads, else
+// a warp shuffle tree and one across the warps.
+template <int NQ>
+__device__ __forceinline__ void df_reduce_store(df (&val)[NQ], double* __restrict__ part) {
+  __shared__ df red[NQ][32];
+  if (blockDim.x < 32) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = val[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        df s = val[q];
+        for (int i = 1; i < (int)blockDim.x; ++i) s = dadd(s, red[q][i]);
+        part[(int64_t)q * gridDim.x + blockIdx.x] = dval(s);
+      }
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    df s = val[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
+    if (lane == 0) red[q][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      df s = lane < nw ? red[q][lane] : df{0.f, 0.f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
+      if (lane == 0) part[(int64_t)q * gridDim.x + blockIdx.x] = dval(s);
+    }
+  }
+}
+
 // The STATS_NORM partial of a CTA (part[blockIdx.x], with 0 for the second
 // quantity at part[gridDim.x + blockIdx.x]).  For the FP32-pipe policies the
 // per-thread exact double-float sums are reduced in double-float and turned
@@ -633,41 +720,40 @@ __device__ __forceinline__ void norm_reduce_store(const typename A::Acc& acc, do
     double q[2] = {acc.value(), 0.0};
     block_reduce_store<2>(q, part);
   } else {
-    __shared__ df red[32];
-    df s = acc.s;
-    if (blockDim.x < 32) {
-      red[threadIdx.x] = s;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)blockDim.x; ++i) s = dadd(s, red[i]);
-        part[blockIdx.x] = dval(s);
-        part[gridDim.x + blockIdx.x] = 0.0;
-      }
-      return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-      s = lane < nw ? red[lane] : df{0.f, 0.f};
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-        s = dadd(s, df{__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)});
-      if (lane == 0) {
-        part[blockIdx.x] = dval(s);
-        part[gridDim.x + blockIdx.x] = 0.0;
-      }
-    }
+    df q[1] = {acc.s};
+    df_reduce_store<1>(q, part);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = 0.0;
+  }
+}
+
+// The STATS_FULL partials (sum |psi|^2, sum V |psi|^2) and the Parseval
+// partial (sum T |psi~|^2) of a CTA, in the policy's accumulator.
+template <class A>
+__device__ __forceinline__ void full_store(const typename A::Full& f, double* __restrict__ part) {
+  if constexpr (A::id == 0) {
+    double q[2] = {f.n2, f.pv};
+    block_reduce_store<2>(q, part);
+  } else {
+    df q[2] = {f.n2, f.pv};
+    df_reduce_store<2>(q, part);
+  }
+}
+template <class A>
+__device__ __forceinline__ void pars_store(const typename A::Pars& f, double* __restrict__ part) {
+  if constexpr (A::id == 0) {
+    double q[1] = {f.pt};
+    block_reduce_store<1>(q, part);
+  } else {
+    df q[1] = {f.pt};
+    df_reduce_store<1>(q, part);
   }
 }
 
 // Partial-sum modes of the passes that write psi (pass A and forward x):
 //   STATS_NONE  no reduction (the common step)
 //   STATS_NORM  sum |psi|^2 (steps that end in a normalisation)
-//   STATS_FULL  sum |psi|^2 and sum V |psi|^2 (energy checks; FP64 per site)
+//   STATS_FULL  sum |psi|^2 and sum V |psi|^2 (energy checks; FP64 sums for
+//               complex128, exact double-float sums on the FP32 pipe otherwise)
 enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 
 // ================================================================ kernels
@@ -721,7 +807,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   for (int m = 0; m < SH::E; ++m) v[m] = W[line0 * N + t + m * SH::T];
   static_assert(SH::T <= 32 || SH::LINES <= 15, "one named barrier per line");
   AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
-  double pt = 0.0;
+  typename A::Pars pacc;
 #pragma unroll
   for (int g = 0; g < ZG; ++g) {
     const int64_t line = line0 + (int64_t)g * SH::LINES;
@@ -736,7 +822,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 #pragma unroll
     for (int m = 0; m < SH::E; ++m) {
       const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
-      if constexpr (PARSEVAL) pt += A::tval(tk) * A::norm2_d(v[m]);
+      if constexpr (PARSEVAL) pacc.add(tk, v[m]);
       v[m] = cscale(v[m], tk);
     }
     fft_line<A, N, +1, decltype(acc), true>(v, t, tw, acc);
@@ -747,10 +833,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
       for (int m = 0; m < SH::E; ++m) v[m] = nx[m];
     }
   }
-  if constexpr (PARSEVAL) {
-    double q[1] = {pt};
-    block_reduce_store<1>(q, part);
-  }
+  if constexpr (PARSEVAL) pars_store<A>(pacc, part);
 }
 
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
@@ -761,7 +844,7 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 template <class A, int N, int STATS>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
-           const double* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
+           const typename A::VT* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
            const typename A::C* __restrict__ tw, double* __restrict__ part) {
   using C = typename A::C;
   using K = typename A::K;
@@ -791,7 +874,7 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   typename A::S s{};
   if (scaled) s = A::load_scale(scale, scale_f);
   typename A::Acc nacc;
-  double n2 = 0.0, pv = 0.0;
+  typename A::Full facc;
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
@@ -802,20 +885,13 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
     psi[idx] = nw;
     v[m] = nw;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
-    if constexpr (STATS == STATS_FULL) {
-      const double a2 = A::norm2_d(nw);
-      n2 += a2;
-      pv += V[idx] * a2;
-    }
+    if constexpr (STATS == STATS_FULL) facc.add(nw, V[idx]);
   }
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
-  if constexpr (STATS == STATS_FULL) {
-    double q[2] = {n2, pv};
-    block_reduce_store<2>(q, part);
-  }
+  if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }
 
 // Forward DFT_x of src (optionally times *scale, optionally also written to
@@ -823,7 +899,7 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
 // (each CTA reads its whole tile before writing it).
 template <class A, int N, int STATS>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
-k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, const double* __restrict__ V,
+k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, const typename A::VT* __restrict__ V,
             const double* __restrict__ scale, const float* __restrict__ scale_f, const typename A::C* __restrict__ tw,
             double* __restrict__ part) {
   using C = typename A::C;
@@ -838,7 +914,7 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
   if (scaled) s = A::load_scale(scale, scale_f);
   C v[SH::E];
   typename A::Acc nacc;
-  double n2 = 0.0, pv = 0.0;
+  typename A::Full facc;
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
@@ -846,11 +922,7 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
     if (scaled) x = cscale(x, s);
     v[m] = x;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(x);
-    if constexpr (STATS == STATS_FULL) {
-      const double a2 = A::norm2_d(x);
-      n2 += a2;
-      pv += V[idx] * a2;
-    }
+    if constexpr (STATS == STATS_FULL) facc.add(x, V[idx]);
   }
   if (psi_out) {
 #pragma unroll
@@ -861,10 +933,7 @@ k_forward_x(const typename A::C* src, typename A::C* W, typename A::C* psi_out, 
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
-  if constexpr (STATS == STATS_FULL) {
-    double q[2] = {n2, pv};
-    block_reduce_store<2>(q, part);
-  }
+  if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }
 
 // ------------------------------------------------- projection and overlaps
@@ -924,7 +993,8 @@ k_gs_dots(const typename A::C* __restrict__ psi, LowerPtrs lower, int k, int par
 template <class A, int N, int STATS, bool LOWER = true>
 __global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
 k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double* __restrict__ sums, int k, int parity,
-            int offgrid, typename A::C* __restrict__ dst, typename A::C* __restrict__ W, const double* __restrict__ V,
+            int offgrid, typename A::C* __restrict__ dst, typename A::C* __restrict__ W,
+            const typename A::VT* __restrict__ V,
             const typename A::C* __restrict__ tw, double* __restrict__ part) {
   using C = typename A::C;
   using SH = Shape<A, N>;
@@ -952,7 +1022,7 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
     for (int m = 0; m < SH::E; ++m) rv[m] = src[rbase + (int64_t)reflect1<N>(t + m * SH::T, offgrid) * S];
   }
   typename A::Acc nacc;
-  double n2 = 0.0, pv = 0.0;
+  typename A::Full facc;
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) {
     const int x = t + m * SH::T;
@@ -965,21 +1035,14 @@ k_project_x(const typename A::C* __restrict__ src, LowerPtrs lower, const double
     dst[idx] = p;
     v[m] = p;
     if constexpr (STATS == STATS_NORM) nacc.add_norm(p);
-    if constexpr (STATS == STATS_FULL) {
-      const double a2 = A::norm2_d(p);
-      n2 += a2;
-      pv += V[idx] * a2;
-    }
+    if constexpr (STATS == STATS_FULL) facc.add(p, V[idx]);
   }
   AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
   fft_line<A, N, -1>(v, t, tw, acc);
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
-  if constexpr (STATS == STATS_FULL) {
-    double q[2] = {n2, pv};
-    block_reduce_store<2>(q, part);
-  }
+  if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }
 
 // psi *= f in the policy's arithmetic, f = scal[0] (mode 0) or 1 / sqrt(scal[1]) (mode 1).

@@ -37,7 +37,8 @@ struct LaunchArgs {
   const void* src = nullptr;   // forward-x input (may alias W)
   void* psi_out = nullptr;     // forward-x: where to store the scaled input (or null)
   const void* coef = nullptr;  // update coefficients per site
-  const double* V = nullptr;   // FP64 potential
+  const void* V = nullptr;     // potential as the policy's energy sums read it:
+                               // FP64 (F64), double-float pairs (F32, DF)
   const double* scale = nullptr;  // normalisation factor (FP64) or null
   const float* scale_f = nullptr;  // its FP32 rounding and double-float split
   const void* tw = nullptr;    // twiddles exp(-2 pi i e / N), e < N

@@ -18,13 +18,14 @@ static void ensure_smem(K kern, size_t bytes) {
 template <class A, int N>
 cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
+  using VT = typename A::VT;
   using SH = Shape<A, N>;
   const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
   const int grid = (int)((int64_t)N * N / SH::XCOLS);
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
-    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, a.V, a.scale,
-                                                  a.scale_f, (const C*)a.tw, a.part);
+    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, (const VT*)a.V,
+                                                  a.scale, a.scale_f, (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL>);
   else if (a.stats == STATS_NORM) go(k_update_x<A, N, STATS_NORM>);
@@ -36,12 +37,13 @@ cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
 template <class A, int N>
 cudaError_t Launch<A, N>::forward_x(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
+  using VT = typename A::VT;
   using SH = Shape<A, N>;
   const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
   const int grid = (int)((int64_t)N * N / SH::XCOLS);
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
-    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, (C*)a.W, (C*)a.psi_out, a.V, a.scale,
+    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, (C*)a.W, (C*)a.psi_out, (const VT*)a.V, a.scale,
                                                   a.scale_f, (const C*)a.tw, a.part);
   };
   if (a.stats == STATS_FULL) go(k_forward_x<A, N, STATS_FULL>);
@@ -102,6 +104,7 @@ cudaError_t Launch<A, N>::zpass(const LaunchArgs& a, int* nblocks) {
 template <class A, int N>
 cudaError_t Launch<A, N>::project_x(const LaunchArgs& a, int* nblocks) {
   using C = typename A::C;
+  using VT = typename A::VT;
   using SH = Shape<A, N>;
   const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
   const int grid = (int)((int64_t)N * N / SH::XCOLS);
@@ -110,7 +113,7 @@ cudaError_t Launch<A, N>::project_x(const LaunchArgs& a, int* nblocks) {
   auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<grid, SH::XTHREADS, smem, a.stream>>>((const C*)a.src, lp, a.sums, a.k, a.parity, a.offgrid,
-                                                      (C*)a.dst, (C*)a.W, a.V, (const C*)a.tw, a.part);
+                                                      (C*)a.dst, (C*)a.W, (const VT*)a.V, (const C*)a.tw, a.part);
   };
   if (a.k > 0) {
     if (a.stats == STATS_FULL) go(k_project_x<A, N, STATS_FULL, true>);
