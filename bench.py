@@ -405,6 +405,8 @@ def run_qfd(args):
     if args.serve > 0:
         line["serve"] = serve_section(torch, Q, dev, args.serve, [int(x) for x in args.serve_sizes.split(",")],
                                       args.serve_precisions.split(","))
+    if args.batched_step:
+        line["batched_step"] = batched_step_section(torch, Q, dev)
     if args.solve:
         c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
             others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
@@ -512,6 +514,61 @@ def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_st
     return out
 
 
+def batched_step_section(torch, Q, dev, sizes=(64, 96, 128), precisions=("c64", "df64"), count=32, steps=100,
+                         reps=3):
+    """Lockstep steps of `count` independent lattices of one size (Cornell V =
+    -alpha/r + sigma r with alpha U[0.1,0.5], sigma U[0.1,0.3]; kinetic term
+    1..3 in turn; mass U[1,5]; a = 0.1; dtau = 0.5 * 2 / max T(k); seeded
+    uniform starts; normalisation every 10 steps): qfd_step_batch (one launch
+    per pass over all lattices) against qfd_step on each plan in turn.  Wall
+    clock around each variant (both return after their work has completed),
+    best of `reps`; site-updates/s = count n^3 steps / time."""
+    from paper_2006_16935_gb300 import serve as S
+
+    rng = np.random.default_rng(8)
+    out = {"lattices": count, "steps": steps, "spacing_a": 0.1, "ortho_every": 10, "cases": []}
+    for prec in precisions:
+        for n in sizes:
+            plans = []
+            try:
+                for i in range(count):
+                    kin = 1 + i % 3
+                    mass = float(rng.uniform(1.0, 5.0))
+                    p = Q.Plan(n, 0.1, mass, 0.5 * 2.0 / S.kinetic_max(kin, 0.1, mass, 0), kin, ortho_every=10,
+                               precision=prec)
+                    p.fill_potential("cornell", (float(rng.uniform(0.1, 0.5)), float(rng.uniform(0.1, 0.3))))
+                    p.fill_psi_uniform(0, 300 + i)
+                    plans.append(p)
+                Q.step_batch(plans, 0, 10)  # warm-up of both variants
+                for p in plans:
+                    p.step(0, 10)
+                best = {"single": float("inf"), "batched": float("inf")}
+                launches = {}
+                for _ in range(reps):
+                    for mode in ("single", "batched"):
+                        c0 = sum(p.launch_count() for p in plans)
+                        torch.cuda.synchronize(dev)
+                        t0 = time.perf_counter()
+                        if mode == "single":
+                            for p in plans:
+                                p.step(0, steps)
+                        else:
+                            Q.step_batch(plans, 0, steps)
+                        torch.cuda.synchronize(dev)
+                        best[mode] = min(best[mode], time.perf_counter() - t0)
+                        launches[mode] = sum(p.launch_count() for p in plans) - c0
+            finally:
+                for p in plans:
+                    p.close()
+            sites = float(count) * n ** 3 * steps
+            out["cases"].append({"n": n, "precision": prec,
+                                 "single_site_updates_per_s": sites / best["single"],
+                                 "batched_site_updates_per_s": sites / best["batched"],
+                                 "speedup": best["single"] / best["batched"],
+                                 "launches_per_step": {k: v / steps for k, v in launches.items()}})
+    return out
+
+
 def run_batch_only(args):
     import torch
 
@@ -581,6 +638,8 @@ def main():
     ap.add_argument("--batch-sizes", default="64,96,128,192")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched workload")
     ap.add_argument("--batch-max-steps", type=int, default=50000)
+    ap.add_argument("--batched-step", type=int, default=1,
+                    help="1: add the lockstep batched-step sample (qfd_step_batch vs qfd_step) to the line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -201,6 +201,38 @@ qfd_status qfd_set_parity(qfd_plan_t plan, int state, int parity);
  * (complex64 for QFD_C64 and, before a refinement, QFD_C64_REFINE). */
 qfd_status qfd_step(qfd_plan_t plan, int state, int64_t nsteps);
 
+/* Largest number of lattices one qfd_step_batch call steps together. */
+#define QFD_MAX_BATCH 32
+
+/* qfd_step for several plans at once: advances states[i] of plans[i] by
+ * nsteps steps of Eq. (iter_proced) (Sec. 2.2, with the FFT kinetic terms of
+ * Sec. 2.1), i < count, with exactly the operations qfd_step applies to each.
+ * Each pass of a step (the y transforms, the z pass with T(k), the update
+ * with the x transforms) is one launch over all the lattices; the cadence
+ * (projection, deflation, normalisation) runs per plan.  There is no
+ * counterpart in the paper, whose code steps one lattice.
+ *   plans, states  arrays of `count` entries, 1 <= count <= QFD_MAX_BATCH;
+ *                  the plans are distinct, have the same n <= 256 (a
+ *                  larger lattice fills the GPU alone), the same current
+ *                  arithmetic and FFT kinetic terms (kinetic 1..3), and a
+ *                  potential; their parameters may differ otherwise.
+ *   nsteps         >= 0.
+ * Launch shapes: the batched passes use the default shapes (not those chosen
+ * by qfd_autotune / qfd_set_tuning).  With default shapes on every plan the
+ * double-float states are bit-identical to qfd_step's; complex128 and
+ * complex64 states agree with them to rounding (the compiler may contract a
+ * product and a sum into an FMA differently in the batched kernels).
+ * Streams: the work runs on plans[0]'s stream; each other plan's stream is
+ * ordered before it and after it with events, and the call returns after
+ * every plan's work has completed (as qfd_step does).
+ * Errors: QFD_ERR_ARG for a null array, a count out of range, a repeated
+ * plan, a state index out of range, n > 256, or plans that differ in n,
+ * arithmetic or kinetic kind (message in qfd_last_error of plans[0], or of NULL when plans
+ * is NULL or count is out of range); QFD_ERR_STATE for a plan without a
+ * potential; a launch error as QFD_ERR_CUDA.  Nothing is stepped when an
+ * argument is rejected. */
+qfd_status qfd_step_batch(const qfd_plan_t* plans, const int* states, int count, int64_t nsteps);
+
 /* Rayleigh energy <psi|H_K + V|psi> / <psi|psi> of `state` (FP64 sums;
  * <psi|H_K|psi> by Parseval, (1/N^3) sum_k T(k) |FFT psi|^2) and its squared
  * norm sum |psi|^2.  Either output may be NULL. */

@@ -1106,6 +1106,87 @@ bool uses32(int precision) {
 }
 bool refines(int precision) { return precision == QFD_C64_REFINE || precision == QFD_C64_REFINE_DF; }
 
+// qfd_step_batch after its checks, with every plan's stream pointed at
+// plans[0]'s: per step, the lattices whose W holds the forward x transform
+// take passes B, C and D as three batched launches (any other advances
+// alone), then pass A runs as one batched launch per partial-sum mode; the
+// cadence and the bookkeeping are step_once's, per plan.
+template <class A>
+qfd_status step_batch(qfd_plan_s* const* pls, const int* ss, int count, int64_t nsteps) {
+  qfd_plan_t p0 = pls[0];
+  const int64_t n = p0->p.n;
+  qfd_status r;
+  for (int64_t it = 0; it < nsteps; ++it) {
+    BatchY by{};
+    BatchZ bz{};
+    int nx = 0;
+    for (int i = 0; i < count; ++i) {
+      qfd_plan_t pl = pls[i];
+      if ((r = ensure_w<A>(pl, ss[i])) != QFD_OK) return r;
+      if (pl->w_stage == ST_X) {
+        by.W[nx] = bz.W[nx] = pl->W;
+        by.tw[nx] = bz.tw[nx] = tw_of<A>(pl);
+        bz.ktab[nx] = ktab_of<A>(pl);
+        bz.kp[nx] = pl->kin;
+        ++nx;
+      } else if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) {
+        return r;
+      }
+    }
+    if (nx > 0) {
+      qfd_plan_t pl = p0;  // the batched launches are counted and timed on plans[0]
+      QFD_RUN(PASS_FWD_Y, launch_fft_y_batch<A>(n, by, nx, -1, p0->st));
+      QFD_RUN(PASS_ZKIN, launch_zpass_batch<A>(n, bz, nx, p0->st));
+      QFD_RUN(PASS_INV_Y, launch_fft_y_batch<A>(n, by, nx, +1, p0->st));
+    }
+    // pass A: STATS_NORM for the lattices whose next step ends in a cadence
+    // without a projection (the partials feed the normalisation), else none
+    BatchU bu[2] = {};
+    int nu[2] = {0, 0};
+    uint32_t scaled[2] = {0u, 0u};
+    for (int i = 0; i < count; ++i) {
+      qfd_plan_t pl = pls[i];
+      const int s = ss[i];
+      const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
+      const int g = ortho_next && !projects(pl, s) ? 1 : 0;
+      const int j = nu[g]++;
+      BatchU& b = bu[g];
+      b.W[j] = pl->W;
+      b.psi[j] = psi_of<A>(pl, s);
+      b.coef[j] = coef_of<A>(pl);
+      b.V[j] = v_of<A>(pl);
+      b.scale[j] = pl->scal + SC_SCALE;
+      b.scale_f[j] = pl->scalf;
+      b.tw[j] = tw_of<A>(pl);
+      b.part[j] = pl->partA;
+      if (pl->pending) scaled[g] |= 1u << j;
+    }
+    int nb = 0;
+    for (int g = 0; g < 2; ++g) {
+      if (nu[g] == 0) continue;
+      qfd_plan_t pl = p0;
+      QFD_RUN(PASS_UPDATE_X,
+              launch_update_x_batch<A>(n, bu[g], nu[g], scaled[g], g ? STATS_NORM : STATS_NONE, p0->st, &nb));
+    }
+    for (int i = 0; i < count; ++i) {
+      qfd_plan_t pl = pls[i];
+      const int s = ss[i];
+      pl->nA = nb;
+      pl->w_stage = ST_X;
+      pl->pending = false;
+      pl->t[s] += 1;
+      if (pl->t[s] % pl->p.ortho_every == 0) {
+        if ((r = cadence<A>(pl, s, 0)) != QFD_OK) return r;
+        if (pl->snap_every > 0 && s == 0 && pl->t[s] % pl->snap_every == 0 && (r = take_snapshot<A>(pl)) != QFD_OK)
+          return r;
+      }
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if ((r = materialize<A>(pls[i], ss[i])) != QFD_OK) return r;
+  return QFD_OK;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1464,6 +1545,55 @@ qfd_status qfd_step(qfd_plan_t pl, int s, int64_t nsteps) {
     qfd_status q = materialize<A>(pl, s);
     return q != QFD_OK ? q : check_kernel_errors(pl);
   });
+}
+
+qfd_status qfd_step_batch(const qfd_plan_t* plans, const int* states, int count, int64_t nsteps) {
+  static_assert(QFD_MAX_BATCH == MAX_BATCH, "batch size of the header and of the kernels");
+  if (!plans || !states || count < 1 || count > QFD_MAX_BATCH || !plans[0]) {
+    g_create_error = "qfd_step_batch: null array or plan, or count outside 1..QFD_MAX_BATCH";
+    return QFD_ERR_ARG;
+  }
+  qfd_plan_t p0 = plans[0];
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = plans[i];
+    if (!pl) return fail(p0, QFD_ERR_ARG, "null plan in the batch");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == pl) return fail(p0, QFD_ERR_ARG, "a plan appears twice in the batch");
+    if (states[i] < 0 || states[i] >= pl->p.nstates) return fail(p0, QFD_ERR_ARG, "state index out of range");
+    if (pl->p.n != p0->p.n || pl->phase != p0->phase)
+      return fail(p0, QFD_ERR_ARG, "the plans of a batch share n and the current arithmetic");
+    if (pl->p.kinetic == 0) return fail(p0, QFD_ERR_ARG, "batched steps take the FFT kinetic terms (kinetic 1..3)");
+    if (pl->p.n > MAX_BATCH_N) return fail(p0, QFD_ERR_ARG, "batched steps take lattices of n <= 256");
+    if (!pl->has_pot) return fail(p0, QFD_ERR_STATE, "set a potential before stepping");
+  }
+  if (nsteps < 0) return fail(p0, QFD_ERR_ARG, "nsteps < 0");
+  // order every plan's earlier work before the batch, run the batch on
+  // plans[0]'s stream, order every plan's later work after it
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+    return fail(p0, QFD_ERR_CUDA, "cudaEventCreate failed");
+  std::vector<cudaStream_t> own(count);
+  for (int i = 0; i < count; ++i) {
+    own[i] = plans[i]->st;
+    if (own[i] != p0->st) {
+      cudaEventRecord(ev, own[i]);
+      cudaStreamWaitEvent(p0->st, ev, 0);
+    }
+    plans[i]->st = p0->st;
+  }
+  qfd_status r = with_policy(p0->phase, [&](auto pol) -> qfd_status {
+    return step_batch<decltype(pol)>(plans, states, count, nsteps);
+  });
+  cudaEventRecord(ev, p0->st);
+  for (int i = 0; i < count; ++i) {
+    plans[i]->st = own[i];
+    if (own[i] != p0->st) cudaStreamWaitEvent(own[i], ev, 0);
+  }
+  cudaEventDestroy(ev);
+  if (r != QFD_OK) return r;
+  for (int i = 0; i < count; ++i)
+    if ((r = check_kernel_errors(plans[i])) != QFD_OK) return r;
+  return QFD_OK;
 }
 
 qfd_status qfd_energy(qfd_plan_t pl, int s, double* E, double* norm2) {

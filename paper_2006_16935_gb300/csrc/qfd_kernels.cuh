@@ -756,6 +756,35 @@ __device__ __forceinline__ void pars_store(const typename A::Pars& f, double* __
 //               complex128, exact double-float sums on the FP32 pipe otherwise)
 enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 
+// ------------------------------------------------------------ lattice batches
+// A batched launch runs one pass of the step over up to MAX_BATCH lattices of
+// one size and arithmetic: blockIdx.y selects the lattice, blockIdx.x the
+// tile exactly as in the single-lattice launch, so each lattice sees the same
+// arithmetic.  The per-lattice pointers travel as __grid_constant__ kernel
+// parameters (each descriptor set stays under 4 KB).
+constexpr int MAX_BATCH = 32;
+struct BatchY {  // passes B and D
+  void* W[MAX_BATCH];
+  const void* tw[MAX_BATCH];
+};
+struct BatchZ {  // pass C
+  void* W[MAX_BATCH];
+  const void* tw[MAX_BATCH];
+  const void* ktab[MAX_BATCH];
+  KinParams kp[MAX_BATCH];
+};
+struct BatchU {  // pass A
+  void* W[MAX_BATCH];
+  void* psi[MAX_BATCH];
+  const void* coef[MAX_BATCH];
+  const void* V[MAX_BATCH];
+  const double* scale[MAX_BATCH];
+  const float* scale_f[MAX_BATCH];
+  const void* tw[MAX_BATCH];
+  double* part[MAX_BATCH];
+};
+static_assert(sizeof(BatchZ) <= 4000 && sizeof(BatchU) <= 4000, "kernel parameter space");
+
 // ================================================================ kernels
 
 // Pass B / D (and the plain x transform): in-place strided line FFT over tiles
@@ -763,10 +792,9 @@ enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 // base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
 // YC (the tile width) is a launch-shape choice of the autotuner; the
 // arithmetic of every column is the same for all widths.
-template <class A, int N, int DIR, int YC = Shape<A, N>::YCOLS>
-__global__ void __launch_bounds__(N / FftPlan<N>::E * YC)
-k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
-              int64_t outer_stride) {
+template <class A, int N, int DIR, int YC>
+__device__ __forceinline__ void fft_strided_body(typename A::C* W, const typename A::C* __restrict__ tw,
+                                                 int64_t stride, int tiles_inner, int64_t outer_stride) {
   using C = typename A::C;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -784,6 +812,21 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
 }
+template <class A, int N, int DIR, int YC = Shape<A, N>::YCOLS>
+__global__ void __launch_bounds__(N / FftPlan<N>::E * YC)
+k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
+              int64_t outer_stride) {
+  fft_strided_body<A, N, DIR, YC>(W, tw, stride, tiles_inner, outer_stride);
+}
+// The same pass over the lattices of a batch (blockIdx.y = lattice).
+template <class A, int N, int DIR>
+__global__ void __launch_bounds__(N / FftPlan<N>::E * Shape<A, N>::YCOLS)
+k_fft_strided_batch(const __grid_constant__ BatchY b, int64_t stride, int tiles_inner, int64_t outer_stride) {
+  using C = typename A::C;
+  fft_strided_body<A, N, DIR, Shape<A, N>::YCOLS>(static_cast<C*>(b.W[blockIdx.y]),
+                                                  static_cast<const C*>(b.tw[blockIdx.y]), stride, tiles_inner,
+                                                  outer_stride);
+}
 
 // Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial when PARSEVAL),
 // inverse DFT_z.  The canonical layout is the same before and after a
@@ -791,10 +834,10 @@ k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t st
 // A CTA takes ZG groups of LINES consecutive lines in turn; the loads of the
 // next group are issued before the current group's transforms, so they are in
 // flight while it computes.
-template <class A, int N, bool PARSEVAL, int ZG = Shape<A, N>::ZG>
-__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
-k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
-        KinParams kp, double* __restrict__ part) {
+template <class A, int N, bool PARSEVAL, int ZG>
+__device__ __forceinline__ void zpass_body(typename A::C* W, const typename A::C* __restrict__ tw,
+                                           const typename A::T* __restrict__ ktab, const KinParams& kp,
+                                           double* __restrict__ part) {
   using C = typename A::C;
   using T = typename A::T;
   using SH = Shape<A, N>;
@@ -835,6 +878,20 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
   }
   if constexpr (PARSEVAL) pars_store<A>(pacc, part);
 }
+template <class A, int N, bool PARSEVAL, int ZG = Shape<A, N>::ZG>
+__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
+k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
+        const __grid_constant__ KinParams kp, double* __restrict__ part) {
+  zpass_body<A, N, PARSEVAL, ZG>(W, tw, ktab, kp, part);
+}
+// The same pass (without the Parseval partial) over the lattices of a batch.
+template <class A, int N>
+__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS) k_zpass_batch(const __grid_constant__ BatchZ b) {
+  using C = typename A::C;
+  const int i = blockIdx.y;
+  zpass_body<A, N, false, Shape<A, N>::ZG>(static_cast<C*>(b.W[i]), static_cast<const C*>(b.tw[i]),
+                                           static_cast<const typename A::T*>(b.ktab[i]), b.kp[i], nullptr);
+}
 
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
 // Eq. (iter_proced) with the coefficients of Sec. 2.2 (times an optional
@@ -842,10 +899,11 @@ k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A
 // per STATS; forward DFT_x of the new psi into W.  psi and the coefficients
 // are loaded before the inverse transform so that their latency overlaps it.
 template <class A, int N, int STATS>
-__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
-k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
-           const typename A::VT* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
-           const typename A::C* __restrict__ tw, double* __restrict__ part) {
+__device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* __restrict__ psi,
+                                              const typename A::K* __restrict__ coef,
+                                              const typename A::VT* __restrict__ V, const double* __restrict__ scale,
+                                              const float* __restrict__ scale_f, const typename A::C* __restrict__ tw,
+                                              double* __restrict__ part) {
   using C = typename A::C;
   using K = typename A::K;
   using SH = Shape<A, N>;
@@ -892,6 +950,25 @@ k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::
   for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
   if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
+}
+template <class A, int N, int STATS>
+__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
+k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
+           const typename A::VT* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
+           const typename A::C* __restrict__ tw, double* __restrict__ part) {
+  update_x_body<A, N, STATS>(W, psi, coef, V, scale, scale_f, tw, part);
+}
+// The same pass over the lattices of a batch; lattice i applies its pending
+// normalisation factor when bit i of `scaled` is set.
+template <class A, int N, int STATS>
+__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
+k_update_x_batch(const __grid_constant__ BatchU b, uint32_t scaled) {
+  using C = typename A::C;
+  const int i = blockIdx.y;
+  update_x_body<A, N, STATS>(static_cast<C*>(b.W[i]), static_cast<C*>(b.psi[i]),
+                             static_cast<const typename A::K*>(b.coef[i]), static_cast<const typename A::VT*>(b.V[i]),
+                             (scaled >> i) & 1u ? b.scale[i] : nullptr, b.scale_f[i],
+                             static_cast<const C*>(b.tw[i]), b.part[i]);
 }
 
 // Forward DFT_x of src (optionally times *scale, optionally also written to

@@ -12,6 +12,9 @@
 namespace qfd {
 
 struct KinParams;
+struct BatchY;
+struct BatchZ;
+struct BatchU;
 struct F64;
 struct F32;
 struct DF;
@@ -61,6 +64,11 @@ struct LaunchArgs {
   int vz = -1;
 };
 
+// Batched passes exist for lattices of N <= MAX_BATCH_N only: a larger
+// lattice fills the GPU on its own, and the instantiations would only
+// lengthen the build.
+constexpr int MAX_BATCH_N = 256;
+
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the
 // number of CTAs (= partials per reduced quantity) when non-null.
 template <class A, int N> struct Launch {
@@ -71,6 +79,12 @@ template <class A, int N> struct Launch {
   static cudaError_t project_x(const LaunchArgs& a, int* nblocks);
   static cudaError_t gs_dots(const LaunchArgs& a, int nblocks);
   static int partials();  // largest CTA count of a reducing pass
+  // batched passes over `count` lattices (default launch shapes; pass A with
+  // STATS_NONE or STATS_NORM, pass C without the Parseval partial)
+  static cudaError_t fft_y_batch(const BatchY& b, int count, int dir, cudaStream_t st);
+  static cudaError_t zpass_batch(const BatchZ& b, int count, cudaStream_t st);
+  static cudaError_t update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
+                                    int* nblocks);
 };
 
 template <int N> struct Tag {
@@ -111,6 +125,18 @@ template <class A> cudaError_t launch_project_x(const LaunchArgs& a, int* nb) {
 }
 template <class A> cudaError_t launch_gs_dots(const LaunchArgs& a, int nblocks) {
   return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::gs_dots(a, nblocks); });
+}
+template <class A> cudaError_t launch_fft_y_batch(int64_t n, const BatchY& b, int count, int dir, cudaStream_t st) {
+  return dispatch_n(n, [&](auto t) { return Launch<A, decltype(t)::value>::fft_y_batch(b, count, dir, st); });
+}
+template <class A> cudaError_t launch_zpass_batch(int64_t n, const BatchZ& b, int count, cudaStream_t st) {
+  return dispatch_n(n, [&](auto t) { return Launch<A, decltype(t)::value>::zpass_batch(b, count, st); });
+}
+template <class A>
+cudaError_t launch_update_x_batch(int64_t n, const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
+                                  int* nb) {
+  return dispatch_n(
+      n, [&](auto t) { return Launch<A, decltype(t)::value>::update_x_batch(b, count, scaled, stats, st, nb); });
 }
 template <class A> int max_partials(int64_t n) {
   int out = 0;

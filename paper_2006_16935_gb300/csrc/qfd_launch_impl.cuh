@@ -135,6 +135,60 @@ cudaError_t Launch<A, N>::gs_dots(const LaunchArgs& a, int nblocks) {
 }
 
 template <class A, int N>
+cudaError_t Launch<A, N>::fft_y_batch(const BatchY& b, int count, int dir, cudaStream_t st) {
+  if constexpr (N > MAX_BATCH_N) {
+    return cudaErrorInvalidValue;
+  } else {
+    using SH = Shape<A, N>;
+    constexpr int yc = SH::YCOLS;
+    const size_t smem = (size_t)N * yc * sizeof(typename A::C);
+    const int tiles_inner = N / yc;
+    auto go = [&](auto kern) {
+      ensure_smem(kern, smem);
+      kern<<<dim3(N * tiles_inner, count), SH::T * yc, smem, st>>>(b, (int64_t)N, tiles_inner, (int64_t)N * N);
+    };
+    if (dir < 0) go(k_fft_strided_batch<A, N, -1>);
+    else go(k_fft_strided_batch<A, N, +1>);
+    return cudaGetLastError();
+  }
+}
+
+template <class A, int N>
+cudaError_t Launch<A, N>::zpass_batch(const BatchZ& b, int count, cudaStream_t st) {
+  if constexpr (N > MAX_BATCH_N) {
+    return cudaErrorInvalidValue;
+  } else {
+    using SH = Shape<A, N>;
+    const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(typename A::C);
+    const int grid = (int)((int64_t)N * N / (SH::LINES * SH::ZG));
+    auto kern = k_zpass_batch<A, N>;
+    ensure_smem(kern, smem);
+    kern<<<dim3(grid, count), SH::LINE_THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  }
+}
+
+template <class A, int N>
+cudaError_t Launch<A, N>::update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
+                                         int* nblocks) {
+  if constexpr (N > MAX_BATCH_N) {
+    return cudaErrorInvalidValue;
+  } else {
+    using SH = Shape<A, N>;
+    const size_t smem = (size_t)N * SH::XPITCH * sizeof(typename A::C);
+    const int grid = (int)((int64_t)N * N / SH::XCOLS);
+    auto go = [&](auto kern) {
+      ensure_smem(kern, smem);
+      kern<<<dim3(grid, count), SH::XTHREADS, smem, st>>>(b, scaled);
+    };
+    if (stats == STATS_NORM) go(k_update_x_batch<A, N, STATS_NORM>);
+    else go(k_update_x_batch<A, N, STATS_NONE>);
+    if (nblocks) *nblocks = grid;
+    return cudaGetLastError();
+  }
+}
+
+template <class A, int N>
 int Launch<A, N>::partials() {
   using SH = Shape<A, N>;
   const int x = (int)((int64_t)N * N / SH::XCOLS);

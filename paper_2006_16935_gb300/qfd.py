@@ -101,6 +101,7 @@ def load():
         "qfd_set_parity": (I, [P, I, I]),
         "qfd_observables": (I, [P, I, D, ctypes.POINTER(D), I]),
         "qfd_step": (I, [P, I, I64]),
+        "qfd_step_batch": (I, [ctypes.POINTER(P), ctypes.POINTER(I), I, I64]),
         "qfd_energy": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_set_limits": (I, [P, I64, D, D]),
@@ -441,6 +442,25 @@ class Server:
             for r in self.poll(capacity):
                 res[r["id"]] = r
         return res
+
+
+MAX_BATCH = 32  # QFD_MAX_BATCH
+
+
+def step_batch(plans, states, nsteps):
+    """qfd_step_batch: advances states[i] of plans[i] by nsteps steps, each pass
+    of a step one launch over all the lattices (same n, arithmetic and FFT
+    kinetic kind; at most MAX_BATCH plans)."""
+    lib = load()
+    plans = list(plans)
+    if isinstance(states, int):
+        states = [states] * len(plans)
+    hs = (ctypes.c_void_p * max(1, len(plans)))(*[p.h for p in plans])
+    ss = (ctypes.c_int * max(1, len(plans)))(*[int(s) for s in states])
+    st = lib.qfd_step_batch(hs, ss, len(plans), int(nsteps))
+    if st != OK:
+        msg = lib.qfd_last_error(plans[0].h if plans and 1 <= len(plans) <= MAX_BATCH else None)
+        raise QfdError(st, msg.decode() if msg else "")
 
 
 def plan_bytes(n, precision="c128", nstates=1):

@@ -63,6 +63,19 @@ def test_plan_rejects_unstable_time_step(lib):
         assert st != qfd.ERR_UNSTABLE_DT  # (fails later without a GPU, with QFD_ERR_CUDA)
 
 
+def test_step_batch_rejects_bad_batches_without_a_plan(lib):
+    # rejected before any plan is touched: null arrays, count outside 1..32
+    P = ctypes.c_void_p * 33
+    I = ctypes.c_int * 33
+    for plans, states, count in [(None, None, 1), (P(), I(), 0), (P(), I(), 33), (P(), I(), -2), (P(), I(), 1)]:
+        st = lib.qfd_step_batch(plans, states, count, 1)
+        assert st == qfd.ERR_ARG
+        assert "qfd_step_batch" in lib.qfd_last_error(None).decode()
+    import re
+    hdr = open(qfd.HEADER_PATH).read()
+    assert int(re.search(r"#define QFD_MAX_BATCH (\d+)", hdr).group(1)) == qfd.MAX_BATCH == 32
+
+
 def test_splitmix64_published_first_output():
     # SplitMix64 from state 0 yields 0xE220A8397B1DCDAF first (Steele, Lea, Flood 2014; Vigna's splitmix64.c)
     assert int(inputs.splitmix64(np.array([0], np.uint64))[0]) == 0xE220A8397B1DCDAF
