@@ -258,8 +258,9 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
 
 
 # DRAM read + write bytes per site of the dominant kernel, from one ncu capture
-# of a 256^3 launch of the same kernel (`--set full`, profile_step driver);
-# traffic grows with the sites, so a 512^3 launch moves 512^3 times this
+# of a 256^3 launch of the same kernel (`--set full`, profile_step driver; a
+# later capture of the DRAM counters alone on the current kernels agrees to
+# 0.3 %); traffic grows with the sites, so a 512^3 launch moves 512^3 times this
 DRAM_BYTES_PER_SITE = {
     ("c128", "update_x"): (806.0e6 + 484.0e6) / 256 ** 3,
     ("df64", "update_x"): (805.0e6 + 484.0e6) / 256 ** 3,
