@@ -322,6 +322,46 @@ def test_oscillator_levels_one_step(level):
     assert e == pytest.approx(level * w + (1 - c) * ev, rel=1e-11)
 
 
+def test_stability_limit_is_dtau_times_max_t_equal_two():
+    # Sec. 2.2: without a potential the update multiplies a plane wave by
+    # 1 - dtau T(k), which grows in modulus exactly when dtau T(k) > 2; with the
+    # oscillator of the 32^3 configuration (A = 0.1, M = 1, V = r^2/2, H_K(1),
+    # max T = 3 pi^2 / (2 A^2 M)) the evolution at dtau T_max = 1.98 settles
+    # toward the ground state, while at 2.02 the modes above the limit take over
+    # (energy -> T_max) after 1000 steps with normalisation every 10
+    n, a, m = 32, 0.1, 1.0
+    V = O.potential(n, a, "ho", (1.0,))
+    tmax = O.kinetic_max(n, a, m, 1)
+    assert tmax == pytest.approx(3 * math.pi ** 2 / (2 * a * a * m), rel=1e-14)
+    psi0 = rand_psi(n, 1)
+    for c in (1.98, 2.02):
+        dt = c / tmax
+        prob = O.Problem(n, a, m, dt, 1, V, ortho_every=10, method="library")
+        psi, _ = O.evolve(psi0, prob, 1000)
+        w = np.abs(O.fft3(psi, "library")) ** 2
+        w /= w.sum()
+        e = O.energy(psi, V, prob.T, "library")
+        if c < 2:
+            assert w[dt * prob.T > 1.9].sum() < 1e-12
+            assert 1.3 < e < 1.6  # near the oscillator's 3/2
+        else:
+            assert w[dt * prob.T > 2].sum() > 1 - 1e-6
+            assert e > 0.99 * tmax
+
+
+def test_coulomb_ground_state_near_hydrogen_level():
+    # loose: pure Coulomb V = -1/r (clamped at r = A/2, Sec. 5.3 POTENTIAL 2),
+    # M = 1, H_K(2), 32^3 at A = 0.3 (box half-width 4.8 Bohr radii): the
+    # ground state lies within 2 % of the continuum -M/2 (what remains are the
+    # pole's discretisation artefacts discussed in Sec. 3.3 and the finite box)
+    n, a = 32, 0.3
+    V = O.potential(n, a, "coulomb", (), "offgrid")
+    dt = 0.8 / O.kinetic_max(n, a, 1.0, 2)
+    prob = O.Problem(n, a, 1.0, dt, 2, V, centre="offgrid", ortho_every=10, check_every=100, method="library")
+    r = O.solve_state(rand_psi(n, 1), prob, 20000, 1e-6, 1, rule="tail")
+    assert abs(r.energy + 0.5) <= 0.02 * 0.5, r.energy
+
+
 # --------------------------------------------------------- parity / GS ----
 
 @pytest.mark.parametrize("centre", ["grid", "offgrid"])
