@@ -268,6 +268,17 @@ DRAM_BYTES_PER_SITE = {
 }
 
 
+def step_hbm(prec, ms_per_imaginary_step, peaks):
+    """HBM roofline of the whole step: the design traffic of the four passes
+    (update with the x transforms, y, z with T(k), y) per site times the
+    sites, over the measured time of one imaginary-time step (cadence and
+    energy-check work included in the time, not in the bytes)."""
+    per_site = sum(PASS_BYTES[prec][p] for p in ("update_x", "fwd_y", "z_kinetic", "inv_y"))
+    gbs = per_site * float(N) ** 3 / (ms_per_imaginary_step / 1e3) / 1e9
+    return {"bytes_per_site": per_site, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+            "frac": gbs / peaks["hbm_gbs"]}
+
+
 def roofline_for(prec, per_pass, peaks):
     dom = max(per_pass, key=lambda k: per_pass[k]["total_ms"])
     cnt, tot = per_pass[dom]["launches"], per_pass[dom]["total_ms"]
@@ -371,6 +382,7 @@ def run_qfd(args):
         pl_o.close()
         others[other] = {"value": float(N) ** 3 * steps_o / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
                          "energy_at_end": e_o, "roofline": roofline_for(other, per_pass_o, peaks),
+                         "step_hbm": step_hbm(other, ms_o / steps_o, peaks),
                          "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass_o.items()}}
     if rank != 0:
         if world > 1:
@@ -383,6 +395,7 @@ def run_qfd(args):
         "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded uniform start, analytic potential)",
         "config": workload_config(args, prec),
         "roofline": roofline_for(prec, per_pass, peaks),
+        "step_hbm": step_hbm(prec, ms / steps, peaks),
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,

@@ -48,3 +48,14 @@ def test_roofline_object(prec):
         assert r["achieved"] == pytest.approx(bench.PASS_BYTES[prec]["update_x"] * sites / 15e-3 / 1e9)
     assert r["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_SITE[(prec, "update_x")] * sites)
     assert r["share_of_step"] == pytest.approx(150.0 / 425.0)
+
+
+def test_step_hbm_fraction():
+    peaks = {"hbm_gbs": 6800.0}
+    sites = float(bench.N) ** 3
+    r = bench.step_hbm("c64", 2.777, peaks)
+    assert r["bytes_per_site"] == 88.0
+    assert r["achieved_gbs"] == pytest.approx(88.0 * sites / 2.777e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved_gbs"] / 6800.0)
+    assert 0.6 < r["frac"] < 0.65  # the measured complex64 step at 512^3
+    assert bench.step_hbm("c128", 44.1, peaks)["bytes_per_site"] == 176.0
