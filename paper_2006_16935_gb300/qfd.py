@@ -455,6 +455,9 @@ def step_batch(plans, states, nsteps):
     plans = list(plans)
     if isinstance(states, int):
         states = [states] * len(plans)
+    states = list(states)
+    if len(states) != len(plans):
+        raise ValueError(f"{len(plans)} plans but {len(states)} states")
     hs = (ctypes.c_void_p * max(1, len(plans)))(*[p.h for p in plans])
     ss = (ctypes.c_int * max(1, len(plans)))(*[int(s) for s in states])
     st = lib.qfd_step_batch(hs, ss, len(plans), int(nsteps))

@@ -71,6 +71,14 @@ def test_step_batch_rejects_bad_batches_without_a_plan(lib):
         st = lib.qfd_step_batch(plans, states, count, 1)
         assert st == qfd.ERR_ARG
         assert "qfd_step_batch" in lib.qfd_last_error(None).decode()
+    # the binding: one state per plan, and the library's rejection of an empty batch
+    class Fake:
+        h = None
+    with pytest.raises(ValueError):
+        qfd.step_batch([Fake(), Fake()], [0], 1)
+    with pytest.raises(qfd.QfdError) as e:
+        qfd.step_batch([], 0, 1)
+    assert e.value.status == qfd.ERR_ARG
     import re
     hdr = open(qfd.HEADER_PATH).read()
     assert int(re.search(r"#define QFD_MAX_BATCH (\d+)", hdr).group(1)) == qfd.MAX_BATCH == 32
