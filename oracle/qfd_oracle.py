@@ -317,7 +317,19 @@ def potential(n: int, a: float, kind: str, params=(), centre: str = "grid") -> n
     'coulomb':   V = -1 / r, r >= A/2                   (POTENTIAL 2 clamped at the origin)
     'softcoul':  V = -1 / sqrt(r^2 + eps2), params (eps2,)
     """
-    r = radius(n, a, centre)
+    return potential_of_radius(radius(n, a, centre), a, kind, params)
+
+
+def potential_at(n: int, a: float, kind: str, params, sites: np.ndarray, centre: str = "grid") -> np.ndarray:
+    """V at the lattice sites `sites` (integer array [m, 3] of x1, x2, x3),
+    without building the whole lattice: the same V(r) as `potential`."""
+    d = displacement(n, centre)[np.asarray(sites)]
+    r = a * np.sqrt(np.sum(d * d, axis=1))
+    return potential_of_radius(r, a, kind, params)
+
+
+def potential_of_radius(r: np.ndarray, a: float, kind: str, params=()) -> np.ndarray:
+    """The potential forms of `potential` as functions of r = A |x - centre|."""
     if kind == "zero":
         return np.zeros_like(r)
     if kind == "ho":

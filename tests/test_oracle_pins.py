@@ -403,6 +403,20 @@ def test_gram_schmidt_leaves_no_overlap():
 
 # ---------------------------------------------------------- potentials ----
 
+@pytest.mark.parametrize("centre", ["grid", "offgrid"])
+def test_potential_at_sites_equals_the_lattice_potential(centre):
+    # the sampled form used at lattices too large to build whole: same values
+    n, a = 12, 0.3
+    rng = np.random.default_rng(3)
+    sites = rng.integers(0, n, size=(200, 3))
+    sites[0] = [n // 2] * 3
+    for kind, prm in [("zero", ()), ("ho", (2.0,)), ("cornell", (0.3, 0.2)), ("coulomb", ()),
+                      ("softcoul", (0.01,))]:
+        full = O.potential(n, a, kind, prm, centre)
+        got = O.potential_at(n, a, kind, prm, sites, centre)
+        assert np.array_equal(got, full[sites[:, 0], sites[:, 1], sites[:, 2]])
+
+
 def test_potential_values_by_hand():
     n, a = 8, 0.1
     # centre site (4,4,4): r = 0, clamped to a/2 for the singular forms
