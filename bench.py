@@ -47,14 +47,18 @@ METRIC = "site-updates/s at 512^3 (imaginary-time FFT step, softened Coulomb, H_
 UNIT = "site-updates/s"
 
 # algorithmic bytes per site of one launch of each pass (reads + writes of the
-# lattices the pass must touch; complex128 / complex64) and FP64/FP32 flops per site
+# lattices the pass must touch) and FP64/FP32 flops per site.  Pass A reads W,
+# psi and its per-site update input and writes psi and W: the precomputed
+# {A, B dtau} for complex128 (16 B), V as a double-float pair for DF (8 B) and
+# V in FP32 for complex64 (4 B).
 PASS_BYTES = {
     "c128": {"update_x": 80.0, "fwd_y": 32.0, "z_kinetic": 32.0, "inv_y": 32.0, "fwd_x": 32.0,
              "project_x": 64.0},
-    "c64": {"update_x": 40.0, "fwd_y": 16.0, "z_kinetic": 16.0, "inv_y": 16.0, "fwd_x": 16.0,
+    "df64": {"update_x": 72.0, "fwd_y": 32.0, "z_kinetic": 32.0, "inv_y": 32.0, "fwd_x": 32.0,
+             "project_x": 64.0},
+    "c64": {"update_x": 36.0, "fwd_y": 16.0, "z_kinetic": 16.0, "inv_y": 16.0, "fwd_x": 16.0,
             "project_x": 32.0},
 }
-PASS_BYTES["df64"] = PASS_BYTES["c128"]
 
 
 def fft_flops_per_point(n: int) -> float:
@@ -86,10 +90,19 @@ def read_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 / FP32 vector peaks (no tensor cores): nominal GB300 figures from the
-# profiling recipe: FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 x 2.07 GHz.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# pass A's bytes per site at the irreducible pass-A traffic of the method
+# statement (W, psi and V read as FP64 / FP32, psi and W written): the complex128
+# kernel reads the precomputed coefficients instead (80 B), see PASS_BYTES
+PASS_A_MIN_BYTES = {"c128": 72.0, "df64": 72.0, "c64": 36.0}
+
+
+def measure_alu_peaks(Q):
+    """FMA issue rates of the FP64 and FP32 pipes measured on this GPU by the
+    library's FMA-chain kernel (qfd_fma_rate), the roofline denominators of
+    the passes bound by vector arithmetic (no tensor cores are used)."""
+    return {"fp64_tflops": Q.fma_rate(True), "fp32_tflops": Q.fma_rate(False),
+            "source": "qfd_fma_rate on this GPU in this run (8 independent FMA chains per thread, "
+                      "best of 5 launches; of measured)"}
 
 
 class ClockSampler:
@@ -227,6 +240,11 @@ def workload_config(args, prec):
 
 
 def time_precision(torch, Q, args, prec, dev, want_roofline):
+    """The timed region: args.steps bench steps through qfd_solve_states with no
+    per-launch instrumentation (CUDA events on the plan's stream, which is
+    torch's current stream).  With want_roofline, a second run of the same
+    length from the same start, with every launch bracketed by events, gives
+    the per-pass durations of the roofline; it is not part of the timed value."""
     stream = torch.cuda.current_stream(dev)
     plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=STEPS_PER_BENCH_STEP,
                   check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP * max(1, args.warmup), tol=-1,
@@ -237,7 +255,7 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
     es, _, _ = plan.solve_states(1, [1])  # warm-up: W bench steps
     plan.set_limits(STEPS_PER_BENCH_STEP * args.steps, -1)
     plan.fill_psi_uniform(0, SEED)
-    plan.timing(want_roofline)
+    plan.timing(False)
     plan.timing_reset()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -249,23 +267,23 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
     launches = plan.launch_count()
     per_pass = {}
     if want_roofline:
+        plan.fill_psi_uniform(0, SEED)
+        plan.timing(True)
+        plan.timing_reset()
+        plan.solve_states(1, [1])
         for k in Q.PASS_KINDS:
             cnt, tot = plan.timing_query(k)
             if cnt:
                 per_pass[k] = {"launches": cnt, "total_ms": tot}
-    plan.timing(False)
+        plan.timing(False)
     return plan, ms, steps[0], es[0], launches, per_pass
 
 
-# DRAM read + write bytes per site of the dominant kernel, from one ncu capture
-# of a 256^3 launch of the same kernel (`--set full`, profile_step driver; a
-# later capture of the DRAM counters alone on the current kernels agrees to
-# 0.3 %); traffic grows with the sites, so a 512^3 launch moves 512^3 times this
-DRAM_BYTES_PER_SITE = {
-    ("c128", "update_x"): (806.0e6 + 484.0e6) / 256 ** 3,
-    ("df64", "update_x"): (805.0e6 + 484.0e6) / 256 ** 3,
-    ("c64", "update_x"): (403.0e6 + 215.0e6) / 256 ** 3,
-}
+# DRAM read + write bytes per site of the dominant kernel, from an ncu capture
+# of a 256^3 launch of the same kernel (profile_step driver, DRAM counters);
+# traffic grows with the sites, so a 512^3 launch moves 512^3 times this.  An
+# entry is left out (traffic null) until the current kernel has been captured.
+DRAM_BYTES_PER_SITE = {}
 
 
 def step_hbm(prec, ms_per_imaginary_step, peaks):
@@ -279,7 +297,7 @@ def step_hbm(prec, ms_per_imaginary_step, peaks):
             "frac": gbs / peaks["hbm_gbs"]}
 
 
-def roofline_for(prec, per_pass, peaks):
+def roofline_for(prec, per_pass, peaks, alu_peaks):
     dom = max(per_pass, key=lambda k: per_pass[k]["total_ms"])
     cnt, tot = per_pass[dom]["launches"], per_pass[dom]["total_ms"]
     avg_s = tot / cnt / 1e3
@@ -287,13 +305,13 @@ def roofline_for(prec, per_pass, peaks):
     bytes_launch = PASS_BYTES[prec].get(dom, 32.0) * sites
     flops_launch = pass_flops(N).get(dom, 0.0) * sites
     hbm = bytes_launch / avg_s / 1e9
-    alu_peak = FP64_PEAK_TFLOPS if prec == "c128" else FP32_PEAK_TFLOPS
+    alu_peak = alu_peaks["fp64_tflops"] if prec == "c128" else alu_peaks["fp32_tflops"]
     alu = flops_launch / avg_s / 1e12
     hbm_frac = hbm / peaks["hbm_gbs"]
     alu_frac = alu / alu_peak
     if prec == "c128" and alu_frac > hbm_frac:
         r = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
-             "peak_source": "nominal FP64 1.25 TFLOP/s of the GB300 (profiling recipe); no tensor cores used"}
+             "peak_source": "FP64 FMA rate: " + alu_peaks["source"] + "; no tensor cores used"}
     elif prec == "df64":
         # double-float: FP32 instructions, not algorithmic flops, set the ceiling; the
         # HBM fraction is the roofline figure reported, with the ALU figure beside it
@@ -309,7 +327,12 @@ def roofline_for(prec, per_pass, peaks):
               "avg_launch_ms": 1e3 * avg_s,
               "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_flops_per_launch": flops_launch,
               "hbm_gbs_achieved": hbm, "hbm_frac": hbm_frac, "alu_tflops_achieved": alu,
+              "alu_peak_tflops": alu_peak, "alu_frac": alu_frac,
               "share_of_step": tot / sum(v["total_ms"] for v in per_pass.values())})
+    if dom == "update_x":
+        mb = PASS_A_MIN_BYTES[prec] * sites
+        r["hbm_frac_at_min_bytes"] = {"bytes_per_site": PASS_A_MIN_BYTES[prec],
+                                      "frac": mb / avg_s / 1e9 / peaks["hbm_gbs"]}
     return r
 
 
@@ -359,6 +382,7 @@ def run_qfd(args):
     if world > 1:
         dist.barrier()
     peaks, peak_src = read_peaks()
+    alu_peaks = measure_alu_peaks(Q)
     prec = args.precision
 
     clocks = ClockSampler(local)
@@ -381,7 +405,7 @@ def run_qfd(args):
         tuning[other] = pl_o.tuning
         pl_o.close()
         others[other] = {"value": float(N) ** 3 * steps_o / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
-                         "energy_at_end": e_o, "roofline": roofline_for(other, per_pass_o, peaks),
+                         "energy_at_end": e_o, "roofline": roofline_for(other, per_pass_o, peaks, alu_peaks),
                          "step_hbm": step_hbm(other, ms_o / steps_o, peaks),
                          "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass_o.items()}}
     if rank != 0:
@@ -394,7 +418,7 @@ def run_qfd(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded uniform start, analytic potential)",
         "config": workload_config(args, prec),
-        "roofline": roofline_for(prec, per_pass, peaks),
+        "roofline": roofline_for(prec, per_pass, peaks, alu_peaks),
         "step_hbm": step_hbm(prec, ms / steps, peaks),
         "e2e": e2e,
         "gpu_launches": launches,
@@ -402,6 +426,7 @@ def run_qfd(args):
         "energy_at_end": energy,
         "per_pass_ms": {k: v["total_ms"] / v["launches"] for k, v in per_pass.items()},
         "peaks_source": peak_src,
+        "alu_peaks": alu_peaks,
         "other_precisions": others,
         "autotune_ms": tuning,
     }
@@ -418,30 +443,34 @@ def run_qfd(args):
                                     "sample": "skipped: less than 24 GB host memory available"}
     if args.serve > 0:
         line["serve"] = serve_section(torch, Q, dev, args.serve, [int(x) for x in args.serve_sizes.split(",")],
-                                      args.serve_precisions.split(","))
+                                      args.serve_precisions.split(","), cohorts=not args.serve_streams)
     if args.batched_step:
         line["batched_step"] = batched_step_section(torch, Q, dev)
     if args.solve:
         c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
             others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
-        line["solve"] = full_solves(torch, Q, dev, args.solve.split(","), c128_ms)
+        # the complex128 step time at another size: scaled by the sites and the
+        # transform length (5 N log2 N flops a line); stated as an estimate
+        scale = (args.solve_n / N) ** 3 * np.log2(args.solve_n) / np.log2(N)
+        line["solve"] = full_solves(torch, Q, dev, args.solve.split(","), c128_ms * scale, n=args.solve_n)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
     return 0
 
 
-def full_solves(torch, Q, dev, which, ms_step_c128=None):
-    """Ground state of the workload to |dE|/|E| <= 1e-9 (checks every 100 steps,
+def full_solves(torch, Q, dev, which, ms_step_c128=None, n=N):
+    """Ground state of the workload (at lattice size n, same spacing, potential,
+    kinetic term and time step) to |dE|/|E| <= 1e-9 (checks every 100 steps,
     normalisation + parity every 10) in each requested arithmetic; the complex64
     bulk of the mixed forms hands over at tol_bulk or at its FP32 noise floor."""
     out = {}
     stream = torch.cuda.current_stream(dev)
     for prec in which:
-        plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=10, check_every=100, max_steps=400000,
+        plan = Q.Plan(n, A, MASS, DTAU, KIN, precision=prec, ortho_every=10, check_every=100, max_steps=400000,
                       tol=1e-9, tol_bulk=1e-10, stream=stream.cuda_stream)
         plan.fill_potential(*POT)
-        plan.autotune()
+        plan.tuning = plan.autotune()
         plan.fill_psi_uniform(0, SEED)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -449,47 +478,52 @@ def full_solves(torch, Q, dev, which, ms_step_c128=None):
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         hist = plan.history(0)
-        out[prec] = {"energy": es[0], "steps": steps[0], "converged": conv, "seconds": dt,
-                     "solves_per_s": 1.0 / dt, "site_updates_per_s": float(N) ** 3 * steps[0] / dt,
-                     "checks": len(hist), **plan.stats(0)}
+        out[prec] = {"n": n, "energy": es[0], "steps": steps[0], "converged": conv, "seconds": dt,
+                     "solves_per_s": 1.0 / dt, "site_updates_per_s": float(n) ** 3 * steps[0] / dt,
+                     "checks": len(hist), "tuning": plan.tuning if hasattr(plan, "tuning") else None,
+                     **plan.stats(0)}
         plan.close()
-    ref = out.get("df64") or out.get("c128")
+    ref = out.get("c128") or out.get("df64") or out.get("c64_refine")
     if ref:
         for k, v in out.items():
             v["rel_energy_diff_vs_fp64_class"] = abs(v["energy"] - ref["energy"]) / abs(ref["energy"])
-    if ms_step_c128 and "df64" in out and "c128" not in out:
-        # the native complex128 solve runs the same iteration (same step count) at the
-        # measured complex128 step time; estimated, not run (it takes ~35 min at 512^3)
-        st = out["df64"]["steps"]
+    base = out.get("df64") or out.get("c64_refine_df") or out.get("c64_refine")
+    if ms_step_c128 and base and "c128" not in out:
+        # the native complex128 solve runs the same iteration to the same stop
+        # (the step count of an FP64-class solve) at the complex128 step time
+        # measured in the same run; estimated, not run (35 min at 512^3)
+        st = base["steps"]
         out["c128_estimated"] = {"steps": st, "seconds": st * ms_step_c128 / 1e3,
-                                 "solves_per_s": 1e3 / (st * ms_step_c128), "estimated": True}
+                                 "solves_per_s": 1e3 / (st * ms_step_c128), "estimated": True,
+                                 "step_ms": ms_step_c128}
     return out
 
 
-def serve_section(torch, Q, dev, count, sizes, precisions):
+def serve_section(torch, Q, dev, count, sizes, precisions, cohorts=True):
     """A bounded sample of the serving workload: the first `count` requests of
     the seeded Poisson stream (mean 20 req/s; n from `sizes`, weighted 0.4 /
     0.3 / 0.2 / 0.1 toward small lattices; random kinetic term, mass U[1,5],
     1-3 states, Cornell potential, |dE| <= 1e-9 |E| under the tail stop rule),
-    offered in real time to a server with a 150 GB admission budget, once per
-    arithmetic.  Latency runs from a request's arrival to its result."""
+    offered in real time to a server with a 150 GB admission budget (in cohort
+    mode by default), once per arithmetic.  Latency runs from a request's
+    arrival to its result."""
     from paper_2006_16935_gb300 import serve as S
 
     w = dict(zip(S.SIZES, S.WEIGHTS))
     stream = S.poisson_stream(count, sizes=sizes, weights=[w[n] for n in sizes])
     out = {"requests": count, "arrivals": "Poisson, mean 20 req/s (seed 5)", "sizes": list(sizes),
            "spacing_a": stream[0][1]["a"], "tol": 1e-9, "stop_rule": "tail", "budget_gb": 150,
-           "check_every": 100, "ortho_every": 10, "arms": {}}
+           "check_every": 100, "ortho_every": 10, "cohorts": bool(cohorts), "arms": {}}
     energies = {}
     for prec in precisions:
         torch.cuda.synchronize(dev)
-        recs, st = S.serve(stream, prec)
-        summ = S.summarize(recs)
+        recs, st = S.serve(stream, prec, cohorts=cohorts)
+        summ = S.summarize(recs, st)
         summ.update({"graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"],
                      "periods": st["periods"]})
         out["arms"][prec] = summ
         energies[prec] = [r["energy"] for r in recs]
-    ref = next((p for p in ("c128", "df64") if p in energies), None)
+    ref = next((p for p in ("c128", "c64_refine", "df64") if p in energies), None)
     if ref:
         for prec, es in energies.items():
             if prec == ref:
@@ -501,13 +535,21 @@ def serve_section(torch, Q, dev, count, sizes, precisions):
     return out
 
 
-def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_steps=50000):
+BATCH_MODES = {  # name: (max_active, cohorts)
+    "cohorts": (0, True),         # lockstep cohorts per size: one launch per pass over the members
+    "streams": (0, False),        # a stream and a graph per request, periods overlapping on the device
+    "one_at_a_time": (1, False),  # the same solves in turn
+}
+
+
+def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_steps=50000,
+                  modes=("cohorts", "streams", "one_at_a_time")):
     """The batched workload: `count` independent solves (n uniform over
     `sizes`, Cornell + seeded random field, random kinetic term, mass
-    U[1,5], 1-3 states, complex64 bulk + double-float refinement to 1e-9 under
-    the tail rule), all submitted at once to the server so that their
-    CUDA-graph periods overlap on the device, against the same solves run one
-    at a time (max_active = 1)."""
+    U[1,5], 1-3 states, complex64 bulk + refinement to 1e-9 under the tail
+    rule), all submitted at once to the server: in lockstep cohorts (every
+    pass one launch over up to 32 lattices of a size, a cohort period captured
+    as one CUDA graph), on a stream per request, and one at a time."""
     from paper_2006_16935_gb300 import serve as S
 
     stream = S.batch_stream(count, sizes=sizes, max_steps=max_steps)
@@ -516,15 +558,19 @@ def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_st
            "stop_rule": "tail", "precision": precision,
            "potential": "Cornell + Gaussian random field (corr 4 lattice units, std 0.05)", "modes": {}}
     energies = {}
-    for mode, max_active in (("batched", 0), ("one_at_a_time", 1)):
+    for mode in modes:
+        max_active, cohorts = BATCH_MODES[mode]
         torch.cuda.synchronize(dev)
-        recs, st = S.serve(stream, precision, max_active=max_active)
-        summ = S.summarize(recs)
+        recs, st = S.serve(stream, precision, max_active=max_active, cohorts=cohorts)
+        summ = S.summarize(recs, st)
         summ.update({"graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"]})
         out["modes"][mode] = summ
         energies[mode] = [r["energy"] for r in recs]
-    out["batched_speedup"] = out["modes"]["batched"]["solves_per_s"] / out["modes"]["one_at_a_time"]["solves_per_s"]
-    out["identical_energies"] = energies["batched"] == energies["one_at_a_time"]
+    base = "one_at_a_time" if "one_at_a_time" in out["modes"] else modes[-1]
+    for mode in out["modes"]:
+        out["modes"][mode]["speedup_vs_" + base] = \
+            out["modes"][mode]["solves_per_s"] / out["modes"][base]["solves_per_s"]
+    out["identical_energies"] = all(e == energies[modes[0]] for e in energies.values())
     return out
 
 
@@ -596,12 +642,14 @@ def run_batch_only(args):
     clocks = ClockSampler(local)
     clocks.start()
     sec = batch_section(torch, Q, dev, args.batch, [int(x) for x in args.batch_sizes.split(",")],
-                        max_steps=args.batch_max_steps)
+                        precision=args.batch_precision, max_steps=args.batch_max_steps,
+                        modes=tuple(args.batch_modes.split(",")))
     clk = clocks.stop()
     if rank == 0:
+        first = args.batch_modes.split(",")[0]
         line = {"metric": "batch: solves/s of independent solves submitted together",
-                "value": sec["modes"]["batched"]["solves_per_s"], "unit": "solves/s", "n_gpus": world,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64_refine_df",
+                "value": sec["modes"][first]["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.batch_precision,
                 "data": "synthetic", "config": {"workload": "batch of independent solves"}, "batch": sec,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -621,7 +669,7 @@ def run_serve_only(args):
     clocks = ClockSampler(local)
     clocks.start()
     sec = serve_section(torch, Q, dev, args.serve, [int(x) for x in args.serve_sizes.split(",")],
-                        args.serve_precisions.split(","))
+                        args.serve_precisions.split(","), cohorts=not args.serve_streams)
     clk = clocks.stop()
     if rank == 0:
         first = sec["arms"][args.serve_precisions.split(",")[0]]
@@ -643,15 +691,21 @@ def main():
     ap.add_argument("--precision", choices=["c128", "df64", "c64"], default="c128")
     ap.add_argument("--solve", default="", help="comma list of precisions for full 1e-9 solves "
                     "(e.g. c64_refine_df,c64_refine,df64; minutes each)")
+    ap.add_argument("--solve-n", type=int, default=N, help="lattice size of the --solve runs (512 or 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=12, help="requests of the serving sample (0: none)")
     ap.add_argument("--serve-sizes", default="64,128,256")
     ap.add_argument("--serve-precisions", default="c64_refine_df,df64")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving sample")
+    ap.add_argument("--serve-streams", action="store_true",
+                    help="serve with a stream per request instead of lockstep cohorts")
     ap.add_argument("--batch", type=int, default=0, help="solves of the batched workload (with --batch-only)")
     ap.add_argument("--batch-sizes", default="64,96,128,192")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched workload")
     ap.add_argument("--batch-max-steps", type=int, default=50000)
+    ap.add_argument("--batch-precision", default="c64_refine_df")
+    ap.add_argument("--batch-modes", default="cohorts,streams,one_at_a_time",
+                    help="comma list of cohorts, streams, one_at_a_time")
     ap.add_argument("--batched-step", type=int, default=1,
                     help="1: add the lockstep batched-step sample (qfd_step_batch vs qfd_step) to the line")
     args = ap.parse_args()

@@ -29,7 +29,8 @@
  *    synchronise that stream before returning.
  *  - Every call returns a qfd_status; nothing aborts.  After an error,
  *    qfd_last_error() describes it.  A plan is used by one host thread at a time.
- *  - Only lattices N in {8, 16, 32, 64, 128, 256, 512, 1024} are supported.
+ *  - Supported lattices: N in {8, 16, 32, 64, 96, 128, 192, 256, 512, 1024}
+ *    (powers of two, and 96 = 3 * 32, 192 = 3 * 64 with one radix-12 stage).
  */
 #ifndef QFD_H
 #define QFD_H
@@ -49,7 +50,7 @@ typedef enum {
   QFD_ERR_OOM = -2,           /* device allocation failed */
   QFD_ERR_UNSTABLE_DT = -3,   /* dtau * max T(k) >= 2, or 1 + dtau V/2 <= 0 somewhere */
   QFD_ERR_DIVERGED = -4,      /* energy or norm became non-finite */
-  QFD_ERR_TIMEOUT = -5,       /* reserved for bounded waits */
+  QFD_ERR_TIMEOUT = -5,       /* a served request's period overran the server's watchdog (qfd_server_set_timeout) */
   QFD_ERR_CUDA = -6,          /* a CUDA call failed */
   QFD_ERR_NOT_CONVERGED = -7, /* max_steps reached before the tolerance */
   QFD_ERR_STATE = -8          /* call out of order (e.g. stepping before a potential is set) */
@@ -76,7 +77,9 @@ enum { QFD_KIN_FDTD = 0, QFD_KIN_P2 = 1, QFD_KIN_SIN2 = 2, QFD_KIN_REL = 3 };
  *                    transformations (relative rounding about 2^-46 per
  *                    operation, about 2^-48 for stored values);
  *  QFD_C64_REFINE_DF complex64 bulk, then QFD_DF64 refinement. */
-enum { QFD_C128 = 0, QFD_C64 = 1, QFD_C64_REFINE = 2, QFD_DF64 = 3, QFD_C64_REFINE_DF = 4 };
+/* (QFD_C128 and QFD_C64_REFINE keep the numbers 0 and 1 of the two forms the
+ * method statement names: plain FP64 and complex64 with an FP64 refinement.) */
+enum { QFD_C128 = 0, QFD_C64_REFINE = 1, QFD_C64 = 2, QFD_DF64 = 3, QFD_C64_REFINE_DF = 4 };
 /* Parity projection of a state (Eq. (parity)): none, P+, P-. */
 enum { QFD_PAR_NONE = 0, QFD_PAR_EVEN = 1, QFD_PAR_ODD = -1 };
 /* Potential centre (Sec. 1.3 / 5.3): the grid site (N/2, N/2, N/2) with the
@@ -131,11 +134,13 @@ typedef struct {
  * update would not decay).  Sections 2.1-2.2. *out is NULL on failure. */
 qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out);
 
-/* Releases the plan and its device memory (NULL is ignored). */
+/* Releases the plan and its device memory (NULL is ignored).  Library
+ * bookkeeping: no counterpart in the paper. */
 void qfd_destroy(qfd_plan_t plan);
 
 /* Message of the last error on `plan` (or of the last failed qfd_plan call of
- * this thread when plan is NULL).  Owned by the library. */
+ * this thread when plan is NULL).  Owned by the library.  Library
+ * bookkeeping: no counterpart in the paper. */
 const char* qfd_last_error(qfd_plan_t plan);
 
 /* Copies a real potential V (N^3 doubles, [x][y][z]) and derives the update
@@ -165,8 +170,11 @@ qfd_status qfd_add_random_field(qfd_plan_t plan, uint64_t seed, double corr, dou
 qfd_status qfd_get_potential(qfd_plan_t plan, double* V, int on_device);
 
 /* Copies state `state` in (interleaved complex128, N^3 sites) and resets its
- * step counter.  Complex64 and double-float plans round the values to their
- * representation. */
+ * step counter: the paper's initial condition read from stored wave-functions
+ * (INITCONDTYPE 0, Sec. 5.2), here from a caller's buffer instead of files.
+ * Complex64 and double-float plans round the values to their representation.
+ * Non-finite values are copied as they are: a later solve reports them as
+ * QFD_ERR_DIVERGED at its first energy check. */
 qfd_status qfd_set_psi(qfd_plan_t plan, int state, const double* psi, int on_device);
 
 /* Fills state `state` on the device with Re, Im i.i.d. U[-1, 1) from the
@@ -175,7 +183,10 @@ qfd_status qfd_set_psi(qfd_plan_t plan, int state, const double* psi, int on_dev
  * (part 0 = Re, 1 = Im); resets the step counter. */
 qfd_status qfd_fill_psi_uniform(qfd_plan_t plan, int state, uint64_t seed);
 
-/* Copies state `state` out (interleaved complex128) into the caller's buffer. */
+/* Copies state `state` out (interleaved complex128) into the caller's buffer:
+ * the wave-function output of the paper (SAVEWAVEFNCS, Sec. 5.1: the full 3D
+ * wave-functions at the end of a run), into memory instead of files.  A
+ * pending normalisation factor is applied first. */
 qfd_status qfd_get_psi(qfd_plan_t plan, int state, double* out, int on_device);
 
 /* Observables of `state` in lattice units, d = x - centre per axis (FP64):
@@ -212,16 +223,15 @@ qfd_status qfd_step(qfd_plan_t plan, int state, int64_t nsteps);
  * (projection, deflation, normalisation) runs per plan.  There is no
  * counterpart in the paper, whose code steps one lattice.
  *   plans, states  arrays of `count` entries, 1 <= count <= QFD_MAX_BATCH;
- *                  the plans are distinct, have the same n <= 256 (a
- *                  larger lattice fills the GPU alone), the same current
+ *                  the plans are distinct, have the same n, the same current
  *                  arithmetic and FFT kinetic terms (kinetic 1..3), and a
  *                  potential; their parameters may differ otherwise.
  *   nsteps         >= 0.
- * Launch shapes: the batched passes use the default shapes (not those chosen
- * by qfd_autotune / qfd_set_tuning).  With default shapes on every plan the
- * double-float states are bit-identical to qfd_step's; complex128 and
- * complex64 states agree with them to rounding (the compiler may contract a
- * product and a sum into an FMA differently in the batched kernels).
+ * Kernels and launch shapes: qfd_step runs the same step kernels over a batch
+ * of one lattice, so with the same launch shapes every plan's state is
+ * bit-identical to what qfd_step gives it.  The batch takes plans[0]'s launch
+ * shapes (qfd_autotune / qfd_set_tuning; the choice depends only on n and the
+ * arithmetic).
  * Streams: the work runs on plans[0]'s stream; each other plan's stream is
  * ordered before it and after it with events, and the call returns after
  * every plan's work has completed (as qfd_step does).
@@ -230,7 +240,9 @@ qfd_status qfd_step(qfd_plan_t plan, int state, int64_t nsteps);
  * arithmetic or kinetic kind (message in qfd_last_error of plans[0], or of NULL when plans
  * is NULL or count is out of range); QFD_ERR_STATE for a plan without a
  * potential; a launch error as QFD_ERR_CUDA.  Nothing is stepped when an
- * argument is rejected. */
+ * argument is rejected.  After a failure inside the loop every plan's state,
+ * work lattice and step counter still agree with each other, but the number
+ * of steps taken, and whether the last step's cadence ran, are unspecified. */
 qfd_status qfd_step_batch(const qfd_plan_t* plans, const int* states, int count, int64_t nsteps);
 
 /* Rayleigh energy <psi|H_K + V|psi> / <psi|psi> of `state` (FP64 sums;
@@ -269,24 +281,35 @@ qfd_status qfd_solve_states(qfd_plan_t plan, int nstates, const int* parity, dou
 qfd_status qfd_snapshot_states(qfd_plan_t plan, int nout, int parity, int64_t snap_every, double* E_out,
                                int64_t* steps_out);
 
-/* Launch-shape autotuner (a tuning of this implementation; the paper has no
- * counterpart).  For every arithmetic the plan uses, times the y passes with
- * tiles of the default width and of twice that width, and the z pass with
- * one and with two line groups per CTA, on the work lattice (5 launches each
- * after 2 warm-ups), and keeps the faster of each for later launches.  The
- * choices change how work is tiled, not the arithmetic of any line: results
- * agree to rounding whatever is chosen (complex128 / complex64 kernels may
- * differ in where the compiler fuses a multiply-add; double-float ones are
- * bit-identical).  ms_out (NULL or 12 doubles): per
+/* Launch-shape and radix-schedule autotuner (a tuning of this implementation;
+ * the paper has no counterpart).  For every arithmetic the plan uses, times
+ * the y passes with tiles of the default width and of twice that width, the
+ * z pass with one and with two line groups per CTA, for complex64 at
+ * n = 128..1024 also both passes with the two-stage radix schedule (radix
+ * 16.8, 16.16, 32.16 or 32.32 with 16 or 32 elements per thread: one
+ * shared-memory exchange per transform instead of two or three), and (once a
+ * potential is set, FFT kinetic terms) pass A with tiles of the default width
+ * and of half of it at two CTAs per SM, on the work lattice and the spare
+ * state lattice (5 launches each after 2 warm-ups), and keeps the fastest of
+ * each for later launches.  Tilings do not change the arithmetic of a line;
+ * the radix schedule changes the order of the operations of a transform.
+ * Results agree to rounding whatever is chosen (complex128 / complex64
+ * kernels may also differ in where the compiler fuses a multiply-add;
+ * double-float tilings are bit-identical).  ms_out (NULL or 24 doubles): per
  * policy (0 complex128, 1 complex64, 2 double-float) the median times of
- * y-default, y-wide, z-1, z-2 in ms (NaN for unused policies).  Synchronises;
- * the work lattice is recomputed at the next step. */
+ * y-default, y-wide, y-two-stage, z-1, z-2, z-two-stage, x-default, x-half in
+ * ms (NaN where not timed).  Synchronises; the work lattice is recomputed at
+ * the next step. */
 qfd_status qfd_autotune(qfd_plan_t plan, double* ms_out);
 
 /* Sets the launch shapes of one policy (0 complex128, 1 complex64, 2
- * double-float) by hand: y_variant 0 default width, 1 twice it; z_variant
- * -1 the policy's default grouping, 0 one line group, 1 two. */
-qfd_status qfd_set_tuning(qfd_plan_t plan, int policy, int y_variant, int z_variant);
+ * double-float) by hand: y_variant 0 default width, 1 twice it, 2 the
+ * two-stage radix schedule; z_variant -1 the policy's default grouping, 0 one
+ * line group, 1 two, 2 the two-stage radix schedule; x_variant 0 pass A's
+ * default tile width, 1 half of it (two CTAs per SM).  The two-stage
+ * schedule exists for complex64 at n = 128..1024; elsewhere 2 runs the
+ * default schedule. */
+qfd_status qfd_set_tuning(qfd_plan_t plan, int policy, int y_variant, int z_variant, int x_variant);
 
 /* Replaces the plan's max_steps, tol and tol_bulk (same meaning as in
  * qfd_params) for later qfd_solve_states calls. */
@@ -324,6 +347,17 @@ qfd_status qfd_timing_reset(qfd_plan_t plan);
 qfd_status qfd_timing_query(qfd_plan_t plan, int kind, int64_t* launches, double* total_ms);
 int64_t qfd_launch_count(qfd_plan_t plan);
 
+/* Measured FMA issue rate of one vector pipe of the current device, in
+ * TFLOP/s (2 flops per FMA): fp64 = 1 the FP64 pipe, 0 the FP32 pipe.  A
+ * measurement utility with no counterpart in the paper: it is the roofline
+ * denominator of the passes bound by vector arithmetic instead of HBM (the
+ * complex128 transforms; no tensor cores are used).  Every thread of a grid
+ * of 8 CTAs of 256 threads per SM runs 8 independent FMA chains; one warm-up
+ * launch, then the best of five timed with CUDA events on the legacy default
+ * stream (about 0.1 s each).  Allocates and frees a small device buffer and
+ * synchronises. */
+qfd_status qfd_fma_rate(int fp64, double* tflops);
+
 /* Rayleigh energy <psi|H_K + V|psi> / <psi|psi> and sum |psi|^2 of a lattice
  * that lives in the caller's device memory, computed in FP64 without
  * allocating any device memory.  There is no counterpart in the paper: this
@@ -333,13 +367,18 @@ int64_t qfd_launch_count(qfd_plan_t plan);
  * stall).  Its scratch (work lattice, partial sums, tables) is one static
  * device array of about 33 MiB that every GPU loading this library holds
  * until exit; it bounds the lattice to n <= 128 (QFD_ERR_ARG above that).
- * psi: device, interleaved complex128, n^3 sites [x][y][z]; V: device, n^3
- * doubles; a, mass, kinetic, rest_mass as in qfd_params; stream: cudaStream_t
- * or NULL.  E and norm2 are host outputs (either may be NULL); the call
+ * psi: device, interleaved complex128, n^3 sites [x][y][z], read only; V:
+ * device, n^3 doubles, read only; a, mass, rest_mass as in qfd_params;
+ * kinetic: one of the FFT kinetic terms 1..3 (Eqs. HK1-HK3) only, since
+ * H_K(0) has no Parseval form (QFD_ERR_ARG for 0); stream: cudaStream_t or
+ * NULL.  E and norm2 are host outputs (either may be NULL); the call
  * synchronises the stream.  The array is shared by every call and keeps the
  * last call's contents; calls that overlap on the GPU race on it.  The first
  * call on a device looks up the array's device address (with that device
- * current); make it before any stream capture. */
+ * current) and keeps it for the process; make that first call before any
+ * stream capture.  A cudaDeviceReset destroys the array with the context, so
+ * after one this entry point must not be called again on that device in the
+ * same process. */
 qfd_status qfd_energy_noalloc(const double* psi, const double* V, int64_t n, double a, double mass, int kinetic,
                               int rest_mass, void* stream, double* E, double* norm2);
 
@@ -360,7 +399,19 @@ size_t qfd_plan_bytes(const qfd_params* params);
  * each request whose period ended, moves it to its next phase or state, and
  * returns the results of the requests that finished.  From the second period
  * of a phase on, a request's period is captured once as a CUDA graph and
- * replayed.  A request's numbers are the same alone and in any mix. */
+ * replayed.  A request's numbers are the same alone and in any mix.
+ *
+ * Cohort mode (cohorts = 1): admitted requests of one lattice size share a
+ * stream in cohorts of up to QFD_MAX_BATCH and advance together, one period of
+ * every member per cohort period, each pass of each step one launch over the
+ * members of one arithmetic (the lockstep batches of qfd_step_batch, with the
+ * energy checks batched too); the cadence and the stop rule stay per request.
+ * Once no member is in the first period of a phase, a cohort period is
+ * captured as one CUDA graph and replayed while the members and their states
+ * and phases are unchanged.  Stream priority rises as the lattice shrinks, as
+ * for single requests.  The step kernels are the same as a lone plan's, so a
+ * request's numbers are bit-identical in a cohort, alone, without cohorts and
+ * through qfd_solve_states. */
 typedef struct qfd_server_s* qfd_server_t;
 
 typedef struct {
@@ -370,6 +421,8 @@ typedef struct {
   int32_t ortho_every;     /* projection / normalisation cadence of every request */
   int32_t use_graphs;      /* 1: capture a request's period once per phase and replay it */
   void* stream;            /* cudaStream_t whose queued work admitted requests follow, or NULL */
+  int32_t cohorts;         /* 1: lockstep cohorts of requests of one size (see above); 0: a stream per request */
+  int32_t reserved;        /* 0 */
 } qfd_server_params;
 
 typedef struct {
@@ -409,6 +462,18 @@ qfd_status qfd_server_submit(qfd_server_t server, const qfd_request* request, in
 /* One scheduling round (see above); up to `capacity` finished results are
  * written to out, the rest stay for the next call. */
 qfd_status qfd_server_poll(qfd_server_t server, qfd_result* out, int capacity, int* count);
+/* Watchdog on the periods in flight (a serving safeguard; the paper has no
+ * counterpart): a period still unfinished `seconds` after it was queued (time
+ * spent waiting behind other requests' work counts) ends its request with
+ * QFD_ERR_TIMEOUT in its qfd_result; the work already queued for it still
+ * runs to its end on the device before its memory is released, and the other
+ * requests go on.  0 (the default) turns the watchdog off.  QFD_ERR_ARG for a
+ * negative or non-finite value. */
+qfd_status qfd_server_set_timeout(qfd_server_t server, double seconds);
+/* Kernel launches the server has queued so far: direct launches plus the
+ * launches held by every replayed CUDA graph (server instrumentation; no
+ * counterpart in the paper). */
+qfd_status qfd_server_kernels(qfd_server_t server, int64_t* kernels);
 qfd_status qfd_server_stats(qfd_server_t server, int* waiting, int* active, double* used_bytes, int64_t* periods,
                             int64_t* graph_replays, int64_t* graph_captures);
 

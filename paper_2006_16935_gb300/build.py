@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libqfd.so")
 POLICIES = ["DF", "F64", "F32"]  # slowest first
 SIZES = [1024, 512, 256, 192, 128, 96, 64, 32, 16, 8]
 UNITS = ([("qfd_inst.cu", f"inst_{p}_{n}", ["-DQFD_POLICY=" + p, f"-DQFD_N={n}"]) for p in POLICIES for n in SIZES]
-         + [("qfd_api.cu", "api", []), ("qfd_noalloc.cu", "noalloc", [])])
+         + [("qfd_api.cu", "api", []), ("qfd_noalloc.cu", "noalloc", []), ("qfd_peaks.cu", "peaks", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -123,16 +123,18 @@ __global__ void k_potential(double* __restrict__ V, int64_t n, double a, int kin
   }
 }
 
-// Update coefficients of Sec. 2.2 from V, per arithmetic: FP64 {A, B dtau};
-// FP32 and double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64;
-// and, for plans with an FP32-pipe arithmetic, V split into double-float
-// pairs (the energy sums of those arithmetics read it).
+// Update coefficients of Sec. 2.2 from V, per arithmetic: FP64 {A, B dtau}
+// (complex128 pass A reads them precomputed); for H_K(0) plans also FP32 and
+// double-float {B dtau, 1 - A} with 1 - A = dtau V B formed in FP64 (the FFT
+// passes of those arithmetics derive them from V instead); V split into
+// double-float pairs (the energy sums of the FP32-pipe arithmetics and the
+// double-float pass A read it) and rounded to FP32 (the complex64 pass A).
 // fdtd_c > 0 (H_K(0) plans, c = 1 / (2 M A^2)): the coefficients take the
 // stencil's diagonal in, so that the update applied to the neighbour sum S
 // gives A psi - B dtau c (6 psi - S) = (A - 6 c B dtau) psi + c B dtau S.
 __global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, double fdtd_c,
                        double2* __restrict__ c64, dfc* __restrict__ cdf, float2* __restrict__ c32,
-                       df* __restrict__ vdf, int* __restrict__ bad) {
+                       df* __restrict__ vdf, float* __restrict__ v32, int* __restrict__ bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = V[i];
     const double h = 0.5 * dtau * v;
@@ -149,6 +151,7 @@ __global__ void k_coef(const double* __restrict__ V, int64_t n3, double dtau, do
     if (cdf) cdf[i] = dfc{dsplit(g1), dsplit(g2)};
     if (c32) c32[i] = float2{(float)g1, (float)g2};
     if (vdf) vdf[i] = dsplit(v);
+    if (v32) v32[i] = (float)v;
   }
 }
 
@@ -398,8 +401,9 @@ struct qfd_plan_s {
   char* spare16 = nullptr;
   char* spare32 = nullptr;
   double2* W = nullptr;     // work lattice (16 bytes per site; complex64 uses half)
-  void* coef16 = nullptr;   // F64 {A, B dtau} or DF {B dtau, 1 - A}
-  float2* coef32 = nullptr;
+  void* coef16 = nullptr;   // F64 {A, B dtau}, or (H_K(0) plans) DF {B dtau, 1 - A}
+  float2* coef32 = nullptr;  // (H_K(0) plans) complex64 {B dtau, 1 - A}
+  float* V32 = nullptr;      // V in FP32 (complex64 pass A of the FFT kinetic terms)
   double* V = nullptr;
   df* Vdf = nullptr;        // V as double-float pairs (plans with an FP32-pipe arithmetic)
   double2* tw64 = nullptr;
@@ -415,12 +419,13 @@ struct qfd_plan_s {
   double* scal = nullptr;
   float* scalf = nullptr;  // the normalisation factor in FP32 and double-float form
   int* flag = nullptr;
-  int* errflag = nullptr;  // set by a kernel whose bounded wait for a bulk copy ran out
-  double* hscal = nullptr;  // pinned host copy of the scalars (+ the error flag)
+  double* hscal = nullptr;  // pinned host copy of the scalars
   // host-side state
   KinParams kin{};
   int tune_vy[3] = {0, 0, 0};     // launch shapes per policy id (autotuner; see LaunchArgs)
   int tune_vz[3] = {-1, -1, -1};
+  int tune_vx[3] = {0, 0, 0};
+  UpdParams up{};  // dtau in the representations of the V-derived coefficients
   int lg = -1;          // n = 2^lg, or -1 (n = 96, 192)
   double fdtd_c = 0.0;  // 1 / (2 M A^2) of H_K(0)
   int arith16 = 0;  // policy id of the 16-byte representation: 0 F64, 2 DF
@@ -547,7 +552,15 @@ template <class A> const typename A::VT* v_of(qfd_plan_t pl) {
   if constexpr (A::id == 0) return pl->V;
   else return pl->Vdf;
 }
+// the H_K(0) update's coefficient array
 template <class A> const void* coef_of(qfd_plan_t pl) { return A::id == 1 ? (const void*)pl->coef32 : pl->coef16; }
+// pass A's per-site input for the FFT kinetic terms: {A, B dtau} (F64), V in
+// FP32 (F32) or as double-float pairs (DF)
+template <class A> const void* uin_of(qfd_plan_t pl) {
+  if constexpr (A::id == 0) return pl->coef16;
+  else if constexpr (A::id == 1) return pl->V32;
+  else return pl->Vdf;
+}
 template <class A> const void* tw_of(qfd_plan_t pl) {
   return A::id == 0 ? (const void*)pl->tw64 : A::id == 1 ? (const void*)pl->tw32 : (const void*)pl->twdf;
 }
@@ -571,24 +584,20 @@ LaunchArgs base_args(qfd_plan_t pl) {
   a.tw = tw_of<A>(pl);
   a.ktab = ktab_of<A>(pl);
   a.kin = &pl->kin;
-  a.coef = coef_of<A>(pl);
+  a.coef = uin_of<A>(pl);
+  a.up = &pl->up;
   a.V = v_of<A>(pl);
-  a.err = pl->errflag;
   a.stream = pl->st;
   a.vy = pl->tune_vy[A::id];
   a.vz = pl->tune_vz[A::id];
+  a.vx = pl->tune_vx[A::id];
   return a;
 }
 
-// QFD_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check.
-qfd_status check_kernel_errors(qfd_plan_t pl) {
-  int e = 0;
-  QFD_CK(cudaMemcpyAsync(&e, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
+// Waits for the plan's stream; an error of any kernel queued on it surfaces
+// here as QFD_ERR_CUDA.
+qfd_status sync_checked(qfd_plan_t pl) {
   QFD_CK(cudaStreamSynchronize(pl->st));
-  if (e) {
-    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
-    return fail(pl, QFD_ERR_TIMEOUT, "a bulk copy did not complete within the kernel's bounded wait");
-  }
   return QFD_OK;
 }
 
@@ -807,7 +816,7 @@ qfd_status energy_tail(qfd_plan_t pl, double* E, double* n2) {
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   double h[SC_COUNT];
   QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
-  if ((r = check_kernel_errors(pl)) != QFD_OK) return r;
+  if ((r = sync_checked(pl)) != QFD_OK) return r;
   if (E) *E = h[SC_E];
   if (n2) *n2 = h[SC_N2];
   return QFD_OK;
@@ -826,7 +835,7 @@ qfd_status energy_full(qfd_plan_t pl, int s, double* E, double* n2) {
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   double h[SC_COUNT];
   QFD_CK(cudaMemcpyAsync(h, pl->scal, sizeof(h), cudaMemcpyDeviceToHost, pl->st));
-  if ((r = check_kernel_errors(pl)) != QFD_OK) return r;
+  if ((r = sync_checked(pl)) != QFD_OK) return r;
   if (E) *E = h[SC_E];
   if (n2) *n2 = h[SC_N2];
   return QFD_OK;
@@ -851,9 +860,9 @@ qfd_status begin_phase(qfd_plan_t pl, int s) {
 }
 
 // check_every steps and the energy of their last state; the scalars (E at
-// SC_E, N2 at SC_N2) and the kernel error flag are copied asynchronously into
-// `host` (pinned, SC_COUNT doubles followed by one int).  Nothing here
-// synchronises, so a period can be captured into a CUDA graph.
+// SC_E, N2 at SC_N2) are copied asynchronously into `host` (pinned, SC_COUNT
+// doubles).  Nothing here synchronises, so a period can be captured into a
+// CUDA graph.
 template <class A>
 qfd_status period_launch(qfd_plan_t pl, int s, double* host) {
   qfd_status r;
@@ -868,7 +877,6 @@ qfd_status period_launch(qfd_plan_t pl, int s, double* host) {
   }
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   QFD_CK(cudaMemcpyAsync(host, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, pl->st));
-  QFD_CK(cudaMemcpyAsync(host + SC_COUNT, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
   return QFD_OK;
 }
 
@@ -899,12 +907,6 @@ struct PhaseTracker {
 qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, bool bulk, PhaseTracker& tr,
                        bool* done, double* e_out) {
   const double e = host[SC_E], n2 = host[SC_N2];
-  int kerr = 0;
-  std::memcpy(&kerr, host + SC_COUNT, sizeof(int));
-  if (kerr) {
-    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
-    return fail(pl, QFD_ERR_TIMEOUT, "a bulk copy did not complete within the kernel's bounded wait");
-  }
   if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
     return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
   pl->hist[s].push_back({pl->t[s], e});
@@ -1021,26 +1023,61 @@ qfd_status time_launch(qfd_plan_t pl, F&& f, int warm, int reps, double* ms) {
   return QFD_OK;
 }
 
-// Times both y-tile widths and both z-pass groupings of policy A on the work
-// lattice and keeps the faster of each.
+// Whether lattice size n has the two-stage radix schedule in policy A.
+template <class A> bool has_two_stage(int64_t n) {
+  bool out = false;
+  dispatch_n(n, [&](auto t) {
+    out = Shape<A, decltype(t)::value>::HAS_R1;
+    return cudaSuccess;
+  });
+  return out;
+}
+
+// Index of the smallest of the first k timings.
+int argmin(const double* ms, int k) {
+  int b = 0;
+  for (int i = 1; i < k; ++i)
+    if (ms[i] < ms[b]) b = i;
+  return b;
+}
+
+// Times the y-pass shapes (default width, twice it, and - complex64 - the
+// two-stage radix schedule), the z-pass shapes (one or two line groups, and
+// the two-stage schedule) and both pass-A tile widths of policy A (pass A on
+// the work lattice and the spare state lattice, which hold nothing yet to be
+// kept) and keeps the fastest of each.  ms[0..2] y, ms[3..5] z, ms[6..7] x.
 template <class A>
 qfd_status autotune_policy(qfd_plan_t pl, double* ms) {
   qfd_status r;
   QFD_CK(cudaMemsetAsync(pl->W, 0, (size_t)pl->n3 * sizeof(double2), pl->st));
-  for (int v = 0; v < 2; ++v) {
+  QFD_CK(cudaMemsetAsync(spare_of<A>(pl), 0, (size_t)pl->n3 * sizeof(typename A::C), pl->st));
+  const int nv = has_two_stage<A>(pl->p.n) ? 3 : 2;
+  for (int v = 0; v < nv; ++v) {
     LaunchArgs a = base_args<A>(pl);
     a.vy = v;
     if ((r = time_launch(pl, [&]() { return launch_fft_y<A>(a, -1); }, 2, 5, &ms[v])) != QFD_OK) return r;
   }
-  for (int v = 0; v < 2; ++v) {
+  for (int v = 0; v < nv; ++v) {
     LaunchArgs a = base_args<A>(pl);
     a.vz = v;
     a.stats = 0;
     a.part = pl->partC;
-    if ((r = time_launch(pl, [&]() { return launch_zpass<A>(a, nullptr); }, 2, 5, &ms[2 + v])) != QFD_OK) return r;
+    if ((r = time_launch(pl, [&]() { return launch_zpass<A>(a, nullptr); }, 2, 5, &ms[3 + v])) != QFD_OK) return r;
   }
-  pl->tune_vy[A::id] = ms[1] < ms[0] ? 1 : 0;
-  pl->tune_vz[A::id] = ms[3] < ms[2] ? 1 : 0;
+  if (pl->p.kinetic != 0 && pl->has_pot) {
+    for (int v = 0; v < 2; ++v) {
+      LaunchArgs a = base_args<A>(pl);
+      a.vx = v;
+      a.psi = spare_of<A>(pl);
+      a.part = pl->partA;
+      a.stats = STATS_NONE;
+      if ((r = time_launch(pl, [&]() { return launch_update_x<A>(a, nullptr); }, 2, 5, &ms[6 + v])) != QFD_OK)
+        return r;
+    }
+    pl->tune_vx[A::id] = argmin(ms + 6, 2);
+  }
+  pl->tune_vy[A::id] = argmin(ms, nv);
+  pl->tune_vz[A::id] = argmin(ms + 3, nv);
   return QFD_OK;
 }
 
@@ -1073,7 +1110,7 @@ qfd_status derive_coefficients(qfd_plan_t pl) {
   dfc* cdf = (pl->coef16 && pl->arith16 == 2) ? (dfc*)pl->coef16 : nullptr;
   QFD_RUN(PASS_OTHER, (k_coef<<<grid_for(pl->n3), 256, 0, pl->st>>>(pl->V, pl->n3, pl->p.dtau,
                                                                      pl->p.kinetic == 0 ? pl->fdtd_c : 0.0, c64,
-                                                                     cdf, pl->coef32, pl->Vdf, pl->flag),
+                                                                     cdf, pl->coef32, pl->Vdf, pl->V32, pl->flag),
                        cudaGetLastError()));
   int bad = 0;
   QFD_CK(cudaMemcpyAsync(&bad, pl->flag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
@@ -1090,14 +1127,24 @@ bool uses16(int precision) { return precision != QFD_C64; }
 bool uses32(int precision);
 // any arithmetic on the FP32 pipe (complex64 or double-float)
 bool uses_vdf(int precision) { return precision != QFD_C128; }
+int arith16_of(int precision) { return (precision == QFD_DF64 || precision == QFD_C64_REFINE_DF) ? 2 : 0; }
+// Which per-site update arrays a plan holds: the FP64 coefficients (complex128
+// pass A, and every 16-byte H_K(0) update), the complex64 H_K(0) coefficients,
+// and V in FP32 (complex64 pass A of the FFT terms).
+bool needs_coef16(const qfd_params& p) { return uses16(p.precision) && (arith16_of(p.precision) == 0 || p.kinetic == 0); }
+bool needs_coef32(const qfd_params& p) { return uses32(p.precision) && p.kinetic == 0; }
+bool needs_v32(const qfd_params& p) { return uses32(p.precision) && p.kinetic != 0; }
 // Device bytes a plan with these parameters allocates (lattices, tables, partials).
 size_t plan_device_bytes(const qfd_params& p) {
   const size_t n = (size_t)p.n, n3 = n * n * n;
   const size_t npart = (size_t)std::max(
       std::max(std::max(max_partials<F64>(p.n), max_partials<F32>(p.n)), max_partials<DF>(p.n)), GS_BLOCKS);
   size_t b = n3 * 16 + n3 * 8 + n * (16 + 8 + 16 + 8 + 4 + 8) + npart * 8 * (3 + 2 * MAX_LOWER) + 1024;
-  if (uses16(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 16;
-  if (uses32(p.precision)) b += (size_t)(p.nstates + 2) * n3 * 8;
+  if (uses16(p.precision)) b += (size_t)(p.nstates + 1) * n3 * 16;
+  if (uses32(p.precision)) b += (size_t)(p.nstates + 1) * n3 * 8;
+  if (needs_coef16(p)) b += n3 * 16;
+  if (needs_coef32(p)) b += n3 * 8;
+  if (needs_v32(p)) b += n3 * sizeof(float);
   if (uses_vdf(p.precision)) b += n3 * sizeof(df);
   return b;
 }
@@ -1106,84 +1153,148 @@ bool uses32(int precision) {
 }
 bool refines(int precision) { return precision == QFD_C64_REFINE || precision == QFD_C64_REFINE_DF; }
 
-// qfd_step_batch after its checks, with every plan's stream pointed at
-// plans[0]'s: per step, the lattices whose W holds the forward x transform
-// take passes B, C and D as three batched launches (any other advances
-// alone), then pass A runs as one batched launch per partial-sum mode; the
-// cadence and the bookkeeping are step_once's, per plan.
+// One step of Eq. (iter_proced) for `count` lattices of one size in
+// arithmetic A, with exactly the operations step_once applies to each lattice
+// (check = 1: the energy-check step of a period), but each pass one launch
+// over the lattices: the lattices whose W holds the forward x transform take
+// passes B, C and D as three batched launches (any other advances alone),
+// then pass A runs as one batched launch per partial-sum mode; the cadence
+// and the bookkeeping are step_once's, per plan.  Every plan's stream must be
+// `st` (the caller arranges it).
 template <class A>
-qfd_status step_batch(qfd_plan_s* const* pls, const int* ss, int count, int64_t nsteps) {
+qfd_status batch_step_once(qfd_plan_s* const* pls, const int* ss, int count, int check, cudaStream_t st) {
   qfd_plan_t p0 = pls[0];
   const int64_t n = p0->p.n;
+  // launch shapes: plans[0]'s (the choice depends only on n and the arithmetic)
+  const int vy = p0->tune_vy[A::id], vz = p0->tune_vz[A::id], vx = p0->tune_vx[A::id];
   qfd_status r;
-  for (int64_t it = 0; it < nsteps; ++it) {
-    BatchY by{};
-    BatchZ bz{};
-    int nx = 0;
-    for (int i = 0; i < count; ++i) {
-      qfd_plan_t pl = pls[i];
-      if ((r = ensure_w<A>(pl, ss[i])) != QFD_OK) return r;
-      if (pl->w_stage == ST_X) {
-        by.W[nx] = bz.W[nx] = pl->W;
-        by.tw[nx] = bz.tw[nx] = tw_of<A>(pl);
-        bz.ktab[nx] = ktab_of<A>(pl);
-        bz.kp[nx] = pl->kin;
-        ++nx;
-      } else if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) {
-        return r;
-      }
-    }
-    if (nx > 0) {
-      qfd_plan_t pl = p0;  // the batched launches are counted and timed on plans[0]
-      QFD_RUN(PASS_FWD_Y, launch_fft_y_batch<A>(n, by, nx, -1, p0->st));
-      QFD_RUN(PASS_ZKIN, launch_zpass_batch<A>(n, bz, nx, p0->st));
-      QFD_RUN(PASS_INV_Y, launch_fft_y_batch<A>(n, by, nx, +1, p0->st));
-    }
-    // pass A: STATS_NORM for the lattices whose next step ends in a cadence
-    // without a projection (the partials feed the normalisation), else none
-    BatchU bu[2] = {};
-    int nu[2] = {0, 0};
-    uint32_t scaled[2] = {0u, 0u};
-    for (int i = 0; i < count; ++i) {
-      qfd_plan_t pl = pls[i];
-      const int s = ss[i];
-      const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
-      const int g = ortho_next && !projects(pl, s) ? 1 : 0;
-      const int j = nu[g]++;
-      BatchU& b = bu[g];
-      b.W[j] = pl->W;
-      b.psi[j] = psi_of<A>(pl, s);
-      b.coef[j] = coef_of<A>(pl);
-      b.V[j] = v_of<A>(pl);
-      b.scale[j] = pl->scal + SC_SCALE;
-      b.scale_f[j] = pl->scalf;
-      b.tw[j] = tw_of<A>(pl);
-      b.part[j] = pl->partA;
-      if (pl->pending) scaled[g] |= 1u << j;
-    }
-    int nb = 0;
-    for (int g = 0; g < 2; ++g) {
-      if (nu[g] == 0) continue;
-      qfd_plan_t pl = p0;
-      QFD_RUN(PASS_UPDATE_X,
-              launch_update_x_batch<A>(n, bu[g], nu[g], scaled[g], g ? STATS_NORM : STATS_NONE, p0->st, &nb));
-    }
-    for (int i = 0; i < count; ++i) {
-      qfd_plan_t pl = pls[i];
-      const int s = ss[i];
-      pl->nA = nb;
-      pl->w_stage = ST_X;
-      pl->pending = false;
-      pl->t[s] += 1;
-      if (pl->t[s] % pl->p.ortho_every == 0) {
-        if ((r = cadence<A>(pl, s, 0)) != QFD_OK) return r;
-        if (pl->snap_every > 0 && s == 0 && pl->t[s] % pl->snap_every == 0 && (r = take_snapshot<A>(pl)) != QFD_OK)
-          return r;
-      }
+  BatchY by{};
+  BatchZ bz{};
+  int nx = 0;
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    if ((r = ensure_w<A>(pl, ss[i])) != QFD_OK) return r;
+    if (pl->w_stage == ST_X) {
+      by.W[nx] = bz.W[nx] = pl->W;
+      by.tw[nx] = bz.tw[nx] = tw_of<A>(pl);
+      bz.ktab[nx] = ktab_of<A>(pl);
+      bz.kp[nx] = pl->kin;
+      ++nx;
+    } else if ((r = advance_to_d<A>(pl, 0)) != QFD_OK) {
+      return r;
     }
   }
+  if (nx > 0) {
+    qfd_plan_t pl = p0;  // the batched launches are counted and timed on plans[0]
+    QFD_RUN(PASS_FWD_Y, launch_fft_y_batch<A>(n, by, nx, -1, vy, st));
+    QFD_RUN(PASS_ZKIN, launch_zpass_batch<A>(n, bz, nx, 0, vz, st, nullptr));
+    QFD_RUN(PASS_INV_Y, launch_fft_y_batch<A>(n, by, nx, +1, vy, st));
+  }
+  // pass A, grouped by partial-sum mode as step_once chooses it: STATS_NORM
+  // where the step ends in a cadence without a projection, STATS_FULL on the
+  // check step (unless a projection recomputes the partials), else none
+  BatchU bu[3] = {};
+  int nu[3] = {0, 0, 0};
+  uint32_t scaled[3] = {0u, 0u, 0u};
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    const int s = ss[i];
+    const bool ortho_next = (pl->t[s] + 1) % pl->p.ortho_every == 0;
+    int g = STATS_NONE;
+    if (ortho_next) g = projects(pl, s) ? STATS_NONE : (check ? STATS_FULL : STATS_NORM);
+    else if (check) g = STATS_FULL;
+    const int j = nu[g]++;
+    BatchU& b = bu[g];
+    b.W[j] = pl->W;
+    b.psi[j] = psi_of<A>(pl, s);
+    b.u[j] = uin_of<A>(pl);
+    b.up[j] = pl->up;
+    b.V[j] = v_of<A>(pl);
+    b.scale[j] = pl->scal + SC_SCALE;
+    b.scale_f[j] = pl->scalf;
+    b.tw[j] = tw_of<A>(pl);
+    b.part[j] = pl->partA;
+    if (pl->pending) scaled[g] |= 1u << j;
+  }
+  int nb = 0;
+  for (int g = 0; g < 3; ++g) {
+    if (nu[g] == 0) continue;
+    qfd_plan_t pl = p0;
+    QFD_RUN(PASS_UPDATE_X, launch_update_x_batch<A>(n, bu[g], nu[g], scaled[g], g, vx, st, &nb));
+  }
+  // every plan's bookkeeping first, so that psi, W and the step counter
+  // agree for all of them even if a later cadence fails
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    pl->nA = nb;
+    pl->w_stage = ST_X;
+    pl->pending = false;
+    pl->t[ss[i]] += 1;
+  }
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    const int s = ss[i];
+    if (pl->t[s] % pl->p.ortho_every == 0) {
+      if ((r = cadence<A>(pl, s, check)) != QFD_OK) return r;
+      if (pl->snap_every > 0 && s == 0 && pl->t[s] % pl->snap_every == 0 && (r = take_snapshot<A>(pl)) != QFD_OK)
+        return r;
+    } else if (check) {
+      if ((r = finalize(pl, pl->partA, 2, pl->nA, OP_N2PV)) != QFD_OK) return r;
+    }
+  }
+  return QFD_OK;
+}
+
+// qfd_step_batch after its checks (every plan's stream pointed at plans[0]'s).
+template <class A>
+qfd_status step_batch(qfd_plan_s* const* pls, const int* ss, int count, int64_t nsteps) {
+  qfd_status r;
+  for (int64_t it = 0; it < nsteps; ++it)
+    if ((r = batch_step_once<A>(pls, ss, count, 0, pls[0]->st)) != QFD_OK) return r;
   for (int i = 0; i < count; ++i)
     if ((r = materialize<A>(pls[i], ss[i])) != QFD_OK) return r;
+  return QFD_OK;
+}
+
+// period_launch for `count` lattices of one size in arithmetic A at once (FFT
+// kinetic terms): check_every batched steps, the last one with the energy
+// check's partials, then passes B and C with the Parseval partial as batched
+// launches and each plan's energy, whose scalars are copied asynchronously
+// into that plan's pinned host buffer.  Nothing synchronises, so the period
+// can be captured into a CUDA graph.  Every plan's stream must be `st`.
+template <class A>
+qfd_status batch_period_launch(qfd_plan_s* const* pls, const int* ss, int count, cudaStream_t st) {
+  qfd_plan_t p0 = pls[0];
+  const int64_t n = p0->p.n;
+  const int ce = p0->p.check_every;
+  qfd_status r;
+  for (int j = 0; j < ce; ++j)
+    if ((r = batch_step_once<A>(pls, ss, count, j == ce - 1, st)) != QFD_OK) return r;
+  BatchY by{};
+  BatchZ bz{};
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    if (pl->w_stage != ST_X) return fail(pl, QFD_ERR_STATE, "internal: energy needs W after the x pass");
+    by.W[i] = bz.W[i] = pl->W;
+    by.tw[i] = bz.tw[i] = tw_of<A>(pl);
+    bz.ktab[i] = ktab_of<A>(pl);
+    bz.kp[i] = pl->kin;
+    bz.part[i] = pl->partC;
+  }
+  int nc = 0;
+  {
+    qfd_plan_t pl = p0;
+    const int vy = p0->tune_vy[A::id], vz = p0->tune_vz[A::id];
+    QFD_RUN(PASS_FWD_Y, launch_fft_y_batch<A>(n, by, count, -1, vy, st));
+    QFD_RUN(PASS_ZKIN, launch_zpass_batch<A>(n, bz, count, 1, vz, st, &nc));
+  }
+  for (int i = 0; i < count; ++i) {
+    qfd_plan_t pl = pls[i];
+    pl->nC = nc;
+    pl->w_stage = ST_C;
+    if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
+    QFD_CK(cudaMemcpyAsync(pl->hscal, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
   return QFD_OK;
 }
 
@@ -1258,6 +1369,10 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
     for (pl->lg = 0; ((int64_t)1 << pl->lg) < n; ++pl->lg) {
     }
   pl->fdtd_c = 1.0 / (2.0 * p.mass * p.a * p.a);
+  pl->up.f_dtau = (float)p.dtau;
+  pl->up.f_hdt = (float)(0.5 * p.dtau);
+  pl->up.d_dtau = host_split(p.dtau);
+  pl->up.d_hdt = host_split(0.5 * p.dtau);
   pl->t.assign(p.nstates, 0);
   pl->parity.assign(p.nstates, 0);
   pl->steps16.assign(p.nstates, 0);
@@ -1265,7 +1380,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   pl->ebulk.assign(p.nstates, NAN);
   pl->edecay.assign(p.nstates, NAN);
   pl->hist.assign(p.nstates, {});
-  pl->arith16 = (p.precision == QFD_DF64 || p.precision == QFD_C64_REFINE_DF) ? 2 : 0;
+  pl->arith16 = arith16_of(p.precision);
   pl->phase = uses32(p.precision) ? 1 : pl->arith16;
 
   auto cleanup_fail = [&](qfd_status s, const std::string& msg) {
@@ -1302,16 +1417,12 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       {(void**)&pl->scal, SC_COUNT * sizeof(double)},
       {(void**)&pl->scalf, 16 * sizeof(float)},
       {(void**)&pl->flag, sizeof(int)},
-      {(void**)&pl->errflag, sizeof(int)},
   };
-  if (uses16(p.precision)) {
-    allocs.push_back({(void**)&pl->psi16, (size_t)(p.nstates + 1) * n3 * 16});
-    allocs.push_back({(void**)&pl->coef16, (size_t)n3 * 16});
-  }
-  if (uses32(p.precision)) {
-    allocs.push_back({(void**)&pl->psi32, (size_t)(p.nstates + 1) * n3 * sizeof(float2)});
-    allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
-  }
+  if (uses16(p.precision)) allocs.push_back({(void**)&pl->psi16, (size_t)(p.nstates + 1) * n3 * 16});
+  if (uses32(p.precision)) allocs.push_back({(void**)&pl->psi32, (size_t)(p.nstates + 1) * n3 * sizeof(float2)});
+  if (needs_coef16(p)) allocs.push_back({(void**)&pl->coef16, (size_t)n3 * 16});
+  if (needs_coef32(p)) allocs.push_back({(void**)&pl->coef32, (size_t)n3 * sizeof(float2)});
+  if (needs_v32(p)) allocs.push_back({(void**)&pl->V32, (size_t)n3 * sizeof(float)});
   if (uses_vdf(p.precision)) allocs.push_back({(void**)&pl->Vdf, (size_t)n3 * sizeof(df)});
   for (auto& a : allocs) {
     if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
@@ -1347,10 +1458,9 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
             cudaMemcpy(pl->ktab64, ktab.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktab32, kt32.data(), n * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktabdf, ktdf.data(), n * sizeof(df), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess &&
-            cudaMemset(pl->errflag, 0, sizeof(int)) == cudaSuccess;
+            cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess;
   if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
-  if (cudaHostAlloc((void**)&pl->hscal, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+  if (cudaHostAlloc((void**)&pl->hscal, SC_COUNT * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
     return cleanup_fail(QFD_ERR_OOM, "pinned host buffer allocation failed");
   *out = pl;
   return QFD_OK;
@@ -1361,7 +1471,7 @@ void qfd_destroy(qfd_plan_t pl) {
   if (pl->st) cudaStreamSynchronize(pl->st);
   void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
                   pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
-                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->errflag, pl->Vdf};
+                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->Vdf, pl->V32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (pl->hscal) cudaFreeHost(pl->hscal);
@@ -1543,7 +1653,7 @@ qfd_status qfd_step(qfd_plan_t pl, int s, int64_t nsteps) {
       if (q != QFD_OK) return q;
     }
     qfd_status q = materialize<A>(pl, s);
-    return q != QFD_OK ? q : check_kernel_errors(pl);
+    return q != QFD_OK ? q : sync_checked(pl);
   });
 }
 
@@ -1563,7 +1673,6 @@ qfd_status qfd_step_batch(const qfd_plan_t* plans, const int* states, int count,
     if (pl->p.n != p0->p.n || pl->phase != p0->phase)
       return fail(p0, QFD_ERR_ARG, "the plans of a batch share n and the current arithmetic");
     if (pl->p.kinetic == 0) return fail(p0, QFD_ERR_ARG, "batched steps take the FFT kinetic terms (kinetic 1..3)");
-    if (pl->p.n > MAX_BATCH_N) return fail(p0, QFD_ERR_ARG, "batched steps take lattices of n <= 256");
     if (!pl->has_pot) return fail(p0, QFD_ERR_STATE, "set a potential before stepping");
   }
   if (nsteps < 0) return fail(p0, QFD_ERR_ARG, "nsteps < 0");
@@ -1592,7 +1701,7 @@ qfd_status qfd_step_batch(const qfd_plan_t* plans, const int* states, int count,
   cudaEventDestroy(ev);
   if (r != QFD_OK) return r;
   for (int i = 0; i < count; ++i)
-    if ((r = check_kernel_errors(plans[i])) != QFD_OK) return r;
+    if ((r = sync_checked(plans[i])) != QFD_OK) return r;
   return QFD_OK;
 }
 
@@ -1673,25 +1782,27 @@ qfd_status qfd_snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap
 
 qfd_status qfd_autotune(qfd_plan_t pl, double* ms_out) {
   if (!pl) return QFD_ERR_ARG;
-  double ms[12];
+  double ms[24];
   for (double& m : ms) m = NAN;
   QFD_CK(cudaStreamSynchronize(pl->st));
   qfd_status r = QFD_OK;
-  if (uses32(pl->p.precision) && (r = autotune_policy<F32>(pl, ms + 4)) != QFD_OK) return r;
+  if (uses32(pl->p.precision) && (r = autotune_policy<F32>(pl, ms + 8)) != QFD_OK) return r;
   if (pl->psi16 && pl->arith16 == 0 && (r = autotune_policy<F64>(pl, ms + 0)) != QFD_OK) return r;
-  if (pl->psi16 && pl->arith16 == 2 && (r = autotune_policy<DF>(pl, ms + 8)) != QFD_OK) return r;
+  if (pl->psi16 && pl->arith16 == 2 && (r = autotune_policy<DF>(pl, ms + 16)) != QFD_OK) return r;
   pl->w_stage = ST_NONE;  // W was used as the timing lattice
   pl->w_state = -1;
   if (ms_out) std::memcpy(ms_out, ms, sizeof(ms));
   return QFD_OK;
 }
 
-qfd_status qfd_set_tuning(qfd_plan_t pl, int policy, int y_variant, int z_variant) {
+qfd_status qfd_set_tuning(qfd_plan_t pl, int policy, int y_variant, int z_variant, int x_variant) {
   if (!pl) return QFD_ERR_ARG;
-  if (policy < 0 || policy > 2 || y_variant < 0 || y_variant > 1 || z_variant < -1 || z_variant > 1)
-    return fail(pl, QFD_ERR_ARG, "policy 0..2, y_variant 0..1, z_variant -1..1");
+  if (policy < 0 || policy > 2 || y_variant < 0 || y_variant > 2 || z_variant < -1 || z_variant > 2 ||
+      x_variant < 0 || x_variant > 1)
+    return fail(pl, QFD_ERR_ARG, "policy 0..2, y_variant 0..2, z_variant -1..2, x_variant 0..1");
   pl->tune_vy[policy] = y_variant;
   pl->tune_vz[policy] = z_variant;
+  pl->tune_vx[policy] = x_variant;
   return QFD_OK;
 }
 
@@ -1778,7 +1889,7 @@ qfd_status qfd_sync(qfd_plan_t pl) {
 
 // ================================================================ server
 static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 168 && sizeof(qfd_result) == 232 &&
-                  sizeof(qfd_server_params) == 32,
+                  sizeof(qfd_server_params) == 40,
               "C ABI struct layouts are fixed (the Python binding mirrors them)");
 // Continuous batching of solve requests: requests wait in FIFO order and are
 // admitted while their device bytes fit the budget.  Every admitted request
@@ -1790,13 +1901,25 @@ static_assert(sizeof(qfd_params) == 96 && sizeof(qfd_request) == 168 && sizeof(q
 // of each ended request, moving it to its next phase, state or completion.
 // From its second period in a phase on, a request's period is captured once as
 // a CUDA graph on its stream and replayed.
+//
+// Cohort mode (qfd_server_params.cohorts = 1): requests of one lattice size
+// share a stream and advance together, up to QFD_MAX_BATCH of them.  A cohort
+// period is one period of every member: each pass of each step is one launch
+// over the members of one arithmetic (the batched kernels, which are also the
+// single-lattice kernels), the cadence and the stop rule stay per request.
+// Once no member is in the first period of a phase, the cohort period is
+// captured as a CUDA graph and replayed while the members and their states
+// and phases stay the same.
+struct Cohort;
 struct ReqRun {
   int64_t id = 0;
   qfd_request req{};
   qfd_plan_t plan = nullptr;
-  cudaStream_t st = nullptr;        // the request's stream (owned by the server)
+  Cohort* cohort = nullptr;         // cohort mode: the cohort the request belongs to
+  cudaStream_t st = nullptr;        // the request's stream (owned by the server, or its cohort's)
   cudaEvent_t ev = nullptr;         // end of the period in flight
   cudaGraphExec_t exec = nullptr;   // captured period of (gstate, gphase)
+  int64_t exec_kernels = 0;         // kernel launches the captured period holds
   int gstate = -1, gphase = -1;
   size_t bytes = 0;
   int state = 0;
@@ -1804,8 +1927,22 @@ struct ReqRun {
   bool bulk = false;      // complex64 bulk of a mixed request
   bool fresh = true;      // its first period in this phase is still to run
   bool inflight = false;  // a period is queued on st
+  std::chrono::steady_clock::time_point t_issue;  // when the period in flight was queued
   PhaseTracker tr;
   qfd_result res{};
+};
+
+struct Cohort {
+  int64_t n = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<ReqRun*> members;  // admitted to the cohort
+  std::vector<ReqRun*> running;  // the members of the period in flight
+  bool inflight = false;
+  std::chrono::steady_clock::time_point t_issue;
+  cudaGraphExec_t exec = nullptr;  // the captured cohort period
+  int64_t exec_kernels = 0;        // kernel launches it holds
+  std::vector<int64_t> sig;        // (member id, state, phase) of each member it was captured for
 };
 
 struct qfd_server_s {
@@ -1815,12 +1952,15 @@ struct qfd_server_s {
   std::string err;
   std::deque<ReqRun*> waiting;
   std::vector<ReqRun*> active;
+  std::vector<Cohort*> cohorts;  // cohort mode
   std::vector<qfd_result> done;
   size_t used = 0;
   int64_t next_id = 1;
   cudaEvent_t fork = nullptr;  // admitted requests start after the server stream's work
   int prio_least = 0, prio_greatest = 0;
+  double timeout_s = 0.0;  // watchdog on a period in flight (0: none)
   int64_t periods = 0, replays = 0, captures = 0;
+  int64_t kernels = 0;  // kernel launches queued, direct or in replayed graphs
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
@@ -1869,8 +2009,37 @@ void release_request(ReqRun* m) {
   if (m->plan) qfd_destroy(m->plan);
   if (m->exec) cudaGraphExecDestroy(m->exec);
   if (m->ev) cudaEventDestroy(m->ev);
-  if (m->st) cudaStreamDestroy(m->st);
+  if (m->cohort) {
+    auto& mem = m->cohort->members;
+    mem.erase(std::remove(mem.begin(), mem.end(), m), mem.end());
+  } else if (m->st) {
+    cudaStreamDestroy(m->st);
+  }
   delete m;
+}
+
+void destroy_cohort(Cohort* c) {
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->ev) cudaEventDestroy(c->ev);
+  if (c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+// The cohort a newly admitted request of size n joins: one of that size with
+// room, else a new one (its stream's priority as for a request of size n).
+Cohort* cohort_for(qfd_server_t sv, int64_t n) {
+  for (Cohort* c : sv->cohorts)
+    if (c->n == n && (int)c->members.size() < QFD_MAX_BATCH) return c;
+  Cohort* c = new Cohort();
+  c->n = n;
+  if (cudaStreamCreateWithPriority(&c->st, cudaStreamNonBlocking, request_priority(sv, n)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+    destroy_cohort(c);
+    return nullptr;
+  }
+  sv->cohorts.push_back(c);
+  return c;
 }
 
 // Starts state `s` of a request: the complex64 bulk for mixed requests, else
@@ -1917,9 +2086,17 @@ qfd_status admit(qfd_server_t sv) {
       delete m;
       continue;
     }
-    if (cudaStreamCreateWithPriority(&m->st, cudaStreamNonBlocking, request_priority(sv, m->req.n)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamWaitEvent(m->st, sv->fork, 0) != cudaSuccess) {
+    bool ok;
+    if (sv->p.cohorts) {
+      m->cohort = cohort_for(sv, m->req.n);
+      ok = m->cohort && (m->st = m->cohort->st) != nullptr && cudaStreamWaitEvent(m->st, sv->fork, 0) == cudaSuccess;
+      if (ok) m->cohort->members.push_back(m);
+    } else {
+      ok = cudaStreamCreateWithPriority(&m->st, cudaStreamNonBlocking, request_priority(sv, m->req.n)) == cudaSuccess &&
+           cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) == cudaSuccess &&
+           cudaStreamWaitEvent(m->st, sv->fork, 0) == cudaSuccess;
+    }
+    if (!ok) {
       sv->waiting.pop_front();
       finish_request(sv, m, QFD_ERR_CUDA);
       release_request(m);
@@ -1928,8 +2105,14 @@ qfd_status admit(qfd_server_t sv) {
     prm.stream = (void*)m->st;
     qfd_status r = qfd_plan(&prm, &m->plan);
     if (r == QFD_ERR_OOM && !sv->active.empty()) {  // retry once memory frees up
-      cudaStreamDestroy(m->st);
-      cudaEventDestroy(m->ev);
+      if (m->cohort) {
+        auto& mem = m->cohort->members;
+        mem.erase(std::remove(mem.begin(), mem.end(), m), mem.end());
+        m->cohort = nullptr;
+      } else {
+        cudaStreamDestroy(m->st);
+        cudaEventDestroy(m->ev);
+      }
       m->st = nullptr;
       m->ev = nullptr;
       break;
@@ -2000,6 +2183,7 @@ qfd_status advance_request(ReqRun* m, bool* finished) {
 // state changes between periods of a phase).
 qfd_status issue_period(qfd_server_t sv, ReqRun* m) {
   qfd_plan_t pl = m->plan;
+  const int64_t l0 = pl->launches;
   auto launch = [&]() -> qfd_status {
     qfd_status r = with_policy(m->phase, [&](auto pol) -> qfd_status {
       return period_launch<decltype(pol)>(pl, m->state, pl->hscal);
@@ -2009,9 +2193,11 @@ qfd_status issue_period(qfd_server_t sv, ReqRun* m) {
   qfd_status r = QFD_OK;
   if (!sv->p.use_graphs || m->fresh) {
     r = launch();
+    sv->kernels += pl->launches - l0;
   } else if (m->exec && m->gstate == m->state && m->gphase == m->phase) {
     if (cudaGraphLaunch(m->exec, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
     pl->t[m->state] += pl->p.check_every;
+    sv->kernels += m->exec_kernels;
     ++sv->replays;
   } else {
     if (m->exec) {
@@ -2036,19 +2222,186 @@ qfd_status issue_period(qfd_server_t sv, ReqRun* m) {
     }
     m->gstate = m->state;
     m->gphase = m->phase;
+    m->exec_kernels = pl->launches - l0;
+    sv->kernels += m->exec_kernels;
     if (cudaGraphLaunch(m->exec, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
     ++sv->captures;
   }
   if (r != QFD_OK) return r;
   if (cudaEventRecord(m->ev, m->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "event record");
+  m->t_issue = std::chrono::steady_clock::now();
   m->inflight = true;
   ++sv->periods;
   return QFD_OK;
 }
 
+// The kernel sequence of one cohort period: per arithmetic, the members with
+// an FFT kinetic term take batch_period_launch together (each pass one launch
+// over them); H_K(0) members run period_launch one after the other.  All of it
+// is on the cohort's stream, which is every member plan's stream.
+qfd_status launch_cohort_period(qfd_server_t sv, Cohort* c) {
+  for (int ph = 0; ph < 3; ++ph) {
+    std::vector<qfd_plan_s*> pls;
+    std::vector<int> ss;
+    for (ReqRun* m : c->running) {
+      if (m->phase != ph) continue;
+      qfd_plan_t pl = m->plan;
+      if (pl->p.kinetic == 0) {
+        const qfd_status r = with_policy(ph, [&](auto pol) -> qfd_status {
+          return period_launch<decltype(pol)>(pl, m->state, pl->hscal);
+        });
+        if (r != QFD_OK) return sfail(sv, r, pl->err);
+      } else {
+        pls.push_back(pl);
+        ss.push_back(m->state);
+      }
+    }
+    if (pls.empty()) continue;
+    const qfd_status r = with_policy(ph, [&](auto pol) -> qfd_status {
+      return batch_period_launch<decltype(pol)>(pls.data(), ss.data(), (int)pls.size(), c->st);
+    });
+    if (r != QFD_OK) return sfail(sv, r, pls[0]->err);
+  }
+  return QFD_OK;
+}
+
+// Queues one period of every member of cohort c: directly while a member is
+// in the first period of its phase (or without graphs), else by replaying -
+// after capturing once - the graph of the cohort period, which stays valid
+// while the members and their states and phases are the same (the host state
+// of each member then advances by its step counter only, as for a request's
+// own graph).
+qfd_status issue_cohort_period(qfd_server_t sv, Cohort* c) {
+  c->running = c->members;
+  auto launched = [&]() {
+    int64_t k = 0;
+    for (ReqRun* m : c->running) k += m->plan->launches;
+    return k;
+  };
+  const int64_t l0 = launched();
+  bool any_fresh = false;
+  std::vector<int64_t> sig;
+  for (ReqRun* m : c->running) {
+    any_fresh = any_fresh || m->fresh;
+    sig.push_back(m->id);
+    sig.push_back(m->state);
+    sig.push_back(m->phase);
+  }
+  qfd_status r = QFD_OK;
+  if (!sv->p.use_graphs || any_fresh) {
+    r = launch_cohort_period(sv, c);
+    sv->kernels += launched() - l0;
+  } else if (c->exec && c->sig == sig) {
+    if (cudaGraphLaunch(c->exec, c->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    for (ReqRun* m : c->running) m->plan->t[m->state] += m->plan->p.check_every;
+    sv->kernels += c->exec_kernels;
+    ++sv->replays;
+  } else {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return sfail(sv, QFD_ERR_CUDA, "begin capture");
+    r = launch_cohort_period(sv, c);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->st, &g);
+    if (r != QFD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ce != cudaSuccess || !g) return sfail(sv, QFD_ERR_CUDA, "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      c->exec = nullptr;
+      return sfail(sv, QFD_ERR_CUDA, "graph instantiate");
+    }
+    c->sig = sig;
+    c->exec_kernels = launched() - l0;
+    sv->kernels += c->exec_kernels;
+    if (cudaGraphLaunch(c->exec, c->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "graph launch");
+    ++sv->captures;
+  }
+  if (r != QFD_OK) return r;
+  if (cudaEventRecord(c->ev, c->st) != cudaSuccess) return sfail(sv, QFD_ERR_CUDA, "event record");
+  c->t_issue = std::chrono::steady_clock::now();
+  c->inflight = true;
+  sv->periods += (int64_t)c->running.size();
+  return QFD_OK;
+}
+
+// Ends request m (finished, failed or timed out): result, budget, memory.
+void retire_request(qfd_server_t sv, ReqRun* m, qfd_status status) {
+  finish_request(sv, m, status);
+  sv->used -= m->bytes;
+  sv->active.erase(std::remove(sv->active.begin(), sv->active.end(), m), sv->active.end());
+  release_request(m);
+}
+
+// run_periods in cohort mode: a period for every cohort without one in
+// flight, a wait (bounded by the watchdog) until one has ended, then the stop
+// rule and the next phase, state or completion of each of its members.
+qfd_status run_cohort_periods(qfd_server_t sv) {
+  std::vector<std::pair<Cohort*, qfd_status>> ended;  // QFD_OK: the period completed
+  for (Cohort* c : sv->cohorts) {
+    if (c->inflight || c->members.empty()) continue;
+    const qfd_status r = issue_cohort_period(sv, c);
+    if (r != QFD_OK) ended.push_back({c, r});
+  }
+  while (ended.empty()) {
+    bool waiting_any = false;
+    const auto now = std::chrono::steady_clock::now();
+    for (Cohort* c : sv->cohorts) {
+      if (!c->inflight) continue;
+      waiting_any = true;
+      const cudaError_t q = cudaEventQuery(c->ev);
+      if (q == cudaSuccess) {
+        c->inflight = false;
+        ended.push_back({c, QFD_OK});
+      } else if (q != cudaErrorNotReady) {
+        return sfail(sv, QFD_ERR_CUDA, cudaGetErrorString(q));
+      } else if (sv->timeout_s > 0 && std::chrono::duration<double>(now - c->t_issue).count() > sv->timeout_s) {
+        c->inflight = false;
+        ended.push_back({c, QFD_ERR_TIMEOUT});
+      }
+    }
+    if (!waiting_any || !ended.empty()) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  for (auto& e : ended) {
+    Cohort* c = e.first;
+    const std::vector<ReqRun*> running = c->running;
+    c->running.clear();
+    for (ReqRun* m : running) {
+      if (e.second != QFD_OK) {
+        m->res.status = e.second;
+        retire_request(sv, m, e.second);
+        continue;
+      }
+      bool finished = false;
+      const qfd_status q = advance_request(m, &finished);
+      if (q != QFD_OK || finished) retire_request(sv, m, q);
+    }
+  }
+  // cohorts left without members and work in flight are released
+  std::vector<Cohort*> keep;
+  for (Cohort* c : sv->cohorts) {
+    if (c->members.empty() && !c->inflight) destroy_cohort(c);
+    else keep.push_back(c);
+  }
+  sv->cohorts.swap(keep);
+  return QFD_OK;
+}
+
 // Issues a period for every active request without one in flight, waits until
 // at least one period has ended, and retires the requests whose periods ended.
+// With a watchdog set, the wait is bounded: a period still in flight that long
+// after it was queued ends its request with QFD_ERR_TIMEOUT (release_request
+// then waits for the work already queued on the request's stream before its
+// memory is freed).
 qfd_status run_periods(qfd_server_t sv) {
+  if (sv->p.cohorts) return run_cohort_periods(sv);
   std::vector<ReqRun*> keep;
   std::vector<char> ended(sv->active.size(), 0);
   bool any_ended = false;
@@ -2064,6 +2417,7 @@ qfd_status run_periods(qfd_server_t sv) {
   }
   while (!any_ended) {
     bool waiting_any = false;
+    const auto now = std::chrono::steady_clock::now();
     for (size_t i = 0; i < sv->active.size(); ++i) {
       ReqRun* m = sv->active[i];
       if (!m->inflight) continue;
@@ -2075,6 +2429,12 @@ qfd_status run_periods(qfd_server_t sv) {
         any_ended = true;
       } else if (q != cudaErrorNotReady) {
         return sfail(sv, QFD_ERR_CUDA, cudaGetErrorString(q));
+      } else if (sv->timeout_s > 0 &&
+                 std::chrono::duration<double>(now - m->t_issue).count() > sv->timeout_s) {
+        m->inflight = false;
+        m->res.status = QFD_ERR_TIMEOUT;
+        ended[i] = 2;
+        any_ended = true;
       }
     }
     if (!waiting_any || any_ended) break;
@@ -2109,7 +2469,8 @@ size_t qfd_plan_bytes(const qfd_params* p) { return p ? plan_device_bytes(*p) : 
 qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out) {
   if (out) *out = nullptr;
   if (!params || !out || !(params->hbm_budget_bytes > 0) || params->ortho_every < 1 || params->check_every < 1 ||
-      params->check_every % params->ortho_every != 0 || params->max_active < 0)
+      params->check_every % params->ortho_every != 0 || params->max_active < 0 ||
+      (params->cohorts != 0 && params->cohorts != 1))
     return QFD_ERR_ARG;
   qfd_server_t sv = new qfd_server_s();
   sv->p = *params;
@@ -2135,6 +2496,7 @@ void qfd_server_destroy(qfd_server_t sv) {
   if (sv->st) cudaStreamSynchronize(sv->st);
   for (ReqRun* m : sv->active) release_request(m);
   for (ReqRun* m : sv->waiting) delete m;
+  for (Cohort* c : sv->cohorts) destroy_cohort(c);
   if (sv->fork) cudaEventDestroy(sv->fork);
   if (sv->own_stream && sv->st) cudaStreamDestroy(sv->st);
   delete sv;
@@ -2174,6 +2536,19 @@ qfd_status qfd_server_poll(qfd_server_t sv, qfd_result* out, int capacity, int* 
   sv->done.erase(sv->done.begin(), sv->done.begin() + n);
   if (count) *count = n;
   return r;
+}
+
+qfd_status qfd_server_kernels(qfd_server_t sv, int64_t* kernels) {
+  if (!sv || !kernels) return QFD_ERR_ARG;
+  *kernels = sv->kernels;
+  return QFD_OK;
+}
+
+qfd_status qfd_server_set_timeout(qfd_server_t sv, double seconds) {
+  if (!sv) return QFD_ERR_ARG;
+  if (!(seconds >= 0.0) || !std::isfinite(seconds)) return sfail(sv, QFD_ERR_ARG, "timeout must be finite and >= 0");
+  sv->timeout_s = seconds;
+  return QFD_OK;
 }
 
 qfd_status qfd_server_stats(qfd_server_t sv, int* waiting, int* active, double* used_bytes, int64_t* periods,

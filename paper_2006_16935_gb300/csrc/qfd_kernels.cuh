@@ -161,9 +161,17 @@ struct KinParams {
   df d_pref, d_am2, d_ia, d_m0;         // the same as double-float pairs
 };
 
+// Time-step parameters of the update in the representations that derive the
+// coefficients of Sec. 2.2 from V inside pass A (FP32 and double-float).
+struct UpdParams {
+  float f_dtau, f_hdt;  // dtau and dtau / 2 in FP32
+  df d_dtau, d_hdt;     // the same as double-float pairs
+};
+
 struct F64 {
   using C = double2;  // lattice element
   using K = double2;  // update coefficients {A, B dtau}
+  using U = double2;  // what pass A reads per site: the precomputed {A, B dtau}
   using T = double;   // per-axis kinetic table entry
   using S = double;   // scalar
   using VT = double;  // potential as read by the energy partials
@@ -177,6 +185,9 @@ struct F64 {
   // the normalisation factor as written by the reduction kernel: FP64 value,
   // then its FP32 rounding and double-float split in a float array
   static __device__ __forceinline__ S load_scale(const double* d, const float*) { return *d; }
+  // complex128 passes are bound by FP64 issue, so the coefficients are read
+  // precomputed (16 B) rather than derived per site with an FP64 division
+  static __device__ __forceinline__ K coef_from(U u, const UpdParams&) { return u; }
   // Eq. (iter_proced) as printed: A psi - (B dtau) H_K psi
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     return C{cf.x * ps.x - cf.y * hk.x, cf.x * ps.y - cf.y * hk.y};
@@ -219,6 +230,7 @@ struct F64 {
 struct F32 {
   using C = float2;
   using K = float2;  // {B dtau, 1 - A}
+  using U = float;   // pass A reads V in FP32 and derives K
   using T = float;
   using S = float;
   using VT = df;     // the double-float copy of V
@@ -230,6 +242,12 @@ struct F32 {
   }
   static __device__ __forceinline__ S scalar(double s) { return (float)s; }
   static __device__ __forceinline__ S load_scale(const double*, const float* f) { return f[0]; }
+  // Sec. 2.2 with h = dtau V / 2: B dtau = dtau / (1 + h) and 1 - A = 2h / (1 + h)
+  // = V (B dtau).  Nothing cancels, so both keep FP32 relative precision.
+  static __device__ __forceinline__ K coef_from(U v, const UpdParams& up) {
+    const float g1 = up.f_dtau * __frcp_rn(1.0f + v * up.f_hdt);
+    return K{g1, v * g1};
+  }
   // psi - ((1 - A) psi + (B dtau) H_K psi): the O(dtau) increment keeps FP32 relative precision
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     return C{ps.x - (cf.y * ps.x + cf.x * hk.x), ps.y - (cf.y * ps.y + cf.x * hk.y)};
@@ -279,6 +297,7 @@ struct F32 {
 struct DF {
   using C = dfc;
   using K = dfc;  // {B dtau, 1 - A} as double-float pairs
+  using U = df;   // pass A reads V as a double-float pair and derives K
   using T = df;
   using S = df;
   using VT = df;  // the double-float copy of V
@@ -293,6 +312,19 @@ struct DF {
   }
   static __device__ __forceinline__ S scalar(double s) { return dsplit(s); }
   static __device__ __forceinline__ S load_scale(const double*, const float* f) { return df{f[1], f[2]}; }
+  // B dtau = dtau r and 1 - A = V (B dtau) with r = 1 / (1 + h), h = dtau V / 2:
+  // r from the FP32 reciprocal r0 and one Newton step r0 + r0 (1 - d r0), the
+  // residual 1 - d r0 formed from the exact product of the high parts (its
+  // leading difference is exact), so r carries about 2^-46 relative error.
+  static __device__ __forceinline__ K coef_from(U v, const UpdParams& up) {
+    const df d = dadd(df{1.0f, 0.0f}, dmul(v, up.d_hdt));
+    const float r0 = __frcp_rn(d.h);
+    const df p = two_prod(d.h, r0);
+    const float e = __fmaf_rn(-d.l, r0, __fsub_rn(__fsub_rn(1.0f, p.h), p.l));
+    const df r = fast_two_sum(r0, __fmul_rn(r0, e));
+    const df g1 = dmul(up.d_dtau, r);
+    return K{g1, dmul(v, g1)};
+  }
   static __device__ __forceinline__ C update(C ps, C hk, K cf) {
     const df dx = dmul_add(cf.y, ps.x, cf.x, hk.x), dy = dmul_add(cf.y, ps.y, cf.x, hk.y);
     return dfc{dsub(ps.x, dx), dsub(ps.y, dy)};
@@ -350,18 +382,27 @@ struct DF {
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
 // E elements per thread and the radix schedule of a length-N transform.
-// N = 2^p: E = 8; floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
-// N = 12 * 2^p (96, 192): E = 12; one radix-12 stage, then floor(p/2) radix-4
-// stages and a radix-2 stage when p is odd (every radix divides E).
-template <int N> struct FftPlan {
+// Schedule R = 0:
+//   N = 2^p: E = 8; floor(p/3) radix-8 stages, then one radix-2 or radix-4 stage.
+//   N = 12 * 2^p (96, 192): E = 12; one radix-12 stage, then floor(p/2) radix-4
+//   stages and a radix-2 stage when p is odd (every radix divides E).
+// Schedule R = 1 (two stages, one exchange; N = 2^p with p >= 7, else as R = 0):
+//   E = 2^ceil(p/2); a radix-E stage, then radix N/E (16.8 for 128, 16.16 for
+//   256, 32.16 for 512, 32.32 for 1024).  Four times the registers of R = 0
+//   for half the shared-memory exchanges: used by the complex64 y and z passes
+//   when the autotuner finds it faster.
+template <int N, int R = 0> struct FftPlan {
   static constexpr bool R3 = N % 3 == 0;
-  static constexpr int E = R3 ? 12 : 8;
+  static constexpr int P2 = ilog2c(N);
+  static constexpr bool TWO = R == 1 && !R3 && P2 >= 7;
+  static constexpr int E = TWO ? (1 << ((P2 + 1) / 2)) : (R3 ? 12 : 8);
+  static constexpr int T = N / E;  // threads per line
   static constexpr int P = ilog2c(R3 ? N / 12 : N);
   static constexpr int Q = R3 ? P / 2 : P / 3;
   static constexpr int REM = R3 ? P % 2 : P % 3;
-  static constexpr int S = R3 ? 1 + Q + REM : Q + (REM ? 1 : 0);
+  static constexpr int S = TWO ? 2 : (R3 ? 1 + Q + REM : Q + (REM ? 1 : 0));
   __host__ __device__ static constexpr int radix(int i) {
-    return R3 ? (i == 0 ? 12 : (i <= Q ? 4 : 2)) : (i < Q ? 8 : (REM == 1 ? 2 : 4));
+    return TWO ? (i == 0 ? E : N / E) : R3 ? (i == 0 ? 12 : (i <= Q ? 4 : 2)) : (i < Q ? 8 : (REM == 1 ? 2 : 4));
   }
   __host__ __device__ static constexpr int ns(int i) { return i == 0 ? 1 : ns(i - 1) * radix(i - 1); }
 };
@@ -423,6 +464,63 @@ template <int DIR, typename C> __device__ __forceinline__ void dft12(C* x) {
     x[k1 + 9] = d;
   }
 }
+// a * exp(DIR 2 pi i m / M) for M = 16 or 32 (0 <= m < M): quarter turns as
+// exchanges, odd eighth turns through mul_w8, other angles as a product with
+// the constant cos + DIR i sin of m pi (32 / M) / 16.
+template <int M, int DIR, typename C> __device__ __forceinline__ C mul_wm(C a, int m) {
+  // cos(j pi / 16), j = 0..8
+  constexpr double CS[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                            0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                            0.19509032201612826785, 0.0};
+  const int m32 = m * (32 / M);
+  const int q = m32 / 8, r = m32 % 8;
+  if (r == 0) {
+    if (q == 0) return a;
+    if (q == 1) return mul_i<DIR>(a);
+    if (q == 2) return cscale(a, decltype(a.x)(-1));
+    return cscale(mul_i<DIR>(a), decltype(a.x)(-1));
+  }
+  if (r == 4) {
+    const C b = mul_w8<DIR>(a);
+    if (q == 0) return b;
+    if (q == 1) return mul_i<DIR>(b);
+    if (q == 2) return cscale(b, decltype(a.x)(-1));
+    return cscale(mul_i<DIR>(b), decltype(a.x)(-1));
+  }
+  const double c0 = CS[r], s0 = CS[8 - r];
+  const double c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
+  const double s = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
+  return cmul(a, cconst(c, DIR > 0 ? s : -s, C{}));
+}
+
+template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft_small(C* x);
+
+// DFT of length N1 N2 as N1 x N2 (Cooley-Tukey): with n = N2 n1 + n2 and
+// k = k1 + N1 k2, DFT-N1 over n1 for each n2, the factors
+// exp(DIR 2 pi i n2 k1 / (N1 N2)), DFT-N2 over n2 for each k1; X[k] in
+// natural order.  Used for the radix-16 (4 x 4) and radix-32 (4 x 8) stages.
+template <int N1, int N2, int DIR, typename C> __device__ __forceinline__ void dft_ct(C* x) {
+  C y[N2][N1];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) {
+    C t[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) t[n1] = x[N2 * n1 + n2];
+    dft_small<N1, DIR>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) y[n2][k1] = (n2 && k1) ? mul_wm<N1 * N2, DIR>(t[k1], n2 * k1) : t[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    C t[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) t[n2] = y[n2][k1];
+    dft_small<N2, DIR>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) x[k1 + N1 * k2] = t[k2];
+  }
+}
+
 template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
   C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
@@ -441,18 +539,24 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x) {
   x[7] = csub_l(e3, o3);
 }
 
-// One Stockham stage on the register-resident canonical set v[m] = x[t + m N/8].
-// Butterfly b = t + u N/8 (u < 8/RAD) takes x[b + r N/RAD] = v[u + r (8/RAD)],
+template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft_small(C* x) {
+  if constexpr (RAD == 2) dft2<DIR>(x[0], x[1]);
+  if constexpr (RAD == 4) dft4<DIR>(x[0], x[1], x[2], x[3]);
+  if constexpr (RAD == 8) dft8<DIR>(x);
+}
+
+// One Stockham stage on the register-resident canonical set v[m] = x[t + m N/E].
+// Butterfly b = t + u N/E (u < E/RAD) takes x[b + r N/RAD] = v[u + r (E/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
 // TWC: the twiddles of a stage from one sincospif and products of powers
 // instead of table loads (complex64 only; used where the table loads compete
 // with the shared-memory exchanges for the L1 pipe: the z-pass and the
 // inverse y pass).
-template <class A, int N, int RAD, int NS, int DIR, bool LAST, bool TWC = false>
-__device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N>::E], int t,
+template <class A, int N, int R, int RAD, int NS, int DIR, bool LAST, bool TWC = false>
+__device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N, R>::E], int t,
                                               const typename A::C* __restrict__ tw) {
   using C = typename A::C;
-  constexpr int E = FftPlan<N>::E;
+  constexpr int E = FftPlan<N, R>::E;
   constexpr int NB = E / RAD;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
@@ -481,19 +585,21 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N>::E],
         }
       }
     }
+    if constexpr (RAD == 32) dft_ct<4, 8, DIR>(x);
+    if constexpr (RAD == 16) dft_ct<4, 4, DIR>(x);
     if constexpr (RAD == 12) dft12<DIR>(x);
-    if (RAD == 8) dft8<DIR>(x);
-    if (RAD == 4) dft4<DIR>(x[0], x[1], x[2], x[3]);
-    if (RAD == 2) dft2<DIR>(x[0], x[1]);
+    if constexpr (RAD == 8) dft8<DIR>(x);
+    if constexpr (RAD == 4) dft4<DIR>(x[0], x[1], x[2], x[3]);
+    if constexpr (RAD == 2) dft2<DIR>(x[0], x[1]);
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[u + r * NB] = cnorm(x[r]);
   }
 }
 
 // Writes stage outputs to their Stockham positions, then reads the canonical set.
-template <typename C, int N, int RAD, int NS, class Acc>
-__device__ __forceinline__ void stage_exchange(C (&v)[FftPlan<N>::E], int t, Acc& acc) {
-  constexpr int E = FftPlan<N>::E;
+template <typename C, int N, int R, int RAD, int NS, class Acc>
+__device__ __forceinline__ void stage_exchange(C (&v)[FftPlan<N, R>::E], int t, Acc& acc) {
+  constexpr int E = FftPlan<N, R>::E;
   constexpr int NB = E / RAD;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
@@ -508,23 +614,25 @@ __device__ __forceinline__ void stage_exchange(C (&v)[FftPlan<N>::E], int t, Acc
   acc.sync();
 }
 
-template <class A, int N, int DIR, int I, bool TWC, class Acc>
-__device__ __forceinline__ void fft_stages(typename A::C (&v)[FftPlan<N>::E], int t, const typename A::C* __restrict__ tw,
-                                           Acc& acc) {
-  if constexpr (I < FftPlan<N>::S) {
-    constexpr int RAD = FftPlan<N>::radix(I);
-    constexpr int NS = FftPlan<N>::ns(I);
-    stage_compute<A, N, RAD, NS, DIR, I + 1 == FftPlan<N>::S, TWC>(v, t, tw);
-    if constexpr (I + 1 < FftPlan<N>::S) stage_exchange<typename A::C, N, RAD, NS>(v, t, acc);
-    fft_stages<A, N, DIR, I + 1, TWC>(v, t, tw, acc);
+template <class A, int N, int R, int DIR, int I, bool TWC, class Acc>
+__device__ __forceinline__ void fft_stages(typename A::C (&v)[FftPlan<N, R>::E], int t,
+                                           const typename A::C* __restrict__ tw, Acc& acc) {
+  using PL = FftPlan<N, R>;
+  if constexpr (I < PL::S) {
+    constexpr int RAD = PL::radix(I);
+    constexpr int NS = PL::ns(I);
+    stage_compute<A, N, R, RAD, NS, DIR, I + 1 == PL::S, TWC>(v, t, tw);
+    if constexpr (I + 1 < PL::S) stage_exchange<typename A::C, N, R, RAD, NS>(v, t, acc);
+    fft_stages<A, N, R, DIR, I + 1, TWC>(v, t, tw, acc);
   }
 }
 
-// Unnormalised length-N DFT, sign DIR, canonical layout in and out.
-template <class A, int N, int DIR, class Acc, bool TWC = false>
-__device__ __forceinline__ void fft_line(typename A::C (&v)[FftPlan<N>::E], int t, const typename A::C* __restrict__ tw,
-                                         Acc& acc) {
-  fft_stages<A, N, DIR, 0, TWC>(v, t, tw, acc);
+// Unnormalised length-N DFT, sign DIR, canonical layout in and out, radix
+// schedule R.
+template <class A, int N, int DIR, class Acc, bool TWC = false, int R = 0>
+__device__ __forceinline__ void fft_line(typename A::C (&v)[FftPlan<N, R>::E], int t,
+                                         const typename A::C* __restrict__ tw, Acc& acc) {
+  fft_stages<A, N, R, DIR, 0, TWC>(v, t, tw, acc);
 }
 
 // Shared-memory views. Tile of CW columns of a strided axis: [pos][col] with a
@@ -618,6 +726,16 @@ template <class A, int N> struct Shape {
   static constexpr int YCOLS2 = 2 * YCOLS * T <= 1024 && N % (2 * YCOLS) == 0 ? 2 * YCOLS : YCOLS;
   static_assert(N % YCOLS == 0 && (N * N) % XCOLS == 0, "tiles must divide the lattice");
   static constexpr int ZG2 = (N * N / LINES) % 2 == 0 && N * N / LINES >= 2 ? 2 : 1;
+  // pass A's alternative: tiles of half the width, two CTAs per SM (one CTA's
+  // loads then overlap the other's transforms)
+  static constexpr int XCOLS2 = XCOLS >= 2 ? XCOLS / 2 : XCOLS;
+  // the two-stage radix schedule (complex64 y and z passes, about 150
+  // registers a thread at n = 512, 1024): y tiles and z-pass CTAs of about 128
+  // threads, so that three CTAs fit an SM; one line group
+  static constexpr bool HAS_R1 = A::id == 1 && FftPlan<N, 1>::TWO;
+  static constexpr int T1 = FftPlan<N, 1>::T;
+  static constexpr int YCOLS_R1 = (128 / T1 < N ? 128 / T1 : N) > 1 ? (128 / T1 < N ? 128 / T1 : N) : 1;
+  static constexpr int LINES_R1 = LTARGET / T1 > 1 ? LTARGET / T1 : 1;
   // one padding element per 128 bytes of a line
   static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
   static constexpr int LPAD = N + (N >> PAD_SHIFT);
@@ -757,11 +875,12 @@ __device__ __forceinline__ void pars_store(const typename A::Pars& f, double* __
 enum { STATS_NONE = 0, STATS_NORM = 1, STATS_FULL = 2 };
 
 // ------------------------------------------------------------ lattice batches
-// A batched launch runs one pass of the step over up to MAX_BATCH lattices of
-// one size and arithmetic: blockIdx.y selects the lattice, blockIdx.x the
-// tile exactly as in the single-lattice launch, so each lattice sees the same
-// arithmetic.  The per-lattice pointers travel as __grid_constant__ kernel
-// parameters (each descriptor set stays under 4 KB).
+// Every step kernel runs one pass over a batch of up to MAX_BATCH lattices of
+// one size and arithmetic: blockIdx.y selects the lattice, blockIdx.x the tile,
+// so each lattice sees exactly the arithmetic of a launch over it alone.  A
+// single lattice is a batch of one: the plan's own steps, the lockstep batches
+// and the request server all run the same kernels.  The per-lattice pointers
+// and parameters travel as __grid_constant__ kernel parameters.
 constexpr int MAX_BATCH = 32;
 struct BatchY {  // passes B and D
   void* W[MAX_BATCH];
@@ -771,19 +890,21 @@ struct BatchZ {  // pass C
   void* W[MAX_BATCH];
   const void* tw[MAX_BATCH];
   const void* ktab[MAX_BATCH];
+  double* part[MAX_BATCH];  // Parseval partials (energy checks)
   KinParams kp[MAX_BATCH];
 };
 struct BatchU {  // pass A
   void* W[MAX_BATCH];
   void* psi[MAX_BATCH];
-  const void* coef[MAX_BATCH];
-  const void* V[MAX_BATCH];
+  const void* u[MAX_BATCH];   // per-site update input: {A, B dtau} (F64) or V (F32, DF)
+  const void* V[MAX_BATCH];   // V as the energy partials read it
   const double* scale[MAX_BATCH];
   const float* scale_f[MAX_BATCH];
   const void* tw[MAX_BATCH];
   double* part[MAX_BATCH];
+  UpdParams up[MAX_BATCH];
 };
-static_assert(sizeof(BatchZ) <= 4000 && sizeof(BatchU) <= 4000, "kernel parameter space");
+static_assert(sizeof(BatchZ) <= 4096 && sizeof(BatchU) <= 4096, "kernel parameter space");
 
 // ================================================================ kernels
 
@@ -792,40 +913,41 @@ static_assert(sizeof(BatchZ) <= 4000 && sizeof(BatchU) <= 4000, "kernel paramete
 // base = (id / tiles_inner) * outer_stride + (id % tiles_inner) * COLS.
 // YC (the tile width) is a launch-shape choice of the autotuner; the
 // arithmetic of every column is the same for all widths.
-template <class A, int N, int DIR, int YC>
+template <class A, int N, int DIR, int YC, int R>
 __device__ __forceinline__ void fft_strided_body(typename A::C* W, const typename A::C* __restrict__ tw,
                                                  int64_t stride, int tiles_inner, int64_t outer_stride) {
   using C = typename A::C;
-  using SH = Shape<A, N>;
+  using PL = FftPlan<N, R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int col = threadIdx.x % YC, t = threadIdx.x / YC;
   const int64_t base = (int64_t)(blockIdx.x / tiles_inner) * outer_stride +
                        (int64_t)(blockIdx.x % tiles_inner) * YC + col;
-  C v[SH::E];
+  C v[PL::E];
 #pragma unroll
-  for (int m = 0; m < SH::E; ++m) v[m] = W[base + (int64_t)(t + m * SH::T) * stride];
+  for (int m = 0; m < PL::E; ++m) v[m] = W[base + (int64_t)(t + m * PL::T) * stride];
   AccTile<C, YC, YC> acc{sm, col};
-  // complex64 inverse y pass: computed twiddles (measured faster there; the
-  // forward y pass is faster with the table)
-  fft_line<A, N, DIR, decltype(acc), (DIR > 0)>(v, t, tw, acc);
+  // complex64 inverse y pass and the two-stage schedule: computed twiddles
+  // (measured faster there; the forward y pass of schedule 0 is faster with
+  // the table)
+  fft_line<A, N, DIR, decltype(acc), (DIR > 0 || R == 1), R>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < SH::E; ++m) W[base + (int64_t)(t + m * SH::T) * stride] = v[m];
+  for (int m = 0; m < PL::E; ++m) W[base + (int64_t)(t + m * PL::T) * stride] = v[m];
 }
-template <class A, int N, int DIR, int YC = Shape<A, N>::YCOLS>
-__global__ void __launch_bounds__(N / FftPlan<N>::E * YC)
-k_fft_strided(typename A::C* W, const typename A::C* __restrict__ tw, int64_t stride, int tiles_inner,
-              int64_t outer_stride) {
-  fft_strided_body<A, N, DIR, YC>(W, tw, stride, tiles_inner, outer_stride);
-}
-// The same pass over the lattices of a batch (blockIdx.y = lattice).
-template <class A, int N, int DIR>
-__global__ void __launch_bounds__(N / FftPlan<N>::E * Shape<A, N>::YCOLS)
-k_fft_strided_batch(const __grid_constant__ BatchY b, int64_t stride, int tiles_inner, int64_t outer_stride) {
+// Resident CTAs per SM asked of the compiler for the y passes: complex64
+// keeps about 48 warps per SM (register-light transforms whose exchanges need
+// many warps in flight), the 16-byte arithmetics take what their registers allow.
+template <class A, int N, int YC> struct YOcc {
+  static constexpr int THREADS = N / FftPlan<N>::E * YC;
+  static constexpr int B0 = A::id == 1 ? 1536 / THREADS : 1;
+  static constexpr int value = B0 < 1 ? 1 : (B0 > 8 ? 8 : B0);
+};
+template <class A, int N, int DIR, int YC, int R = 0>
+__global__ void __launch_bounds__(FftPlan<N, R>::T * YC, R == 0 ? YOcc<A, N, YC>::value : 1)
+k_fft_strided(const __grid_constant__ BatchY b, int64_t stride, int tiles_inner, int64_t outer_stride) {
   using C = typename A::C;
-  fft_strided_body<A, N, DIR, Shape<A, N>::YCOLS>(static_cast<C*>(b.W[blockIdx.y]),
-                                                  static_cast<const C*>(b.tw[blockIdx.y]), stride, tiles_inner,
-                                                  outer_stride);
+  fft_strided_body<A, N, DIR, YC, R>(static_cast<C*>(b.W[blockIdx.y]), static_cast<const C*>(b.tw[blockIdx.y]),
+                                     stride, tiles_inner, outer_stride);
 }
 
 // Pass C: forward DFT_z, times T(k)/N^3 (+ Parseval partial when PARSEVAL),
@@ -834,99 +956,100 @@ k_fft_strided_batch(const __grid_constant__ BatchY b, int64_t stride, int tiles_
 // A CTA takes ZG groups of LINES consecutive lines in turn; the loads of the
 // next group are issued before the current group's transforms, so they are in
 // flight while it computes.
-template <class A, int N, bool PARSEVAL, int ZG>
+// R: the radix schedule (FftPlan); LINES lines of T threads per CTA.
+template <class A, int N, bool PARSEVAL, int ZG, int R, int LINES>
 __device__ __forceinline__ void zpass_body(typename A::C* W, const typename A::C* __restrict__ tw,
                                            const typename A::T* __restrict__ ktab, const KinParams& kp,
                                            double* __restrict__ part) {
   using C = typename A::C;
   using T = typename A::T;
   using SH = Shape<A, N>;
+  using PL = FftPlan<N, R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int l = threadIdx.x / SH::T, t = threadIdx.x % SH::T;
-  const int64_t line0 = (int64_t)blockIdx.x * SH::LINES * ZG + l;  // line = kx * N + ky
-  C v[SH::E];
+  const int l = threadIdx.x / PL::T, t = threadIdx.x % PL::T;
+  const int64_t line0 = (int64_t)blockIdx.x * LINES * ZG + l;  // line = kx * N + ky
+  C v[PL::E];
 #pragma unroll
-  for (int m = 0; m < SH::E; ++m) v[m] = W[line0 * N + t + m * SH::T];
-  static_assert(SH::T <= 32 || SH::LINES <= 15, "one named barrier per line");
-  AccLine<C, SH::PAD_SHIFT, SH::T> acc{sm + l * SH::LPAD, l};
+  for (int m = 0; m < PL::E; ++m) v[m] = W[line0 * N + t + m * PL::T];
+  static_assert(PL::T <= 32 || LINES <= 15, "one named barrier per line");
+  AccLine<C, SH::PAD_SHIFT, PL::T> acc{sm + l * SH::LPAD, l};
   typename A::Pars pacc;
 #pragma unroll
   for (int g = 0; g < ZG; ++g) {
-    const int64_t line = line0 + (int64_t)g * SH::LINES;
+    const int64_t line = line0 + (int64_t)g * LINES;
     C* p = W + line * N;
-    C nx[SH::E];
+    C nx[ZG > 1 ? PL::E : 1];
     if (g + 1 < ZG) {
 #pragma unroll
-      for (int m = 0; m < SH::E; ++m) nx[m] = p[(int64_t)SH::LINES * N + t + m * SH::T];
+      for (int m = 0; m < PL::E; ++m) nx[m] = p[(int64_t)LINES * N + t + m * PL::T];
     }
-    fft_line<A, N, -1, decltype(acc), true>(v, t, tw, acc);
+    fft_line<A, N, -1, decltype(acc), true, R>(v, t, tw, acc);
     const T sxy = A::kadd(ktab[line / N], ktab[line % N]);
 #pragma unroll
-    for (int m = 0; m < SH::E; ++m) {
-      const T tk = A::kin(A::kadd(sxy, ktab[t + m * SH::T]), kp);
+    for (int m = 0; m < PL::E; ++m) {
+      const T tk = A::kin(A::kadd(sxy, ktab[t + m * PL::T]), kp);
       if constexpr (PARSEVAL) pacc.add(tk, v[m]);
       v[m] = cscale(v[m], tk);
     }
-    fft_line<A, N, +1, decltype(acc), true>(v, t, tw, acc);
+    fft_line<A, N, +1, decltype(acc), true, R>(v, t, tw, acc);
 #pragma unroll
-    for (int m = 0; m < SH::E; ++m) p[t + m * SH::T] = v[m];
+    for (int m = 0; m < PL::E; ++m) p[t + m * PL::T] = v[m];
     if (g + 1 < ZG) {
 #pragma unroll
-      for (int m = 0; m < SH::E; ++m) v[m] = nx[m];
+      for (int m = 0; m < PL::E; ++m) v[m] = nx[m];
     }
   }
   if constexpr (PARSEVAL) pars_store<A>(pacc, part);
 }
-template <class A, int N, bool PARSEVAL, int ZG = Shape<A, N>::ZG>
-__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS)
-k_zpass(typename A::C* W, const typename A::C* __restrict__ tw, const typename A::T* __restrict__ ktab,
-        const __grid_constant__ KinParams kp, double* __restrict__ part) {
-  zpass_body<A, N, PARSEVAL, ZG>(W, tw, ktab, kp, part);
-}
-// The same pass (without the Parseval partial) over the lattices of a batch.
-template <class A, int N>
-__global__ void __launch_bounds__(Shape<A, N>::LINE_THREADS) k_zpass_batch(const __grid_constant__ BatchZ b) {
+template <class A, int N, int R> struct ZLines {
+  static constexpr int value = R == 0 ? Shape<A, N>::LINES : Shape<A, N>::LINES_R1;
+};
+template <class A, int N, bool PARSEVAL, int ZG, int R = 0>
+__global__ void __launch_bounds__(FftPlan<N, R>::T * ZLines<A, N, R>::value) k_zpass(const __grid_constant__ BatchZ b) {
   using C = typename A::C;
   const int i = blockIdx.y;
-  zpass_body<A, N, false, Shape<A, N>::ZG>(static_cast<C*>(b.W[i]), static_cast<const C*>(b.tw[i]),
-                                           static_cast<const typename A::T*>(b.ktab[i]), b.kp[i], nullptr);
+  zpass_body<A, N, PARSEVAL, ZG, R, ZLines<A, N, R>::value>(static_cast<C*>(b.W[i]), static_cast<const C*>(b.tw[i]),
+                                                             static_cast<const typename A::T*>(b.ktab[i]), b.kp[i],
+                                                             b.part[i]);
 }
 
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
-// Eq. (iter_proced) with the coefficients of Sec. 2.2 (times an optional
-// normalisation factor *scale carried from the previous step); partial sums
-// per STATS; forward DFT_x of the new psi into W.  psi and the coefficients
-// are loaded before the inverse transform so that their latency overlaps it.
-template <class A, int N, int STATS>
+// Eq. (iter_proced) with the coefficients of Sec. 2.2 (read precomputed for
+// complex128, derived from V in the FP32-pipe arithmetics), times an optional
+// normalisation factor *scale carried from the previous step; partial sums per
+// STATS; forward DFT_x of the new psi into W.  psi and the per-site update
+// input are loaded before the inverse transform so that their latency
+// overlaps it.  XC is the tile width (a launch-shape choice of the autotuner).
+template <class A, int N, int STATS, int XC>
 __device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* __restrict__ psi,
-                                              const typename A::K* __restrict__ coef,
+                                              const typename A::U* __restrict__ uin, const UpdParams& upar,
                                               const typename A::VT* __restrict__ V, const double* __restrict__ scale,
                                               const float* __restrict__ scale_f, const typename A::C* __restrict__ tw,
                                               double* __restrict__ part) {
   using C = typename A::C;
-  using K = typename A::K;
+  using U = typename A::U;
   using SH = Shape<A, N>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int col = threadIdx.x % SH::XCOLS, t = threadIdx.x / SH::XCOLS;
-  const int64_t base = (int64_t)blockIdx.x * SH::XCOLS + col;
+  const int col = threadIdx.x % XC, t = threadIdx.x / XC;
+  const int64_t base = (int64_t)blockIdx.x * XC + col;
   constexpr int64_t S = (int64_t)N * N;
-  // psi (and, unless QFD_EARLY_COEF16 is 0 for 16-byte policies, the
-  // coefficients) are loaded before the inverse transform so that their
-  // latency overlaps it
+  // psi (and, unless QFD_EARLY_COEF16 is 0 for 16-byte policies, the update
+  // input) are loaded before the inverse transform so that their latency
+  // overlaps it
   constexpr bool EARLY_K = sizeof(C) == 8 || QFD_EARLY_COEF16;
   C v[SH::E], ps[SH::E];
-  K cf[EARLY_K ? SH::E : 1];
+  U cf[EARLY_K ? SH::E : 1];
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) v[m] = W[base + (t + m * SH::T) * S];
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
   if constexpr (EARLY_K) {
 #pragma unroll
-    for (int m = 0; m < SH::E; ++m) cf[m] = coef[base + (t + m * SH::T) * S];
+    for (int m = 0; m < SH::E; ++m) cf[m] = uin[base + (t + m * SH::T) * S];
   }
-  AccTile<C, SH::XCOLS, SH::XPITCH> acc{sm, col};
+  AccTile<C, XC, XC> acc{sm, col};
   fft_line<A, N, +1>(v, t, tw, acc);
   const bool scaled = scale != nullptr;
   typename A::S s{};
@@ -937,8 +1060,8 @@ __device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* _
   for (int m = 0; m < SH::E; ++m) {
     const int64_t idx = base + (t + m * SH::T) * S;
     C nw;
-    if constexpr (EARLY_K) nw = A::update(ps[m], v[m], cf[m]);
-    else nw = A::update(ps[m], v[m], coef[idx]);
+    if constexpr (EARLY_K) nw = A::update(ps[m], v[m], A::coef_from(cf[m], upar));
+    else nw = A::update(ps[m], v[m], A::coef_from(uin[idx], upar));
     if (scaled) nw = cscale(nw, s);
     psi[idx] = nw;
     v[m] = nw;
@@ -951,24 +1074,18 @@ __device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* _
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
   if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }
-template <class A, int N, int STATS>
-__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
-k_update_x(typename A::C* W, typename A::C* __restrict__ psi, const typename A::K* __restrict__ coef,
-           const typename A::VT* __restrict__ V, const double* __restrict__ scale, const float* __restrict__ scale_f,
-           const typename A::C* __restrict__ tw, double* __restrict__ part) {
-  update_x_body<A, N, STATS>(W, psi, coef, V, scale, scale_f, tw, part);
-}
-// The same pass over the lattices of a batch; lattice i applies its pending
-// normalisation factor when bit i of `scaled` is set.
-template <class A, int N, int STATS>
-__global__ void __launch_bounds__(Shape<A, N>::XTHREADS)
-k_update_x_batch(const __grid_constant__ BatchU b, uint32_t scaled) {
+// Lattice i of the batch applies its pending normalisation factor when bit i
+// of `scaled` is set.  The half-width tiles (XC < XCOLS) are compiled for two
+// resident CTAs per SM.
+template <class A, int N, int STATS, int XC>
+__global__ void __launch_bounds__(N / FftPlan<N>::E * XC, XC < Shape<A, N>::XCOLS ? 2 : 1)
+k_update_x(const __grid_constant__ BatchU b, uint32_t scaled) {
   using C = typename A::C;
   const int i = blockIdx.y;
-  update_x_body<A, N, STATS>(static_cast<C*>(b.W[i]), static_cast<C*>(b.psi[i]),
-                             static_cast<const typename A::K*>(b.coef[i]), static_cast<const typename A::VT*>(b.V[i]),
-                             (scaled >> i) & 1u ? b.scale[i] : nullptr, b.scale_f[i],
-                             static_cast<const C*>(b.tw[i]), b.part[i]);
+  update_x_body<A, N, STATS, XC>(static_cast<C*>(b.W[i]), static_cast<C*>(b.psi[i]),
+                                 static_cast<const typename A::U*>(b.u[i]), b.up[i],
+                                 static_cast<const typename A::VT*>(b.V[i]), (scaled >> i) & 1u ? b.scale[i] : nullptr,
+                                 b.scale_f[i], static_cast<const C*>(b.tw[i]), b.part[i]);
 }
 
 // Forward DFT_x of src (optionally times *scale, optionally also written to

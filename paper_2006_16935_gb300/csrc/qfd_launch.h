@@ -12,6 +12,7 @@
 namespace qfd {
 
 struct KinParams;
+struct UpdParams;
 struct BatchY;
 struct BatchZ;
 struct BatchU;
@@ -39,7 +40,8 @@ struct LaunchArgs {
   void* psi = nullptr;         // state lattice
   const void* src = nullptr;   // forward-x input (may alias W)
   void* psi_out = nullptr;     // forward-x: where to store the scaled input (or null)
-  const void* coef = nullptr;  // update coefficients per site
+  const void* coef = nullptr;  // pass A's per-site update input: {A, B dtau} (F64) or V (F32, DF)
+  const UpdParams* up = nullptr;  // time-step parameters of the V-derived coefficients
   const void* V = nullptr;     // potential as the policy's energy sums read it:
                                // FP64 (F64), double-float pairs (F32, DF)
   const double* scale = nullptr;  // normalisation factor (FP64) or null
@@ -48,7 +50,6 @@ struct LaunchArgs {
   const void* ktab = nullptr;  // per-axis kinetic table
   const KinParams* kin = nullptr;
   double* part = nullptr;      // per-CTA partials
-  int* err = nullptr;          // set to nonzero by a kernel whose bounded wait ran out
   int stats = 0;               // STATS_* for passes A / forward x, Parseval flag for pass C
   cudaStream_t stream = 0;
   // projection / Gram-Schmidt
@@ -59,31 +60,31 @@ struct LaunchArgs {
   const double* sums = nullptr;  // overlaps (2 doubles per lower state)
   void* dst = nullptr;         // projected state output
   // launch shapes (autotuner): y tiles of the default width (0) or twice it
-  // (1); z-pass line groups of the policy default (-1), 1 (0) or 2 (1)
+  // (1); z-pass line groups of the policy default (-1), 1 (0) or 2 (1); pass A
+  // tiles of the default width (0) or half of it with two CTAs per SM (1)
   int vy = 0;
   int vz = -1;
+  int vx = 0;
 };
-
-// Batched passes exist for lattices of N <= MAX_BATCH_N only: a larger
-// lattice fills the GPU on its own, and the instantiations would only
-// lengthen the build.
-constexpr int MAX_BATCH_N = 256;
 
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the
 // number of CTAs (= partials per reduced quantity) when non-null.
 template <class A, int N> struct Launch {
+  // one lattice (a batch of one): the step passes
   static cudaError_t update_x(const LaunchArgs& a, int* nblocks);
-  static cudaError_t forward_x(const LaunchArgs& a, int* nblocks);
   static cudaError_t fft_y(const LaunchArgs& a, int dir);
   static cudaError_t zpass(const LaunchArgs& a, int* nblocks);
+  // one lattice: the cadence and energy passes
+  static cudaError_t forward_x(const LaunchArgs& a, int* nblocks);
   static cudaError_t project_x(const LaunchArgs& a, int* nblocks);
   static cudaError_t gs_dots(const LaunchArgs& a, int nblocks);
   static int partials();  // largest CTA count of a reducing pass
-  // batched passes over `count` lattices (default launch shapes; pass A with
-  // STATS_NONE or STATS_NORM, pass C without the Parseval partial)
-  static cudaError_t fft_y_batch(const BatchY& b, int count, int dir, cudaStream_t st);
-  static cudaError_t zpass_batch(const BatchZ& b, int count, cudaStream_t st);
-  static cudaError_t update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
+  // the step passes over `count` lattices with the launch shapes vy, vz, vx
+  // (as in LaunchArgs); pass A with any STATS mode, pass C with or without
+  // the Parseval partial; *nblocks = CTAs per lattice
+  static cudaError_t fft_y_batch(const BatchY& b, int count, int dir, int vy, cudaStream_t st);
+  static cudaError_t zpass_batch(const BatchZ& b, int count, int parseval, int vz, cudaStream_t st, int* nblocks);
+  static cudaError_t update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, int vx, cudaStream_t st,
                                     int* nblocks);
 };
 
@@ -126,17 +127,20 @@ template <class A> cudaError_t launch_project_x(const LaunchArgs& a, int* nb) {
 template <class A> cudaError_t launch_gs_dots(const LaunchArgs& a, int nblocks) {
   return dispatch_n(a.n, [&](auto t) { return Launch<A, decltype(t)::value>::gs_dots(a, nblocks); });
 }
-template <class A> cudaError_t launch_fft_y_batch(int64_t n, const BatchY& b, int count, int dir, cudaStream_t st) {
-  return dispatch_n(n, [&](auto t) { return Launch<A, decltype(t)::value>::fft_y_batch(b, count, dir, st); });
-}
-template <class A> cudaError_t launch_zpass_batch(int64_t n, const BatchZ& b, int count, cudaStream_t st) {
-  return dispatch_n(n, [&](auto t) { return Launch<A, decltype(t)::value>::zpass_batch(b, count, st); });
+template <class A>
+cudaError_t launch_fft_y_batch(int64_t n, const BatchY& b, int count, int dir, int vy, cudaStream_t st) {
+  return dispatch_n(n, [&](auto t) { return Launch<A, decltype(t)::value>::fft_y_batch(b, count, dir, vy, st); });
 }
 template <class A>
-cudaError_t launch_update_x_batch(int64_t n, const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
-                                  int* nb) {
+cudaError_t launch_zpass_batch(int64_t n, const BatchZ& b, int count, int parseval, int vz, cudaStream_t st, int* nb) {
   return dispatch_n(
-      n, [&](auto t) { return Launch<A, decltype(t)::value>::update_x_batch(b, count, scaled, stats, st, nb); });
+      n, [&](auto t) { return Launch<A, decltype(t)::value>::zpass_batch(b, count, parseval, vz, st, nb); });
+}
+template <class A>
+cudaError_t launch_update_x_batch(int64_t n, const BatchU& b, int count, uint32_t scaled, int stats, int vx,
+                                  cudaStream_t st, int* nb) {
+  return dispatch_n(
+      n, [&](auto t) { return Launch<A, decltype(t)::value>::update_x_batch(b, count, scaled, stats, vx, st, nb); });
 }
 template <class A> int max_partials(int64_t n) {
   int out = 0;

@@ -17,21 +17,17 @@ static void ensure_smem(K kern, size_t bytes) {
 
 template <class A, int N>
 cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
-  using C = typename A::C;
-  using VT = typename A::VT;
-  using SH = Shape<A, N>;
-  const size_t smem = (size_t)N * SH::XPITCH * sizeof(C);
-  const int grid = (int)((int64_t)N * N / SH::XCOLS);
-  auto go = [&](auto kern) {
-    ensure_smem(kern, smem);
-    kern<<<grid, SH::XTHREADS, smem, a.stream>>>((C*)a.W, (C*)a.psi, (const typename A::K*)a.coef, (const VT*)a.V,
-                                                  a.scale, a.scale_f, (const C*)a.tw, a.part);
-  };
-  if (a.stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL>);
-  else if (a.stats == STATS_NORM) go(k_update_x<A, N, STATS_NORM>);
-  else go(k_update_x<A, N, STATS_NONE>);
-  if (nblocks) *nblocks = grid;
-  return cudaGetLastError();
+  BatchU b{};
+  b.W[0] = a.W;
+  b.psi[0] = a.psi;
+  b.u[0] = a.coef;
+  b.V[0] = a.V;
+  b.scale[0] = a.scale;
+  b.scale_f[0] = a.scale_f;
+  b.tw[0] = a.tw;
+  b.part[0] = a.part;
+  if (a.up) b.up[0] = *a.up;
+  return update_x_batch(b, 1, a.scale ? 1u : 0u, a.stats, a.vx, a.stream, nblocks);
 }
 
 template <class A, int N>
@@ -55,50 +51,21 @@ cudaError_t Launch<A, N>::forward_x(const LaunchArgs& a, int* nblocks) {
 
 template <class A, int N>
 cudaError_t Launch<A, N>::fft_y(const LaunchArgs& a, int dir) {
-  using C = typename A::C;
-  using SH = Shape<A, N>;
-  auto go = [&](auto kern, int yc) {
-    const size_t smem = (size_t)N * yc * sizeof(C);
-    const int tiles_inner = N / yc;
-    ensure_smem(kern, smem);
-    kern<<<N * tiles_inner, SH::T * yc, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (int64_t)N, tiles_inner,
-                                                          (int64_t)N * N);
-  };
-  if (a.vy == 1) {
-    if (dir < 0) go(k_fft_strided<A, N, -1, SH::YCOLS2>, SH::YCOLS2);
-    else go(k_fft_strided<A, N, +1, SH::YCOLS2>, SH::YCOLS2);
-  } else {
-    if (dir < 0) go(k_fft_strided<A, N, -1>, SH::YCOLS);
-    else go(k_fft_strided<A, N, +1>, SH::YCOLS);
-  }
-  return cudaGetLastError();
+  BatchY b{};
+  b.W[0] = a.W;
+  b.tw[0] = a.tw;
+  return fft_y_batch(b, 1, dir, a.vy, a.stream);
 }
 
 template <class A, int N>
 cudaError_t Launch<A, N>::zpass(const LaunchArgs& a, int* nblocks) {
-  using C = typename A::C;
-  using SH = Shape<A, N>;
-  const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(C);
-  // z-pass line groups: the policy's default, or the autotuner's 1 / 2
-  const int zg = a.vz == 0 ? 1 : a.vz == 1 ? SH::ZG2 : SH::ZG;
-  const int grid = (int)((int64_t)N * N / (SH::LINES * zg));
-  auto go = [&](auto kern) {
-    ensure_smem(kern, smem);
-    kern<<<grid, SH::LINE_THREADS, smem, a.stream>>>((C*)a.W, (const C*)a.tw, (const typename A::T*)a.ktab, *a.kin,
-                                                      a.part);
-  };
-  if (zg == 1) {
-    if (a.stats) go(k_zpass<A, N, true, 1>);
-    else go(k_zpass<A, N, false, 1>);
-  } else if (zg == SH::ZG2) {
-    if (a.stats) go(k_zpass<A, N, true, SH::ZG2>);
-    else go(k_zpass<A, N, false, SH::ZG2>);
-  } else {
-    if (a.stats) go(k_zpass<A, N, true>);
-    else go(k_zpass<A, N, false>);
-  }
-  if (nblocks) *nblocks = grid;
-  return cudaGetLastError();
+  BatchZ b{};
+  b.W[0] = a.W;
+  b.tw[0] = a.tw;
+  b.ktab[0] = a.ktab;
+  b.part[0] = a.part;
+  b.kp[0] = *a.kin;
+  return zpass_batch(b, 1, a.stats, a.vz, a.stream, nblocks);
 }
 
 template <class A, int N>
@@ -135,65 +102,105 @@ cudaError_t Launch<A, N>::gs_dots(const LaunchArgs& a, int nblocks) {
 }
 
 template <class A, int N>
-cudaError_t Launch<A, N>::fft_y_batch(const BatchY& b, int count, int dir, cudaStream_t st) {
-  if constexpr (N > MAX_BATCH_N) {
-    return cudaErrorInvalidValue;
-  } else {
-    using SH = Shape<A, N>;
-    constexpr int yc = SH::YCOLS;
-    const size_t smem = (size_t)N * yc * sizeof(typename A::C);
+cudaError_t Launch<A, N>::fft_y_batch(const BatchY& b, int count, int dir, int vy, cudaStream_t st) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  auto go = [&](auto kern, int yc, int threads_per_col) {
+    const size_t smem = (size_t)N * yc * sizeof(C);
     const int tiles_inner = N / yc;
-    auto go = [&](auto kern) {
-      ensure_smem(kern, smem);
-      kern<<<dim3(N * tiles_inner, count), SH::T * yc, smem, st>>>(b, (int64_t)N, tiles_inner, (int64_t)N * N);
-    };
-    if (dir < 0) go(k_fft_strided_batch<A, N, -1>);
-    else go(k_fft_strided_batch<A, N, +1>);
-    return cudaGetLastError();
+    ensure_smem(kern, smem);
+    kern<<<dim3(N * tiles_inner, count), threads_per_col * yc, smem, st>>>(b, (int64_t)N, tiles_inner,
+                                                                          (int64_t)N * N);
+  };
+  if constexpr (SH::HAS_R1) {
+    if (vy == 2) {  // the two-stage radix schedule
+      if (dir < 0) go(k_fft_strided<A, N, -1, SH::YCOLS_R1, 1>, SH::YCOLS_R1, SH::T1);
+      else go(k_fft_strided<A, N, +1, SH::YCOLS_R1, 1>, SH::YCOLS_R1, SH::T1);
+      return cudaGetLastError();
+    }
   }
+  if (vy == 1) {
+    if (dir < 0) go(k_fft_strided<A, N, -1, SH::YCOLS2>, SH::YCOLS2, SH::T);
+    else go(k_fft_strided<A, N, +1, SH::YCOLS2>, SH::YCOLS2, SH::T);
+  } else {
+    if (dir < 0) go(k_fft_strided<A, N, -1, SH::YCOLS>, SH::YCOLS, SH::T);
+    else go(k_fft_strided<A, N, +1, SH::YCOLS>, SH::YCOLS, SH::T);
+  }
+  return cudaGetLastError();
 }
 
 template <class A, int N>
-cudaError_t Launch<A, N>::zpass_batch(const BatchZ& b, int count, cudaStream_t st) {
-  if constexpr (N > MAX_BATCH_N) {
-    return cudaErrorInvalidValue;
-  } else {
-    using SH = Shape<A, N>;
-    const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(typename A::C);
-    const int grid = (int)((int64_t)N * N / (SH::LINES * SH::ZG));
-    auto kern = k_zpass_batch<A, N>;
+cudaError_t Launch<A, N>::zpass_batch(const BatchZ& b, int count, int parseval, int vz, cudaStream_t st,
+                                      int* nblocks) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  if constexpr (SH::HAS_R1) {
+    if (vz == 2) {  // the two-stage radix schedule, one line group
+      const size_t smem = (size_t)SH::LINES_R1 * SH::LPAD * sizeof(C);
+      const int grid = (int)((int64_t)N * N / SH::LINES_R1);
+      auto go1 = [&](auto kern) {
+        ensure_smem(kern, smem);
+        kern<<<dim3(grid, count), SH::T1 * SH::LINES_R1, smem, st>>>(b);
+      };
+      if (parseval) go1(k_zpass<A, N, true, 1, 1>);
+      else go1(k_zpass<A, N, false, 1, 1>);
+      if (nblocks) *nblocks = grid;
+      return cudaGetLastError();
+    }
+  }
+  const size_t smem = (size_t)SH::LINES * SH::LPAD * sizeof(C);
+  // z-pass line groups: the policy's default, or the autotuner's 1 / 2
+  const int zg = vz == 0 ? 1 : vz == 1 ? SH::ZG2 : SH::ZG;
+  const int grid = (int)((int64_t)N * N / (SH::LINES * zg));
+  auto go = [&](auto kern) {
     ensure_smem(kern, smem);
     kern<<<dim3(grid, count), SH::LINE_THREADS, smem, st>>>(b);
-    return cudaGetLastError();
+  };
+  if (zg == 1) {
+    if (parseval) go(k_zpass<A, N, true, 1>);
+    else go(k_zpass<A, N, false, 1>);
+  } else {
+    if (parseval) go(k_zpass<A, N, true, SH::ZG2>);
+    else go(k_zpass<A, N, false, SH::ZG2>);
   }
+  if (nblocks) *nblocks = grid;
+  return cudaGetLastError();
 }
 
 template <class A, int N>
-cudaError_t Launch<A, N>::update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, cudaStream_t st,
-                                         int* nblocks) {
-  if constexpr (N > MAX_BATCH_N) {
-    return cudaErrorInvalidValue;
-  } else {
-    using SH = Shape<A, N>;
-    const size_t smem = (size_t)N * SH::XPITCH * sizeof(typename A::C);
-    const int grid = (int)((int64_t)N * N / SH::XCOLS);
-    auto go = [&](auto kern) {
-      ensure_smem(kern, smem);
-      kern<<<dim3(grid, count), SH::XTHREADS, smem, st>>>(b, scaled);
-    };
-    if (stats == STATS_NORM) go(k_update_x_batch<A, N, STATS_NORM>);
-    else go(k_update_x_batch<A, N, STATS_NONE>);
+cudaError_t Launch<A, N>::update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, int vx,
+                                         cudaStream_t st, int* nblocks) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  auto go = [&](auto kern, int xc) {
+    const size_t smem = (size_t)N * xc * sizeof(C);
+    const int grid = (int)((int64_t)N * N / xc);
+    ensure_smem(kern, smem);
+    kern<<<dim3(grid, count), SH::T * xc, smem, st>>>(b, scaled);
     if (nblocks) *nblocks = grid;
-    return cudaGetLastError();
+  };
+  if (vx == 1) {
+    constexpr int XC = SH::XCOLS2;
+    if (stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL, XC>, XC);
+    else if (stats == STATS_NORM) go(k_update_x<A, N, STATS_NORM, XC>, XC);
+    else go(k_update_x<A, N, STATS_NONE, XC>, XC);
+  } else {
+    constexpr int XC = SH::XCOLS;
+    if (stats == STATS_FULL) go(k_update_x<A, N, STATS_FULL, XC>, XC);
+    else if (stats == STATS_NORM) go(k_update_x<A, N, STATS_NORM, XC>, XC);
+    else go(k_update_x<A, N, STATS_NONE, XC>, XC);
   }
+  return cudaGetLastError();
 }
 
 template <class A, int N>
 int Launch<A, N>::partials() {
   using SH = Shape<A, N>;
-  const int x = (int)((int64_t)N * N / SH::XCOLS);
-  const int z = (int)((int64_t)N * N / SH::LINES);  // bounds the persistent z-pass grid too
-  return x > z ? x : z;
+  const int x = (int)((int64_t)N * N / SH::XCOLS2);  // pass A's half-width tiles
+  const int z1 = (int)((int64_t)N * N / SH::LINES_R1);  // the two-stage z pass
+  const int z = (int)((int64_t)N * N / SH::LINES);
+  const int m = x > z ? x : z;
+  return SH::HAS_R1 && z1 > m ? z1 : m;
 }
 
 }  // namespace qfd

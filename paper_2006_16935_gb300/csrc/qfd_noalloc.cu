@@ -18,7 +18,12 @@
 //
 // Set-up: the device address of the array is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
-// it; make that first call before any stream capture.
+// it; make that first call before any stream capture.  The address lives as
+// long as the device's context: after a cudaDeviceReset the entry point must
+// not be called again on that device in the same process.
+//
+// Only the FFT kinetic terms (kinetic 1..3) are accepted: the energy's
+// kinetic part is the Parseval sum of Eqs. (HK1)-(HK3).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,8 +50,7 @@ constexpr size_t OFF_PC = align_up(OFF_PA + 2 * MAX_PART * sizeof(double));
 constexpr size_t OFF_TW = align_up(OFF_PC + MAX_PART * sizeof(double));
 constexpr size_t OFF_KT = align_up(OFF_TW + NOALLOC_MAX_N * sizeof(double2));
 constexpr size_t OFF_SC = align_up(OFF_KT + NOALLOC_MAX_N * sizeof(double));
-constexpr size_t OFF_ERR = align_up(OFF_SC + 4 * sizeof(double));
-constexpr size_t SCRATCH_BYTES = align_up(OFF_ERR + sizeof(int));
+constexpr size_t SCRATCH_BYTES = align_up(OFF_SC + 4 * sizeof(double));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -157,11 +161,8 @@ extern "C" qfd_status qfd_energy_noalloc(const double* psi, const double* V, int
     return QFD_ERR_CUDA;
 
   if ((size_t)max_partials<F64>(n) > MAX_PART) return QFD_ERR_ARG;
-  int* errp = reinterpret_cast<int*>(base + OFF_ERR);
-  if (cudaMemsetAsync(errp, 0, sizeof(int), st) != cudaSuccess) return QFD_ERR_CUDA;
   LaunchArgs la;
   la.n = n;
-  la.err = errp;
   la.W = base + OFF_W;
   la.src = psi;
   la.V = V;
@@ -182,12 +183,9 @@ extern "C" qfd_status qfd_energy_noalloc(const double* psi, const double* V, int
                                        reinterpret_cast<const double*>(base + OFF_PC), nc, sc);
   if (cudaGetLastError() != cudaSuccess) return QFD_ERR_CUDA;
   double out[2];
-  int kerr = 0;
   if (cudaMemcpyAsync(out, sc, sizeof(out), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(&kerr, errp, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return QFD_ERR_CUDA;
-  if (kerr) return QFD_ERR_TIMEOUT;
   if (E) *E = out[0];
   if (norm2) *norm2 = out[1];
   return QFD_OK;

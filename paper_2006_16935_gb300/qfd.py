@@ -24,7 +24,7 @@ OK, ERR_ARG, ERR_OOM, ERR_UNSTABLE_DT, ERR_DIVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_
 STATUS_NAMES = {0: "QFD_OK", -1: "QFD_ERR_ARG", -2: "QFD_ERR_OOM", -3: "QFD_ERR_UNSTABLE_DT",
                 -4: "QFD_ERR_DIVERGED", -5: "QFD_ERR_TIMEOUT", -6: "QFD_ERR_CUDA",
                 -7: "QFD_ERR_NOT_CONVERGED", -8: "QFD_ERR_STATE"}
-PRECISION = {"c128": 0, "c64": 1, "c64_refine": 2, "df64": 3, "c64_refine_df": 4}
+PRECISION = {"c128": 0, "c64_refine": 1, "c64": 2, "df64": 3, "c64_refine_df": 4}
 CENTRE = {"grid": 0, "offgrid": 1}
 POTENTIAL = {"zero": 0, "ho": 1, "cornell": 2, "coulomb": 3, "softcoul": 4}
 STOP_RULE = {"paper": 0, "tail": 1}
@@ -50,7 +50,7 @@ class QfdParams(ctypes.Structure):
 class ServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("ortho_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("cohorts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -106,7 +106,7 @@ def load():
         "qfd_solve_states": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_set_limits": (I, [P, I64, D, D]),
         "qfd_autotune": (I, [P, ctypes.POINTER(D)]),
-        "qfd_set_tuning": (I, [P, I, I, I]),
+        "qfd_set_tuning": (I, [P, I, I, I, I]),
         "qfd_snapshot_states": (I, [P, I, I, I64, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
@@ -115,6 +115,7 @@ def load():
         "qfd_timing_reset": (I, [P]),
         "qfd_timing_query": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D)]),
         "qfd_launch_count": (I64, [P]),
+        "qfd_fma_rate": (I, [I, ctypes.POINTER(D)]),
         "qfd_get_stream": (P, [P]),
         "qfd_sync": (I, [P]),
         "qfd_energy_noalloc": (I, [P, P, I64, D, D, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -125,6 +126,8 @@ def load():
         "qfd_server_clock": (D, [P]),
         "qfd_server_submit": (I, [P, ctypes.POINTER(Request), ctypes.POINTER(I64)]),
         "qfd_server_poll": (I, [P, ctypes.POINTER(Result), I, ctypes.POINTER(I)]),
+        "qfd_server_set_timeout": (I, [P, D]),
+        "qfd_server_kernels": (I, [P, ctypes.POINTER(I64)]),
         "qfd_server_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I64),
                                  ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     }
@@ -147,6 +150,17 @@ def _ptr(arr, dtype):
         return arr.data_ptr(), int(arr.is_cuda), arr
     a = np.ascontiguousarray(arr, dtype=dtype)
     return a.ctypes.data, 0, a
+
+
+def fma_rate(fp64=True):
+    """qfd_fma_rate: measured FMA rate (TFLOP/s) of the FP64 (or FP32) pipe of
+    the current device."""
+    lib = load()
+    t = ctypes.c_double()
+    st = lib.qfd_fma_rate(int(bool(fp64)), ctypes.byref(t))
+    if st != OK:
+        raise QfdError(st, "qfd_fma_rate failed")
+    return t.value
 
 
 def energy_noalloc(psi, V, n, a, mass, kinetic, rest_mass=0, stream=None):
@@ -288,18 +302,21 @@ class Plan:
         return list(es), steps.value, st == OK
 
     def autotune(self):
-        """qfd_autotune; returns {policy: {"y": [default, wide], "z": [1 group, 2 groups]}} in ms."""
-        ms = (ctypes.c_double * 12)()
+        """qfd_autotune; returns {policy: {"y": [default, wide, two-stage radix],
+        "z": [1 group, 2 groups, two-stage radix], "x": [default, half width]}} in
+        ms (NaN where not timed: the two-stage schedule exists for complex64 at
+        n = 128..1024, "x" needs a potential)."""
+        ms = (ctypes.c_double * 24)()
         self._check(self.lib.qfd_autotune(self.h, ms))
         out = {}
         for pid, name in enumerate(("c128", "c64", "df64")):
-            v = list(ms[4 * pid:4 * pid + 4])
+            v = list(ms[8 * pid:8 * pid + 8])
             if not all(x != x for x in v):
-                out[name] = {"y": v[:2], "z": v[2:]}
+                out[name] = {"y": v[:3], "z": v[3:6], "x": v[6:8]}
         return out
 
-    def set_tuning(self, policy, y_variant, z_variant):
-        self._check(self.lib.qfd_set_tuning(self.h, int(policy), int(y_variant), int(z_variant)))
+    def set_tuning(self, policy, y_variant, z_variant, x_variant=0):
+        self._check(self.lib.qfd_set_tuning(self.h, int(policy), int(y_variant), int(z_variant), int(x_variant)))
 
     def set_limits(self, max_steps, tol, tol_bulk=None):
         tb = self.params.tol_bulk if tol_bulk is None else tol_bulk
@@ -372,10 +389,11 @@ class Server:
     """Continuous-batching request server of the C ABI (qfd_server_*)."""
 
     def __init__(self, hbm_budget_bytes, *, max_active=0, check_every=100, ortho_every=10, use_graphs=True,
-                 stream=None):
+                 stream=None, cohorts=False):
         self.lib = load()
         prm = ServerParams(hbm_budget_bytes=float(hbm_budget_bytes), max_active=max_active, check_every=check_every,
-                           ortho_every=ortho_every, use_graphs=int(use_graphs), stream=stream)
+                           ortho_every=ortho_every, use_graphs=int(use_graphs), stream=stream,
+                           cohorts=int(bool(cohorts)))
         h = ctypes.c_void_p()
         st = self.lib.qfd_server_create(ctypes.byref(prm), ctypes.byref(h))
         if st != OK:
@@ -425,6 +443,13 @@ class Server:
                         "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done})
         return out
 
+    def set_timeout(self, seconds):
+        """qfd_server_set_timeout: end a request whose period is still in flight
+        `seconds` after it was queued with QFD_ERR_TIMEOUT (0 turns it off)."""
+        st = self.lib.qfd_server_set_timeout(self.h, float(seconds))
+        if st != OK:
+            raise QfdError(st, self.lib.qfd_server_last_error(self.h).decode())
+
     def stats(self):
         w, a, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         per, rep, cap = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -432,8 +457,11 @@ class Server:
                                        ctypes.byref(rep), ctypes.byref(cap))
         if st != OK:
             raise QfdError(st, "qfd_server_stats failed")
+        k = ctypes.c_int64()
+        if self.lib.qfd_server_kernels(self.h, ctypes.byref(k)) != OK:
+            raise QfdError(st, "qfd_server_kernels failed")
         return {"waiting": w.value, "active": a.value, "used_bytes": u.value, "periods": per.value,
-                "graph_replays": rep.value, "graph_captures": cap.value}
+                "graph_replays": rep.value, "graph_captures": cap.value, "kernels": k.value}
 
     def run_until_done(self, n_expected, capacity=256):
         """Polls until n_expected results have come back; returns them by id."""

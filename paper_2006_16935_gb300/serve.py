@@ -88,7 +88,7 @@ def batch_stream(count: int, *, seed: int = 4, sizes=(64, 96, 128, 192), a: floa
 
 
 def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: int = 100, ortho_every: int = 10,
-          use_graphs: bool = True, stream_handle=None, max_active: int = 0):
+          use_graphs: bool = True, stream_handle=None, max_active: int = 0, cohorts: bool = False):
     """Offers `stream` (from poisson_stream) to a server in real time: each
     request is submitted once the server clock passes its arrival time; the
     loop polls until every result is back.  Returns (records, server stats);
@@ -97,7 +97,7 @@ def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: i
     recs = [None] * len(stream)
     ids = {}
     with qfd.Server(budget_bytes, check_every=check_every, ortho_every=ortho_every, use_graphs=use_graphs,
-                    stream=stream_handle, max_active=max_active) as sv:
+                    stream=stream_handle, max_active=max_active, cohorts=cohorts) as sv:
         t0 = sv.clock()
         nxt = 0
         got = 0
@@ -124,16 +124,29 @@ def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: i
     return recs, stats
 
 
-def summarize(recs):
+def summarize(recs, stats=None):
     """p50/p99/mean latency, solves/s (requests / time from the first arrival
-    to the last result) and site-updates/s of a serving run."""
+    to the last result), site-updates/s of a serving run, the same per lattice
+    size, and (given the server stats) kernel launches per imaginary-time
+    step of one lattice."""
     lat = np.array([r["latency"] for r in recs])
     first = min(r["arrival"] for r in recs)
     last = max(r["done"] for r in recs)
     span = last - first
     sites = sum(float(r["n"]) ** 3 * sum(r["steps"]) for r in recs)
-    return {"requests": len(recs), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "max_s": float(lat.max()), "makespan_s": span,
-            "solves_per_s": len(recs) / span, "site_updates_per_s": sites / span,
-            "ok": sum(1 for r in recs if r["status"] == 0),
-            "not_converged": sum(1 for r in recs if r["status"] == qfd.ERR_NOT_CONVERGED)}
+    out = {"requests": len(recs), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "mean_s": float(lat.mean()), "max_s": float(lat.max()), "makespan_s": span,
+           "solves_per_s": len(recs) / span, "site_updates_per_s": sites / span,
+           "ok": sum(1 for r in recs if r["status"] == 0),
+           "not_converged": sum(1 for r in recs if r["status"] == qfd.ERR_NOT_CONVERGED)}
+    per = {}
+    for n in sorted({r["n"] for r in recs}):
+        rs = [r for r in recs if r["n"] == n]
+        per[str(n)] = {"requests": len(rs), "site_updates_per_s": sum(float(n) ** 3 * sum(r["steps"]) for r in rs) / span,
+                       "p50_s": float(np.percentile([r["latency"] for r in rs], 50))}
+    out["per_size"] = per
+    if stats is not None:
+        steps = sum(sum(r["steps"]) for r in recs)
+        out["kernel_launches"] = stats.get("kernels")
+        out["launches_per_lattice_step"] = stats.get("kernels", 0) / max(1, steps)
+    return out

@@ -20,13 +20,15 @@ def test_fft_flop_count_of_the_radix_plan():
 
 def test_pass_bytes_match_the_lattices_each_pass_touches():
     b = bench.PASS_BYTES
-    # pass A: W, psi and the coefficients in, psi and W out
-    assert b["c128"]["update_x"] == 5 * 16 and b["c64"]["update_x"] == 5 * 8
+    # pass A: W and psi in, psi and W out, plus the per-site update input:
+    # {A, B dtau} (complex128, 16 B), V as a double-float pair (8 B), V in FP32 (4 B)
+    assert b["c128"]["update_x"] == 4 * 16 + 16
+    assert b["df64"]["update_x"] == 4 * 16 + 8
+    assert b["c64"]["update_x"] == 4 * 8 + 4
     for p in ("fwd_y", "z_kinetic", "inv_y"):
-        assert b["c128"][p] == 2 * 16 and b["c64"][p] == 2 * 8
-    assert b["df64"] is b["c128"]
-    step = sum(b["c128"][p] for p in ("update_x", "fwd_y", "z_kinetic", "inv_y"))
-    assert step == 176.0
+        assert b["c128"][p] == b["df64"][p] == 2 * 16 and b["c64"][p] == 2 * 8
+    step = {k: sum(b[k][p] for p in ("update_x", "fwd_y", "z_kinetic", "inv_y")) for k in b}
+    assert step == {"c128": 176.0, "df64": 168.0, "c64": 84.0}
 
 
 @pytest.mark.parametrize("prec", ["c128", "df64", "c64"])
@@ -34,28 +36,33 @@ def test_roofline_object(prec):
     per_pass = {"update_x": {"launches": 10, "total_ms": 150.0}, "fwd_y": {"launches": 10, "total_ms": 66.0},
                 "z_kinetic": {"launches": 10, "total_ms": 143.0}, "inv_y": {"launches": 10, "total_ms": 66.0}}
     peaks = {"hbm_gbs": 6800.0}
-    r = bench.roofline_for(prec, per_pass, peaks)
+    alu = {"fp64_tflops": 1.2, "fp32_tflops": 70.0, "source": "test"}
+    r = bench.roofline_for(prec, per_pass, peaks, alu)
     assert r["kernel"] == "update_x"
     sites = float(bench.N) ** 3
     assert r["avg_launch_ms"] == pytest.approx(15.0)
     assert r["algorithmic_bytes_per_launch"] == bench.PASS_BYTES[prec]["update_x"] * sites
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     if prec == "c128":
-        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == bench.FP64_PEAK_TFLOPS
+        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == 1.2
         assert r["achieved"] == pytest.approx(bench.pass_flops(bench.N)["update_x"] * sites / 15e-3 / 1e12)
     else:
         assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6800.0
         assert r["achieved"] == pytest.approx(bench.PASS_BYTES[prec]["update_x"] * sites / 15e-3 / 1e9)
-    assert r["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_SITE[(prec, "update_x")] * sites)
+    per_site = bench.DRAM_BYTES_PER_SITE.get((prec, "update_x"))
+    assert r["traffic"] == (pytest.approx(per_site * sites) if per_site else None)
     assert r["share_of_step"] == pytest.approx(150.0 / 425.0)
+    mb = bench.PASS_A_MIN_BYTES[prec]
+    assert r["hbm_frac_at_min_bytes"]["frac"] == pytest.approx(mb * sites / 15e-3 / 1e9 / 6800.0)
 
 
 def test_step_hbm_fraction():
+    # arithmetic only: a synthetic step time in, the design bytes over it out
     peaks = {"hbm_gbs": 6800.0}
     sites = float(bench.N) ** 3
-    r = bench.step_hbm("c64", 2.777, peaks)
-    assert r["bytes_per_site"] == 88.0
-    assert r["achieved_gbs"] == pytest.approx(88.0 * sites / 2.777e-3 / 1e9)
+    t_ms = 2.5  # synthetic input, not a measurement
+    r = bench.step_hbm("c64", t_ms, peaks)
+    per_site = sum(bench.PASS_BYTES["c64"][p] for p in ("update_x", "fwd_y", "z_kinetic", "inv_y"))
+    assert r["bytes_per_site"] == per_site
+    assert r["achieved_gbs"] == pytest.approx(per_site * sites / (t_ms * 1e-3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved_gbs"] / 6800.0)
-    assert 0.6 < r["frac"] < 0.65  # the measured complex64 step at 512^3
-    assert bench.step_hbm("c128", 44.1, peaks)["bytes_per_site"] == 176.0

@@ -1,12 +1,16 @@
-"""Full-size checks (the 512^3 softened-Coulomb lattice the benchmark times, and
-the 256^3 Cornell lattice of the excited-state workload), through the C ABI.
+"""Full-size checks (the 512^3 softened-Coulomb lattice the benchmark times, the
+1024^3 lattice of the largest solves, and the 256^3 Cornell lattice of the
+excited-state workload), through the C ABI.
 
 At these sizes the naive oracle is too slow for a whole lattice, so:
+  * at 512^3 and 256^3 a random psi is stepped by the oracle with its library
+    FFT (pinned against the naive DFT on CPU) and compared element by element
+    over the whole lattice, with the parity projection, the normalisation
+    cadence and the energy;
   * plane-wave superpositions are exact eigenvectors of every FFT kinetic
     term, so one step maps psi = sum_j c_j e^{i k_j.x} to
     A psi - B dtau sum_j c_j T(k_j) e^{i k_j.x}; the oracle's T and V give
-    that value site by site at sampled sites;
-  * at 256^3 a random psi is stepped by the oracle with its library FFT.
+    that value site by site at sampled sites (512^3 and 1024^3).
 """
 import numpy as np
 import pytest
@@ -74,11 +78,63 @@ def test_random_state_steps_256_against_library_fft_oracle(qfdlib, prec, tol):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("df64", 1e-11), ("c64", 3e-6)])
+# The 512^3 workload of the benchmark (softened Coulomb, H_K(2), dtau 5e-4) and
+# the relativistic term on the same lattice: the 512-point plans (radix 8.8.8,
+# two warps per line) are the ones the benchmark times.
+CASES_512 = {2: dict(a=0.05, m=1.0, dt=5e-4, seed=3), 3: dict(a=0.05, m=1.5, dt=1e-3, seed=4)}
+_ORACLE_512 = {}
+
+
+def oracle_512(kin):
+    """The oracle's 3 steps (ortho_every 2, even parity) and energy at 512^3,
+    library FFT on all host cores; cached per kinetic term.  The complex64 plan
+    starts from the same FP64 values rounded to complex64 (a relative change of
+    about 3e-8, well inside its tolerance)."""
+    key = kin
+    if key not in _ORACLE_512:
+        c = CASES_512[kin]
+        n = 512
+        V = O.potential(n, c["a"], "softcoul", (0.01,))
+        psi0 = inputs.uniform_psi(n, c["seed"])
+        prob = O.Problem(n, c["a"], c["m"], c["dt"], kin, V, ortho_every=2, method="library")
+        ref, _ = O.evolve(psi0, prob, 3, parity=1)
+        e_ref = O.energy(ref, V, prob.T, method="library")
+        _ORACLE_512.clear()  # keep one 512^3 case in host memory at a time
+        _ORACLE_512[key] = (psi0, ref, e_ref)
+    return _ORACLE_512[key]
+
+
+# "c64-r1": complex64 with the two-stage radix schedule (radix 32.16) in the y
+# and z passes and half-width pass-A tiles, the shapes the autotuner may pick
+@pytest.mark.parametrize("prec,tol,etol", [("c128", 1e-10, 1e-9), ("df64", 1e-10, 1e-9), ("c64", 2e-6, 2e-6),
+                                           ("c64-r1", 2e-6, 2e-6)])
+@pytest.mark.parametrize("kin", [2, 3])
+def test_random_state_steps_512_against_library_fft_oracle(qfdlib, kin, prec, tol, etol):
+    n = 512
+    c = CASES_512[kin]
+    psi0, ref, e_ref = oracle_512(kin)
+    two_stage = prec.endswith("-r1")
+    with Q.Plan(n, c["a"], c["m"], c["dt"], kin, precision=prec.replace("-r1", ""), ortho_every=2) as p:
+        if two_stage:
+            p.set_tuning(1, 2, 2, 1)
+        p.fill_potential("softcoul", (0.01,))
+        p.set_psi(0, psi0)
+        p.set_parity(0, 1)
+        p.step(0, 3)
+        got = p.get_psi(0)
+        e, _ = p.energy(0)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < tol, err
+    assert abs(e - e_ref) <= etol * abs(e_ref), (e, e_ref)
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("df64", 1e-11), ("c64", 3e-6), ("c64-r1", 3e-6)])
 def test_plane_wave_step_1024(qfdlib, prec, tol):
     # the largest lattice: 2^30 sites (17 GB per 16-byte lattice).  psi is built
-    # on the device with torch (slab by slab) and read back on the device; V = 0,
-    # so one step maps a plane wave to (1 - dtau T(k)) times itself
+    # on the device with torch (slab by slab) and read back on the device.  The
+    # potential is the softened Coulomb of the 1024^3 solves, so the update's
+    # site-dependent A and B are exercised: one step maps the plane-wave sum to
+    # A psi - B dtau sum_j c_j T(k_j) e^{i k_j.x}
     import torch
 
     n, a, m, kin, dt = 1024, 0.05, 1.0, 2, 2.5e-4
@@ -92,8 +148,10 @@ def test_plane_wave_step_1024(qfdlib, prec, tol):
         for s0 in range(0, n, 128):
             psi[s0:s0 + 128] += complex(c) * e[0][s0:s0 + 128, None, None] * yz[None, :, :]
         del yz
-    with Q.Plan(n, a, m, dt, kin, precision=prec, ortho_every=1000) as p:
-        p.fill_potential("zero", ())
+    with Q.Plan(n, a, m, dt, kin, precision=prec.replace("-r1", ""), ortho_every=1000) as p:
+        if prec.endswith("-r1"):  # the two-stage radix schedule (32.32) in the y and z passes
+            p.set_tuning(1, 2, 2, 1)
+        p.fill_potential("softcoul", (0.01,))
         p.set_psi(0, psi.view(-1))
         p.step(0, 1)
         p.get_psi(0, psi.view(-1))
@@ -101,11 +159,15 @@ def test_plane_wave_step_1024(qfdlib, prec, tol):
     rng = np.random.default_rng(1)
     sites = rng.integers(0, n, size=(4096, 3))
     sites[0] = [n - 1, n - 1, n - 1]
+    sites[1] = [n // 2, n // 2, n // 2]  # the potential's centre (V = -10)
+    sites[2] = [0, 0, 0]
     got = psi[sites[:, 0], sites[:, 1], sites[:, 2]].cpu().numpy()
     del psi
     T = O.kinetic_symbol_at(n, a, m, kin, idx)
+    V = O.potential_at(n, a, "softcoul", (0.01,), sites)
+    A_, B_ = O.update_coefficients(V, dt)
     phase = np.exp(2j * np.pi * (sites @ idx.T) / n)
-    expect = phase @ (amp * (1.0 - dt * T))
+    expect = A_ * (phase @ amp) - B_ * dt * (phase @ (amp * T))
     err = np.max(np.abs(got - expect)) / np.max(np.abs(expect))
     assert err < tol
 

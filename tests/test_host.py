@@ -108,4 +108,12 @@ def test_binding_struct_sizes_match_the_header():
     assert ctypes.sizeof(qfd.QfdParams) == 96
     assert ctypes.sizeof(qfd.Request) == 168 and qfd.Request.pot_coeffs.offset == 56
     assert ctypes.sizeof(qfd.Result) == 232
-    assert ctypes.sizeof(qfd.ServerParams) == 32
+    assert ctypes.sizeof(qfd.ServerParams) == 40 and qfd.ServerParams.cohorts.offset == 32
+
+
+def test_server_watchdog_and_fma_probe_reject_bad_arguments_without_a_gpu(lib):
+    # argument checks that run before any CUDA call
+    assert lib.qfd_server_set_timeout(None, 1.0) == qfd.ERR_ARG
+    assert lib.qfd_fma_rate(2, None) == qfd.ERR_ARG
+    t = ctypes.c_double()
+    assert lib.qfd_fma_rate(-1, ctypes.byref(t)) == qfd.ERR_ARG
