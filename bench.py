@@ -280,10 +280,16 @@ def time_precision(torch, Q, args, prec, dev, want_roofline):
 
 
 # DRAM read + write bytes per site of the dominant kernel, from an ncu capture
-# of a 256^3 launch of the same kernel (profile_step driver, DRAM counters);
-# traffic grows with the sites, so a 512^3 launch moves 512^3 times this.  An
-# entry is left out (traffic null) until the current kernel has been captured.
-DRAM_BYTES_PER_SITE = {}
+# of a 256^3 launch of the same kernel with the launch shape the autotuner picks
+# at 512^3 (profile_step driver, DRAM counters, two launches each:
+# profiles/update_x_dram_256.md); traffic grows with the sites, so a 512^3
+# launch moves 512^3 times this.  An entry is left out (traffic null) when the
+# kernel has changed since it was captured.
+DRAM_BYTES_PER_SITE = {
+    ("c128", "update_x"): (805.4e6 + 487.4e6) / 256 ** 3,
+    ("df64", "update_x"): (671.2e6 + 478.4e6) / 256 ** 3,
+    ("c64", "update_x"): (335.6e6 + 209.5e6) / 256 ** 3,
+}
 
 
 def step_hbm(prec, ms_per_imaginary_step, peaks):
@@ -382,11 +388,11 @@ def run_qfd(args):
     if world > 1:
         dist.barrier()
     peaks, peak_src = read_peaks()
-    alu_peaks = measure_alu_peaks(Q)
     prec = args.precision
 
     clocks = ClockSampler(local)
     clocks.start()
+    alu_peaks = measure_alu_peaks(Q)  # inside the clock record
     if world > 1:
         dist.barrier()
     plan, ms, steps, energy, launches, per_pass = time_precision(torch, Q, args, prec, dev, True)
@@ -473,15 +479,18 @@ def full_solves(torch, Q, dev, which, ms_step_c128=None, n=N):
         plan.tuning = plan.autotune()
         plan.fill_psi_uniform(0, SEED)
         torch.cuda.synchronize(dev)
+        clocks = ClockSampler(dev.index or 0)
+        clocks.start()
         t0 = time.perf_counter()
         es, steps, conv = plan.solve_states(1, [1], allow_unconverged=True)
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
+        clk = clocks.stop()
         hist = plan.history(0)
         out[prec] = {"n": n, "energy": es[0], "steps": steps[0], "converged": conv, "seconds": dt,
                      "solves_per_s": 1.0 / dt, "site_updates_per_s": float(n) ** 3 * steps[0] / dt,
                      "checks": len(hist), "tuning": plan.tuning if hasattr(plan, "tuning") else None,
-                     **plan.stats(0)}
+                     "clocks": clk, **plan.stats(0)}
         plan.close()
     ref = out.get("c128") or out.get("df64") or out.get("c64_refine")
     if ref:
