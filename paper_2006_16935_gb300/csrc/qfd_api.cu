@@ -2087,16 +2087,38 @@ qfd_status admit(qfd_server_t sv) {
       continue;
     }
     bool ok;
+    cudaStream_t setup = nullptr;  // cohort mode: a new member is set up on a stream of its own
     if (sv->p.cohorts) {
+      // the set-up synchronises its stream (derived coefficients are checked on
+      // the host); on the cohort's stream it would wait for the period in flight
       m->cohort = cohort_for(sv, m->req.n);
-      ok = m->cohort && (m->st = m->cohort->st) != nullptr && cudaStreamWaitEvent(m->st, sv->fork, 0) == cudaSuccess;
-      if (ok) m->cohort->members.push_back(m);
+      ok = m->cohort && cudaStreamCreateWithFlags(&setup, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaStreamWaitEvent(setup, sv->fork, 0) == cudaSuccess;
+      if (ok) {
+        m->st = setup;
+        m->cohort->members.push_back(m);
+      }
     } else {
       ok = cudaStreamCreateWithPriority(&m->st, cudaStreamNonBlocking, request_priority(sv, m->req.n)) == cudaSuccess &&
            cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) == cudaSuccess &&
            cudaStreamWaitEvent(m->st, sv->fork, 0) == cudaSuccess;
     }
+    // hands a cohort member's plan over from its set-up stream to the cohort's
+    auto join_cohort = [&]() -> qfd_status {
+      if (!setup) return QFD_OK;
+      cudaEvent_t ev = nullptr;
+      const bool good = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+                        cudaEventRecord(ev, setup) == cudaSuccess &&
+                        cudaStreamWaitEvent(m->cohort->st, ev, 0) == cudaSuccess;
+      if (ev) cudaEventDestroy(ev);
+      cudaStreamDestroy(setup);  // released once its queued work is done
+      setup = nullptr;
+      m->st = m->cohort->st;
+      if (m->plan) m->plan->st = m->st;
+      return good ? QFD_OK : QFD_ERR_CUDA;
+    };
     if (!ok) {
+      join_cohort();
       sv->waiting.pop_front();
       finish_request(sv, m, QFD_ERR_CUDA);
       release_request(m);
@@ -2109,6 +2131,7 @@ qfd_status admit(qfd_server_t sv) {
         auto& mem = m->cohort->members;
         mem.erase(std::remove(mem.begin(), mem.end(), m), mem.end());
         m->cohort = nullptr;
+        cudaStreamDestroy(setup);
       } else {
         cudaStreamDestroy(m->st);
         cudaEventDestroy(m->ev);
@@ -2126,6 +2149,8 @@ qfd_status admit(qfd_server_t sv) {
       for (int s = 0; r == QFD_OK && s < m->req.nstates; ++s) r = qfd_fill_psi_uniform(m->plan, s, m->req.seed + s);
       if (r == QFD_OK) r = start_state(m, 0);
     }
+    const qfd_status rj = join_cohort();
+    if (r == QFD_OK) r = rj;
     if (r != QFD_OK) {
       finish_request(sv, m, r);
       release_request(m);

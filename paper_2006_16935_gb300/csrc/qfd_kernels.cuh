@@ -636,9 +636,12 @@ __device__ __forceinline__ void fft_line(typename A::C (&v)[FftPlan<N, R>::E], i
 }
 
 // Shared-memory views. Tile of CW columns of a strided axis: [pos][col] with a
-// row pitch of PITCH >= CW elements.
-// The columns of a tile interleave across all warps of the CTA, so an exchange
-// synchronises the whole CTA.
+// row pitch of PITCH >= CW elements.  (Rows of 64 bytes take twice the
+// minimum shared-memory wavefronts in the first exchange, where each thread
+// writes its E outputs E rows apart; a padding row every E rows removes that
+// but was measured slower at 512^3, by the index arithmetic it adds to every
+// access, so the tiles are unpadded.)  The columns of a tile interleave across
+// all warps of the CTA, so an exchange synchronises the whole CTA.
 template <typename C, int CW, int PITCH> struct AccTile {
   C* sm;
   int col;
@@ -646,8 +649,10 @@ template <typename C, int CW, int PITCH> struct AccTile {
   __device__ __forceinline__ void sync() { __syncthreads(); }
 };
 // One contiguous line of T threads, padded by one element every 2^PS elements
-// (128 bytes).  Lines synchronise independently: a warp barrier when lines do
-// not straddle warps (T <= 32), else the named barrier 1 + line (T threads).
+// (128 bytes for the radix-8 schedule; every E elements for the two-stage one,
+// whose first exchange writes each thread's E outputs contiguously).  Lines
+// synchronise independently: a warp barrier when lines do not straddle warps
+// (T <= 32), else the named barrier 1 + line (T threads).
 template <typename C, int PS, int T> struct AccLine {
   C* sm;
   int line;
@@ -736,6 +741,8 @@ template <class A, int N> struct Shape {
   static constexpr int T1 = FftPlan<N, 1>::T;
   static constexpr int YCOLS_R1 = (128 / T1 < N ? 128 / T1 : N) > 1 ? (128 / T1 < N ? 128 / T1 : N) : 1;
   static constexpr int LINES_R1 = LTARGET / T1 > 1 ? LTARGET / T1 : 1;
+  static constexpr int PAD_SHIFT_R1 = ilog2c(FftPlan<N, 1>::E);
+  static constexpr int LPAD_R1 = N + (N >> PAD_SHIFT_R1);
   // one padding element per 128 bytes of a line
   static constexpr int PAD_SHIFT = WIDE ? 3 : 4;
   static constexpr int LPAD = N + (N >> PAD_SHIFT);
@@ -973,7 +980,9 @@ __device__ __forceinline__ void zpass_body(typename A::C* W, const typename A::C
 #pragma unroll
   for (int m = 0; m < PL::E; ++m) v[m] = W[line0 * N + t + m * PL::T];
   static_assert(PL::T <= 32 || LINES <= 15, "one named barrier per line");
-  AccLine<C, SH::PAD_SHIFT, PL::T> acc{sm + l * SH::LPAD, l};
+  constexpr int PS = R == 0 ? SH::PAD_SHIFT : SH::PAD_SHIFT_R1;
+  constexpr int LP = R == 0 ? SH::LPAD : SH::LPAD_R1;
+  AccLine<C, PS, PL::T> acc{sm + l * LP, l};
   typename A::Pars pacc;
 #pragma unroll
   for (int g = 0; g < ZG; ++g) {

@@ -105,11 +105,11 @@ template <class A, int N>
 cudaError_t Launch<A, N>::fft_y_batch(const BatchY& b, int count, int dir, int vy, cudaStream_t st) {
   using C = typename A::C;
   using SH = Shape<A, N>;
-  auto go = [&](auto kern, int yc, int threads_per_col) {
+  auto go = [&](auto kern, int yc, int tpc) {
     const size_t smem = (size_t)N * yc * sizeof(C);
     const int tiles_inner = N / yc;
     ensure_smem(kern, smem);
-    kern<<<dim3(N * tiles_inner, count), threads_per_col * yc, smem, st>>>(b, (int64_t)N, tiles_inner,
+    kern<<<dim3(N * tiles_inner, count), tpc * yc, smem, st>>>(b, (int64_t)N, tiles_inner,
                                                                           (int64_t)N * N);
   };
   if constexpr (SH::HAS_R1) {
@@ -136,7 +136,7 @@ cudaError_t Launch<A, N>::zpass_batch(const BatchZ& b, int count, int parseval, 
   using SH = Shape<A, N>;
   if constexpr (SH::HAS_R1) {
     if (vz == 2) {  // the two-stage radix schedule, one line group
-      const size_t smem = (size_t)SH::LINES_R1 * SH::LPAD * sizeof(C);
+      const size_t smem = (size_t)SH::LINES_R1 * SH::LPAD_R1 * sizeof(C);
       const int grid = (int)((int64_t)N * N / SH::LINES_R1);
       auto go1 = [&](auto kern) {
         ensure_smem(kern, smem);
