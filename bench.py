@@ -522,11 +522,12 @@ def serve_section(torch, Q, dev, count, sizes, precisions, cohorts=True):
     stream = S.poisson_stream(count, sizes=sizes, weights=[w[n] for n in sizes])
     out = {"requests": count, "arrivals": "Poisson, mean 20 req/s (seed 5)", "sizes": list(sizes),
            "spacing_a": stream[0][1]["a"], "tol": 1e-9, "stop_rule": "tail", "budget_gb": 150,
-           "check_every": 100, "ortho_every": 10, "cohorts": bool(cohorts), "arms": {}}
+           "check_every": 100, "ortho_every": 10, "cohorts": bool(cohorts),
+           "autotune": "launch shapes tuned once per lattice size and precision", "arms": {}}
     energies = {}
     for prec in precisions:
         torch.cuda.synchronize(dev)
-        recs, st = S.serve(stream, prec, cohorts=cohorts)
+        recs, st = S.serve(stream, prec, cohorts=cohorts, autotune=True)
         summ = S.summarize(recs, st)
         summ.update({"graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"],
                      "periods": st["periods"]})
@@ -564,13 +565,15 @@ def batch_section(torch, Q, dev, count, sizes, precision="c64_refine_df", max_st
     stream = S.batch_stream(count, sizes=sizes, max_steps=max_steps)
     out = {"solves": count, "sizes": list(sizes), "spacing_a": stream[0][1]["a"], "tol": 1e-9,
            "max_steps_per_state_and_phase": max_steps,
+           "autotune": "launch shapes tuned once per lattice size and precision (each mode's server tunes "
+                       "its own; identical energies across modes need the same choices)",
            "stop_rule": "tail", "precision": precision,
            "potential": "Cornell + Gaussian random field (corr 4 lattice units, std 0.05)", "modes": {}}
     energies = {}
     for mode in modes:
         max_active, cohorts = BATCH_MODES[mode]
         torch.cuda.synchronize(dev)
-        recs, st = S.serve(stream, precision, max_active=max_active, cohorts=cohorts)
+        recs, st = S.serve(stream, precision, max_active=max_active, cohorts=cohorts, autotune=True)
         summ = S.summarize(recs, st)
         summ.update({"graph_replays": st["graph_replays"], "graph_captures": st["graph_captures"]})
         out["modes"][mode] = summ
@@ -702,9 +705,10 @@ def main():
                     "(e.g. c64_refine_df,c64_refine,df64; minutes each)")
     ap.add_argument("--solve-n", type=int, default=N, help="lattice size of the --solve runs (512 or 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve", type=int, default=12, help="requests of the serving sample (0: none)")
-    ap.add_argument("--serve-sizes", default="64,128,256")
-    ap.add_argument("--serve-precisions", default="c64_refine_df,df64")
+    ap.add_argument("--serve", type=int, default=10, help="requests of the serving sample (0: none)")
+    ap.add_argument("--serve-sizes", default="64,128")
+    ap.add_argument("--serve-precisions", default="c64_refine_df,c64_refine,c128",
+                    help="arms of the serving sample; the first is the line's serving headline")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving sample")
     ap.add_argument("--serve-streams", action="store_true",
                     help="serve with a stream per request instead of lockstep cohorts")

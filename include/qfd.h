@@ -422,7 +422,10 @@ typedef struct {
   int32_t use_graphs;      /* 1: capture a request's period once per phase and replay it */
   void* stream;            /* cudaStream_t whose queued work admitted requests follow, or NULL */
   int32_t cohorts;         /* 1: lockstep cohorts of requests of one size (see above); 0: a stream per request */
-  int32_t reserved;        /* 0 */
+  int32_t autotune;        /* 1: the first request of each lattice size and precision runs qfd_autotune
+                              on its plan, and every later one of that kind takes the same launch
+                              shapes (so requests of one kind still give the same numbers in any
+                              mix within the server's life); 0: default shapes */
 } qfd_server_params;
 
 typedef struct {

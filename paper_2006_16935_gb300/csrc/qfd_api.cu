@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -1959,6 +1960,9 @@ struct qfd_server_s {
   cudaEvent_t fork = nullptr;  // admitted requests start after the server stream's work
   int prio_least = 0, prio_greatest = 0;
   double timeout_s = 0.0;  // watchdog on a period in flight (0: none)
+  // autotune = 1: launch shapes per (lattice size, precision), taken by the
+  // first plan of each and given to every later one (vy, vz, vx per policy)
+  std::vector<std::pair<std::pair<int64_t, int>, std::array<int, 9>>> shapes;
   int64_t periods = 0, replays = 0, captures = 0;
   int64_t kernels = 0;  // kernel launches queued, direct or in replayed graphs
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -2073,6 +2077,32 @@ void finish_request(qfd_server_t sv, ReqRun* m, qfd_status status) {
   sv->done.push_back(m->res);
 }
 
+// Launch shapes of a new request's plan when the server autotunes: those of
+// the first plan of the same lattice size and precision, which is tuned once
+// (qfd_autotune, before its states are filled).
+qfd_status server_shapes(qfd_server_t sv, qfd_plan_t pl) {
+  const std::pair<int64_t, int> key{pl->p.n, pl->p.precision};
+  for (auto& e : sv->shapes) {
+    if (e.first != key) continue;
+    for (int q = 0; q < 3; ++q) {
+      pl->tune_vy[q] = e.second[3 * q];
+      pl->tune_vz[q] = e.second[3 * q + 1];
+      pl->tune_vx[q] = e.second[3 * q + 2];
+    }
+    return QFD_OK;
+  }
+  qfd_status r = qfd_autotune(pl, nullptr);
+  if (r != QFD_OK) return r;
+  std::array<int, 9> v{};
+  for (int q = 0; q < 3; ++q) {
+    v[3 * q] = pl->tune_vy[q];
+    v[3 * q + 1] = pl->tune_vz[q];
+    v[3 * q + 2] = pl->tune_vx[q];
+  }
+  sv->shapes.push_back({key, v});
+  return QFD_OK;
+}
+
 qfd_status admit(qfd_server_t sv) {
   while (!sv->waiting.empty()) {
     if (sv->p.max_active > 0 && (int)sv->active.size() >= sv->p.max_active) break;
@@ -2144,6 +2174,7 @@ qfd_status admit(qfd_server_t sv) {
     if (r == QFD_OK) {
       const double c[2] = {m->req.pot_coeffs[0], m->req.pot_coeffs[1]};
       r = qfd_fill_potential(m->plan, m->req.potential, c, 2);
+      if (r == QFD_OK && sv->p.autotune) r = server_shapes(sv, m->plan);
       if (r == QFD_OK && m->req.grf_amplitude > 0)
         r = qfd_add_random_field(m->plan, m->req.grf_seed, m->req.grf_corr, m->req.grf_amplitude);
       for (int s = 0; r == QFD_OK && s < m->req.nstates; ++s) r = qfd_fill_psi_uniform(m->plan, s, m->req.seed + s);
@@ -2495,7 +2526,7 @@ qfd_status qfd_server_create(const qfd_server_params* params, qfd_server_t* out)
   if (out) *out = nullptr;
   if (!params || !out || !(params->hbm_budget_bytes > 0) || params->ortho_every < 1 || params->check_every < 1 ||
       params->check_every % params->ortho_every != 0 || params->max_active < 0 ||
-      (params->cohorts != 0 && params->cohorts != 1))
+      (params->cohorts != 0 && params->cohorts != 1) || (params->autotune != 0 && params->autotune != 1))
     return QFD_ERR_ARG;
   qfd_server_t sv = new qfd_server_s();
   sv->p = *params;

@@ -50,7 +50,7 @@ class QfdParams(ctypes.Structure):
 class ServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("ortho_every", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("cohorts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("cohorts", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -389,11 +389,11 @@ class Server:
     """Continuous-batching request server of the C ABI (qfd_server_*)."""
 
     def __init__(self, hbm_budget_bytes, *, max_active=0, check_every=100, ortho_every=10, use_graphs=True,
-                 stream=None, cohorts=False):
+                 stream=None, cohorts=False, autotune=False):
         self.lib = load()
         prm = ServerParams(hbm_budget_bytes=float(hbm_budget_bytes), max_active=max_active, check_every=check_every,
                            ortho_every=ortho_every, use_graphs=int(use_graphs), stream=stream,
-                           cohorts=int(bool(cohorts)))
+                           cohorts=int(bool(cohorts)), autotune=int(bool(autotune)))
         h = ctypes.c_void_p()
         st = self.lib.qfd_server_create(ctypes.byref(prm), ctypes.byref(h))
         if st != OK:

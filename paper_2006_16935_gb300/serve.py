@@ -88,7 +88,8 @@ def batch_stream(count: int, *, seed: int = 4, sizes=(64, 96, 128, 192), a: floa
 
 
 def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: int = 100, ortho_every: int = 10,
-          use_graphs: bool = True, stream_handle=None, max_active: int = 0, cohorts: bool = False):
+          use_graphs: bool = True, stream_handle=None, max_active: int = 0, cohorts: bool = False,
+          autotune: bool = False):
     """Offers `stream` (from poisson_stream) to a server in real time: each
     request is submitted once the server clock passes its arrival time; the
     loop polls until every result is back.  Returns (records, server stats);
@@ -97,7 +98,7 @@ def serve(stream, precision: str, *, budget_bytes: float = 150e9, check_every: i
     recs = [None] * len(stream)
     ids = {}
     with qfd.Server(budget_bytes, check_every=check_every, ortho_every=ortho_every, use_graphs=use_graphs,
-                    stream=stream_handle, max_active=max_active, cohorts=cohorts) as sv:
+                    stream=stream_handle, max_active=max_active, cohorts=cohorts, autotune=autotune) as sv:
         t0 = sv.clock()
         nxt = 0
         got = 0

@@ -185,3 +185,16 @@ def test_cohort_admission_respects_the_budget_and_the_watchdog_works(qfdlib):
         rid = sv.submit(Q.make_request(**big))
         assert sv.run_until_done(1)[rid]["status"] == Q.ERR_TIMEOUT
         assert sv.stats()["active"] == 0 and sv.stats()["used_bytes"] == 0
+
+
+def test_autotuning_server_gives_requests_of_one_kind_the_same_shapes(qfdlib):
+    # the first request of each (size, precision) is tuned; later ones take its
+    # shapes, so identical requests give identical numbers, alone or together
+    reqs = [COHORT_REQS[1], COHORT_REQS[7], COHORT_REQS[1], COHORT_REQS[7]]
+    with Q.Server(64e9, check_every=CHECK, ortho_every=ORTHO, cohorts=True, autotune=True) as sv:
+        ids = [sv.submit(Q.make_request(**r)) for r in reqs]
+        res = sv.run_until_done(len(ids))
+    got = [res[i] for i in ids]
+    assert all(r["status"] == 0 for r in got)
+    assert got[0]["energy"] == got[2]["energy"] and got[1]["energy"] == got[3]["energy"]
+    assert got[0]["steps"] == got[2]["steps"] and got[1]["steps"] == got[3]["steps"]

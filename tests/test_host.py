@@ -109,6 +109,7 @@ def test_binding_struct_sizes_match_the_header():
     assert ctypes.sizeof(qfd.Request) == 168 and qfd.Request.pot_coeffs.offset == 56
     assert ctypes.sizeof(qfd.Result) == 232
     assert ctypes.sizeof(qfd.ServerParams) == 40 and qfd.ServerParams.cohorts.offset == 32
+    assert qfd.ServerParams.autotune.offset == 36
 
 
 def test_server_watchdog_and_fma_probe_reject_bad_arguments_without_a_gpu(lib):
