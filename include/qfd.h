@@ -50,7 +50,8 @@ typedef enum {
   QFD_ERR_OOM = -2,           /* device allocation failed */
   QFD_ERR_UNSTABLE_DT = -3,   /* dtau * max T(k) >= 2, or 1 + dtau V/2 <= 0 somewhere */
   QFD_ERR_DIVERGED = -4,      /* energy or norm became non-finite */
-  QFD_ERR_TIMEOUT = -5,       /* a served request's period overran the server's watchdog (qfd_server_set_timeout) */
+  QFD_ERR_TIMEOUT = -5,       /* a bounded wait ran out: the server's period watchdog (qfd_server_set_timeout), or the
+                                 TMA-staged pass A giving up on its tile copies (see qfd_set_tuning) */
   QFD_ERR_CUDA = -6,          /* a CUDA call failed */
   QFD_ERR_NOT_CONVERGED = -7, /* max_steps reached before the tolerance */
   QFD_ERR_STATE = -8          /* call out of order (e.g. stepping before a potential is set) */
@@ -288,17 +289,18 @@ qfd_status qfd_snapshot_states(qfd_plan_t plan, int nout, int parity, int64_t sn
  * n = 128..1024 also both passes with the two-stage radix schedule (radix
  * 16.8, 16.16, 32.16 or 32.32 with 16 or 32 elements per thread: one
  * shared-memory exchange per transform instead of two or three), and (once a
- * potential is set, FFT kinetic terms) pass A with tiles of the default width
- * and of half of it at two CTAs per SM, on the work lattice and the spare
- * state lattice (5 launches each after 2 warm-ups), and keeps the fastest of
- * each for later launches.  Tilings do not change the arithmetic of a line;
+ * potential is set, FFT kinetic terms) pass A with tiles of the default width,
+ * of half of it at two CTAs per SM, and (complex64, n = 256..1024) the
+ * TMA-staged persistent kernel, on the work lattice and the spare state
+ * lattice (5 launches each after 2 warm-ups), and keeps the fastest of each
+ * for later launches.  Tilings do not change the arithmetic of a line;
  * the radix schedule changes the order of the operations of a transform.
  * Results agree to rounding whatever is chosen (complex128 / complex64
  * kernels may also differ in where the compiler fuses a multiply-add;
- * double-float tilings are bit-identical).  ms_out (NULL or 24 doubles): per
+ * double-float tilings are bit-identical).  ms_out (NULL or 27 doubles): per
  * policy (0 complex128, 1 complex64, 2 double-float) the median times of
- * y-default, y-wide, y-two-stage, z-1, z-2, z-two-stage, x-default, x-half in
- * ms (NaN where not timed).  Synchronises; the work lattice is recomputed at
+ * y-default, y-wide, y-two-stage, z-1, z-2, z-two-stage, x-default, x-half,
+ * x-TMA in ms (NaN where not timed).  Synchronises; the work lattice is recomputed at
  * the next step. */
 qfd_status qfd_autotune(qfd_plan_t plan, double* ms_out);
 
@@ -306,10 +308,31 @@ qfd_status qfd_autotune(qfd_plan_t plan, double* ms_out);
  * double-float) by hand: y_variant 0 default width, 1 twice it, 2 the
  * two-stage radix schedule; z_variant -1 the policy's default grouping, 0 one
  * line group, 1 two, 2 the two-stage radix schedule; x_variant 0 pass A's
- * default tile width, 1 half of it (two CTAs per SM).  The two-stage
- * schedule exists for complex64 at n = 128..1024; elsewhere 2 runs the
- * default schedule. */
+ * default tile width, 1 half of it (two CTAs per SM), 2 the TMA-staged
+ * persistent pass A.  The two-stage schedule exists for complex64 at
+ * n = 128..1024 and the TMA pass A for complex64 at n = 256..1024 (when the
+ * plan could build its tensor maps, qfd_has_tma); elsewhere 2 runs the default.
+ *
+ * The TMA-staged pass A runs one persistent CTA per SM; the Tensor Memory
+ * Accelerator copies the next tile's W, psi and V (2D tensor maps of the
+ * plan's lattices, boxes of 16, 8 or 4 sites by 256 rows) into shared memory
+ * while the current tile is transformed.  Its waits for those copies are
+ * bounded (about a second); when one runs out the kernel stops, the plan's
+ * error flag is set, and the next synchronising call (qfd_step, an energy,
+ * a solve's check) returns QFD_ERR_TIMEOUT.  The partial sums of a CTA cover
+ * several tiles, so sums and energies agree with the other widths to
+ * rounding. */
 qfd_status qfd_set_tuning(qfd_plan_t plan, int policy, int y_variant, int z_variant, int x_variant);
+
+/* Whether the plan holds the tensor maps of the TMA-staged pass A (1) or not (0). */
+int qfd_has_tma(qfd_plan_t plan);
+
+/* Test switch of the TMA-staged pass A (no counterpart in the paper):
+ * arm_without_copies = 1 arms its barriers without issuing any copy, so that
+ * every bounded wait runs out and the step reports QFD_ERR_TIMEOUT with no
+ * copy in flight; 0 restores normal operation.  The lattice contents are
+ * then undefined: set the states again. */
+qfd_status qfd_set_tma_test(qfd_plan_t plan, int arm_without_copies);
 
 /* Replaces the plan's max_steps, tol and tol_bulk (same meaning as in
  * qfd_params) for later qfd_solve_states calls. */

@@ -6,6 +6,7 @@
 // transforming psi again.  All arithmetic of the method runs in the kernels of
 // qfd_kernels.cuh and the small kernels below; the host only sequences
 // launches, sets up tables and takes the convergence decision.
+#include <cuda.h>  // CUtensorMap and the tensor-map encoder's signature (called through the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +16,7 @@
 #include <deque>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -420,7 +422,13 @@ struct qfd_plan_s {
   double* scal = nullptr;
   float* scalf = nullptr;  // the normalisation factor in FP32 and double-float form
   int* flag = nullptr;
-  double* hscal = nullptr;  // pinned host copy of the scalars
+  int* errflag = nullptr;   // set by a kernel whose bounded wait ran out (the TMA-staged pass A)
+  double* hscal = nullptr;  // pinned host copy of the scalars (+ the error flag)
+  // the TMA-staged pass A (complex64, n = 256..1024): device array of tensor
+  // maps, [0] W as complex64, [1] V in FP32, [2 + i] complex64 state buffer i;
+  // null when the variant is not available for the plan
+  CUtensorMap* tmaps = nullptr;
+  int tma_test = 0;  // 1: the TMA pass A arms its barriers without issuing copies
   // host-side state
   KinParams kin{};
   int tune_vy[3] = {0, 0, 0};     // launch shapes per policy id (autotuner; see LaunchArgs)
@@ -591,15 +599,37 @@ LaunchArgs base_args(qfd_plan_t pl) {
   a.stream = pl->st;
   a.vy = pl->tune_vy[A::id];
   a.vz = pl->tune_vz[A::id];
-  a.vx = pl->tune_vx[A::id];
+  a.vx = pl->tune_vx[A::id] == 2 && !(A::id == 1 && pl->tmaps) ? 0 : pl->tune_vx[A::id];
+  a.err = pl->errflag;
+  a.tma_test = pl->tma_test;
+  if (A::id == 1 && pl->tmaps) {
+    a.tmap[0] = pl->tmaps;
+    a.tmap[2] = pl->tmaps + 1;
+  }
   return a;
 }
 
 // Waits for the plan's stream; an error of any kernel queued on it surfaces
 // here as QFD_ERR_CUDA.
 qfd_status sync_checked(qfd_plan_t pl) {
+  int e = 0;
+  if (pl->tmaps) QFD_CK(cudaMemcpyAsync(&e, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
   QFD_CK(cudaStreamSynchronize(pl->st));
+  if (e) {
+    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
+    return fail(pl, QFD_ERR_TIMEOUT, "the TMA-staged pass A gave up waiting for its tile copies");
+  }
   return QFD_OK;
+}
+
+// The tensor map (device address) of the complex64 state lattice `p`, for the
+// TMA-staged pass A, or null.
+const void* psi_tmap(qfd_plan_t pl, const void* p) {
+  if (!pl->tmaps || !pl->psi32) return nullptr;
+  const size_t bytes = (size_t)pl->n3 * sizeof(float2);
+  const size_t off = (size_t)((const char*)p - (const char*)pl->psi32);
+  if (off % bytes != 0 || off / bytes > (size_t)pl->p.nstates) return nullptr;
+  return pl->tmaps + 2 + off / bytes;
 }
 
 qfd_status finalize(qfd_plan_t pl, const double* part, int nq, int count, int op) {
@@ -774,6 +804,7 @@ qfd_status step_once(qfd_plan_t pl, int s, int check) {
   } else {
     LaunchArgs a = base_args<A>(pl);
     a.psi = psi_of<A>(pl, s);
+    a.tmap[1] = psi_tmap(pl, a.psi);
     a.scale = pl->pending ? pl->scal + SC_SCALE : nullptr;
     a.scale_f = pl->scalf;
     a.part = pl->partA;
@@ -878,6 +909,7 @@ qfd_status period_launch(qfd_plan_t pl, int s, double* host) {
   }
   if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
   QFD_CK(cudaMemcpyAsync(host, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, pl->st));
+  QFD_CK(cudaMemcpyAsync(host + SC_COUNT, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, pl->st));
   return QFD_OK;
 }
 
@@ -908,6 +940,12 @@ struct PhaseTracker {
 qfd_status phase_check(qfd_plan_t pl, int s, const double* host, double tol, bool bulk, PhaseTracker& tr,
                        bool* done, double* e_out) {
   const double e = host[SC_E], n2 = host[SC_N2];
+  int kerr = 0;
+  std::memcpy(&kerr, host + SC_COUNT, sizeof(int));
+  if (kerr) {
+    cudaMemsetAsync(pl->errflag, 0, sizeof(int), pl->st);
+    return fail(pl, QFD_ERR_TIMEOUT, "the TMA-staged pass A gave up waiting for its tile copies");
+  }
   if (!std::isfinite(e) || !std::isfinite(n2) || !(n2 > 0))
     return fail(pl, QFD_ERR_DIVERGED, "energy or norm is not finite (time step or potential too large?)");
   pl->hist[s].push_back({pl->t[s], e});
@@ -1046,7 +1084,7 @@ int argmin(const double* ms, int k) {
 // two-stage radix schedule), the z-pass shapes (one or two line groups, and
 // the two-stage schedule) and both pass-A tile widths of policy A (pass A on
 // the work lattice and the spare state lattice, which hold nothing yet to be
-// kept) and keeps the fastest of each.  ms[0..2] y, ms[3..5] z, ms[6..7] x.
+// kept) and keeps the fastest of each.  ms[0..2] y, ms[3..5] z, ms[6..8] x.
 template <class A>
 qfd_status autotune_policy(qfd_plan_t pl, double* ms) {
   qfd_status r;
@@ -1066,16 +1104,18 @@ qfd_status autotune_policy(qfd_plan_t pl, double* ms) {
     if ((r = time_launch(pl, [&]() { return launch_zpass<A>(a, nullptr); }, 2, 5, &ms[3 + v])) != QFD_OK) return r;
   }
   if (pl->p.kinetic != 0 && pl->has_pot) {
-    for (int v = 0; v < 2; ++v) {
+    const int nxv = A::id == 1 && pl->tmaps ? 3 : 2;  // 2: the TMA-staged pass A
+    for (int v = 0; v < nxv; ++v) {
       LaunchArgs a = base_args<A>(pl);
       a.vx = v;
       a.psi = spare_of<A>(pl);
+      a.tmap[1] = psi_tmap(pl, a.psi);
       a.part = pl->partA;
       a.stats = STATS_NONE;
       if ((r = time_launch(pl, [&]() { return launch_update_x<A>(a, nullptr); }, 2, 5, &ms[6 + v])) != QFD_OK)
         return r;
     }
-    pl->tune_vx[A::id] = argmin(ms + 6, 2);
+    pl->tune_vx[A::id] = argmin(ms + 6, nxv);
   }
   pl->tune_vy[A::id] = argmin(ms, nv);
   pl->tune_vz[A::id] = argmin(ms + 3, nv);
@@ -1166,8 +1206,12 @@ template <class A>
 qfd_status batch_step_once(qfd_plan_s* const* pls, const int* ss, int count, int check, cudaStream_t st) {
   qfd_plan_t p0 = pls[0];
   const int64_t n = p0->p.n;
-  // launch shapes: plans[0]'s (the choice depends only on n and the arithmetic)
-  const int vy = p0->tune_vy[A::id], vz = p0->tune_vz[A::id], vx = p0->tune_vx[A::id];
+  // launch shapes: plans[0]'s (the choice depends only on n and the arithmetic);
+  // the TMA pass A needs every plan's tensor maps
+  const int vy = p0->tune_vy[A::id], vz = p0->tune_vz[A::id];
+  int vx = p0->tune_vx[A::id];
+  for (int i = 0; i < count && vx == 2; ++i)
+    if (!(A::id == 1 && pls[i]->tmaps)) vx = 0;
   qfd_status r;
   BatchY by{};
   BatchZ bz{};
@@ -1215,13 +1259,19 @@ qfd_status batch_step_once(qfd_plan_s* const* pls, const int* ss, int count, int
     b.scale_f[j] = pl->scalf;
     b.tw[j] = tw_of<A>(pl);
     b.part[j] = pl->partA;
+    b.err[j] = pl->errflag;
+    if (A::id == 1 && pl->tmaps) {
+      b.tmap[j][0] = pl->tmaps;
+      b.tmap[j][1] = psi_tmap(pl, b.psi[j]);
+      b.tmap[j][2] = pl->tmaps + 1;
+    }
     if (pl->pending) scaled[g] |= 1u << j;
   }
   int nb = 0;
   for (int g = 0; g < 3; ++g) {
     if (nu[g] == 0) continue;
     qfd_plan_t pl = p0;
-    QFD_RUN(PASS_UPDATE_X, launch_update_x_batch<A>(n, bu[g], nu[g], scaled[g], g, vx, st, &nb));
+    QFD_RUN(PASS_UPDATE_X, launch_update_x_batch<A>(n, bu[g], nu[g], scaled[g], g, vx, st, &nb, p0->tma_test));
   }
   // every plan's bookkeeping first, so that psi, W and the step counter
   // agree for all of them even if a later cadence fails
@@ -1295,11 +1345,67 @@ qfd_status batch_period_launch(qfd_plan_s* const* pls, const int* ss, int count,
     pl->w_stage = ST_C;
     if ((r = finalize(pl, pl->partC, 1, pl->nC, OP_ENERGY)) != QFD_OK) return r;
     QFD_CK(cudaMemcpyAsync(pl->hscal, pl->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QFD_CK(cudaMemcpyAsync(pl->hscal + SC_COUNT, pl->errflag, sizeof(int), cudaMemcpyDeviceToHost, st));
   }
   return QFD_OK;
 }
 
 }  // namespace
+
+// ------------------------------------------------ tensor maps (TMA pass A)
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+EncodeTiled tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// A lattice at `base` viewed as N rows (x) of N^2 sites (y, z) of elem_bytes
+// each; boxes of xt sites by min(N, 256) rows, no swizzle, no fill.
+bool encode_lattice_map(EncodeTiled enc, CUtensorMap* m, void* base, int64_t n, int elem_bytes, int xt) {
+  const cuuint64_t dims[2] = {(cuuint64_t)(n * n), (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)(n * n * elem_bytes)};
+  const cuuint32_t box[2] = {(cuuint32_t)xt, (cuuint32_t)(n < 256 ? n : 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return enc(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of the complex64 work lattice, V in FP32 and every complex64
+// state buffer (the spare included), copied to the device for the TMA pass A.
+bool build_tensor_maps(qfd_plan_t pl) {
+  const EncodeTiled enc = tensor_map_encoder();
+  const int xt = launch_tma_xt<F32>(pl->p.n);
+  if (!enc || xt <= 0 || !pl->psi32 || !pl->V32) return false;
+  const int64_t n = pl->p.n;
+  std::vector<CUtensorMap> maps((size_t)pl->p.nstates + 3);
+  bool ok = encode_lattice_map(enc, &maps[0], pl->W, n, 8, xt) && encode_lattice_map(enc, &maps[1], pl->V32, n, 4, xt);
+  for (int i = 0; ok && i <= pl->p.nstates; ++i)
+    ok = encode_lattice_map(enc, &maps[2 + i], (char*)pl->psi32 + (size_t)i * pl->n3 * sizeof(float2), n, 8, xt);
+  if (!ok) return false;
+  void* d = nullptr;
+  if (cudaMalloc(&d, maps.size() * sizeof(CUtensorMap)) != cudaSuccess) return false;
+  if (cudaMemcpy(d, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return false;
+  }
+  pl->tmaps = static_cast<CUtensorMap*>(d);
+  return true;
+}
 
 // ================================================================ C ABI
 extern "C" {
@@ -1418,6 +1524,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
       {(void**)&pl->scal, SC_COUNT * sizeof(double)},
       {(void**)&pl->scalf, 16 * sizeof(float)},
       {(void**)&pl->flag, sizeof(int)},
+      {(void**)&pl->errflag, sizeof(int)},
   };
   if (uses16(p.precision)) allocs.push_back({(void**)&pl->psi16, (size_t)(p.nstates + 1) * n3 * 16});
   if (uses32(p.precision)) allocs.push_back({(void**)&pl->psi32, (size_t)(p.nstates + 1) * n3 * sizeof(float2)});
@@ -1461,8 +1568,13 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
             cudaMemcpy(pl->ktabdf, ktdf.data(), n * sizeof(df), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(pl->scal, 0, SC_COUNT * sizeof(double)) == cudaSuccess;
   if (!ok) return cleanup_fail(QFD_ERR_CUDA, "table upload failed");
-  if (cudaHostAlloc((void**)&pl->hscal, SC_COUNT * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+  if (cudaHostAlloc((void**)&pl->hscal, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
     return cleanup_fail(QFD_ERR_OOM, "pinned host buffer allocation failed");
+  std::memset(pl->hscal, 0, (SC_COUNT + 1) * sizeof(double));
+  if (cudaMemset(pl->errflag, 0, sizeof(int)) != cudaSuccess) return cleanup_fail(QFD_ERR_CUDA, "memset failed");
+  // the TMA-staged pass A is optional: without the encoder or on failure the
+  // plan simply runs the direct kernels
+  if (needs_v32(p) && launch_tma_xt<F32>(n) > 0 && !build_tensor_maps(pl)) cudaGetLastError();
   *out = pl;
   return QFD_OK;
 }
@@ -1472,7 +1584,7 @@ void qfd_destroy(qfd_plan_t pl) {
   if (pl->st) cudaStreamSynchronize(pl->st);
   void* bufs[] = {pl->psi16, pl->psi32, pl->W,      pl->coef16, pl->coef32, pl->V,     pl->tw64,
                   pl->tw32,  pl->twdf,  pl->ktab64, pl->ktab32, pl->ktabdf, pl->partA, pl->partC,
-                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->Vdf, pl->V32};
+                  pl->partG, pl->scal,  pl->scalf, pl->flag, pl->Vdf, pl->V32, pl->errflag, pl->tmaps};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (pl->hscal) cudaFreeHost(pl->hscal);
@@ -1783,13 +1895,14 @@ qfd_status qfd_snapshot_states(qfd_plan_t pl, int nout, int parity, int64_t snap
 
 qfd_status qfd_autotune(qfd_plan_t pl, double* ms_out) {
   if (!pl) return QFD_ERR_ARG;
-  double ms[24];
+  double ms[27];
   for (double& m : ms) m = NAN;
   QFD_CK(cudaStreamSynchronize(pl->st));
   qfd_status r = QFD_OK;
-  if (uses32(pl->p.precision) && (r = autotune_policy<F32>(pl, ms + 8)) != QFD_OK) return r;
+  if (uses32(pl->p.precision) && (r = autotune_policy<F32>(pl, ms + 9)) != QFD_OK) return r;
   if (pl->psi16 && pl->arith16 == 0 && (r = autotune_policy<F64>(pl, ms + 0)) != QFD_OK) return r;
-  if (pl->psi16 && pl->arith16 == 2 && (r = autotune_policy<DF>(pl, ms + 16)) != QFD_OK) return r;
+  if (pl->psi16 && pl->arith16 == 2 && (r = autotune_policy<DF>(pl, ms + 18)) != QFD_OK) return r;
+  if ((r = sync_checked(pl)) != QFD_OK) return r;  // a TMA timing launch that gave up
   pl->w_stage = ST_NONE;  // W was used as the timing lattice
   pl->w_state = -1;
   if (ms_out) std::memcpy(ms_out, ms, sizeof(ms));
@@ -1799,13 +1912,22 @@ qfd_status qfd_autotune(qfd_plan_t pl, double* ms_out) {
 qfd_status qfd_set_tuning(qfd_plan_t pl, int policy, int y_variant, int z_variant, int x_variant) {
   if (!pl) return QFD_ERR_ARG;
   if (policy < 0 || policy > 2 || y_variant < 0 || y_variant > 2 || z_variant < -1 || z_variant > 2 ||
-      x_variant < 0 || x_variant > 1)
-    return fail(pl, QFD_ERR_ARG, "policy 0..2, y_variant 0..2, z_variant -1..2, x_variant 0..1");
+      x_variant < 0 || x_variant > 2)
+    return fail(pl, QFD_ERR_ARG, "policy 0..2, y_variant 0..2, z_variant -1..2, x_variant 0..2");
   pl->tune_vy[policy] = y_variant;
   pl->tune_vz[policy] = z_variant;
   pl->tune_vx[policy] = x_variant;
   return QFD_OK;
 }
+
+qfd_status qfd_set_tma_test(qfd_plan_t pl, int arm_without_copies) {
+  if (!pl) return QFD_ERR_ARG;
+  if (arm_without_copies != 0 && arm_without_copies != 1) return fail(pl, QFD_ERR_ARG, "0 or 1");
+  pl->tma_test = arm_without_copies;
+  return QFD_OK;
+}
+
+int qfd_has_tma(qfd_plan_t pl) { return pl && pl->tmaps ? 1 : 0; }
 
 qfd_status qfd_set_limits(qfd_plan_t pl, int64_t max_steps, double tol, double tol_bulk) {
   if (!pl) return QFD_ERR_ARG;

@@ -691,9 +691,6 @@ template <typename C, int PS, int T> struct AccLine {
 #ifndef QFD_YCOLS_MIN8
 #define QFD_YCOLS_MIN8 8
 #endif
-#ifndef QFD_EARLY_COEF16
-#define QFD_EARLY_COEF16 1
-#endif
 #ifndef QFD_TILE_TARGET
 #define QFD_TILE_TARGET 256
 #endif
@@ -910,6 +907,10 @@ struct BatchU {  // pass A
   const void* tw[MAX_BATCH];
   double* part[MAX_BATCH];
   UpdParams up[MAX_BATCH];
+  // the TMA-staged pass A (qfd_tma.cuh): device addresses of the tensor maps of
+  // W, psi and the update input, and the plan's error flag for bounded waits
+  const void* tmap[MAX_BATCH][3];
+  int* err[MAX_BATCH];
 };
 static_assert(sizeof(BatchZ) <= 4096 && sizeof(BatchU) <= 4096, "kernel parameter space");
 
@@ -1026,10 +1027,43 @@ __global__ void __launch_bounds__(FftPlan<N, R>::T * ZLines<A, N, R>::value) k_z
 // Pass A: inverse DFT_x of W gives H_K psi at the tile's sites; the update of
 // Eq. (iter_proced) with the coefficients of Sec. 2.2 (read precomputed for
 // complex128, derived from V in the FP32-pipe arithmetics), times an optional
-// normalisation factor *scale carried from the previous step; partial sums per
-// STATS; forward DFT_x of the new psi into W.  psi and the per-site update
-// input are loaded before the inverse transform so that their latency
-// overlaps it.  XC is the tile width (a launch-shape choice of the autotuner).
+// normalisation factor s carried from the previous step; partial sums per
+// STATS; forward DFT_x of the new psi into W.  The core takes a thread's
+// column of W, psi and the update input already in registers, so that the
+// direct kernel (loads from global memory) and the TMA-staged one (loads from
+// shared memory) run the same arithmetic code.  XC is the tile width.
+template <class A, int N, int STATS, int XC>
+__device__ __forceinline__ void update_x_core(typename A::C (&v)[FftPlan<N>::E], const typename A::C (&ps)[FftPlan<N>::E],
+                                              const typename A::U (&cf)[FftPlan<N>::E], int t, int col, int64_t base,
+                                              typename A::C* W, typename A::C* __restrict__ psi, const UpdParams& upar,
+                                              const typename A::VT* __restrict__ V, const double* __restrict__ scale,
+                                              const float* __restrict__ scale_f, const typename A::C* __restrict__ tw,
+                                              typename A::C* sm, typename A::Acc& nacc, typename A::Full& facc) {
+  using C = typename A::C;
+  using SH = Shape<A, N>;
+  constexpr int64_t S = (int64_t)N * N;
+  AccTile<C, XC, XC> acc{sm, col};
+  fft_line<A, N, +1>(v, t, tw, acc);
+  const bool scaled = scale != nullptr;
+  typename A::S s{};
+  if (scaled) s = A::load_scale(scale, scale_f);
+#pragma unroll
+  for (int m = 0; m < SH::E; ++m) {
+    const int64_t idx = base + (t + m * SH::T) * S;
+    C nw = A::update(ps[m], v[m], A::coef_from(cf[m], upar));
+    if (scaled) nw = cscale(nw, s);
+    psi[idx] = nw;
+    v[m] = nw;
+    if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
+    if constexpr (STATS == STATS_FULL) facc.add(nw, V[idx]);
+  }
+  fft_line<A, N, -1>(v, t, tw, acc);
+#pragma unroll
+  for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
+}
+
+// The direct pass A: psi and the per-site update input are loaded before the
+// inverse transform so that their latency overlaps it.
 template <class A, int N, int STATS, int XC>
 __device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* __restrict__ psi,
                                               const typename A::U* __restrict__ uin, const UpdParams& upar,
@@ -1044,42 +1078,17 @@ __device__ __forceinline__ void update_x_body(typename A::C* W, typename A::C* _
   const int col = threadIdx.x % XC, t = threadIdx.x / XC;
   const int64_t base = (int64_t)blockIdx.x * XC + col;
   constexpr int64_t S = (int64_t)N * N;
-  // psi (and, unless QFD_EARLY_COEF16 is 0 for 16-byte policies, the update
-  // input) are loaded before the inverse transform so that their latency
-  // overlaps it
-  constexpr bool EARLY_K = sizeof(C) == 8 || QFD_EARLY_COEF16;
   C v[SH::E], ps[SH::E];
-  U cf[EARLY_K ? SH::E : 1];
+  U cf[SH::E];
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) v[m] = W[base + (t + m * SH::T) * S];
 #pragma unroll
   for (int m = 0; m < SH::E; ++m) ps[m] = psi[base + (t + m * SH::T) * S];
-  if constexpr (EARLY_K) {
 #pragma unroll
-    for (int m = 0; m < SH::E; ++m) cf[m] = uin[base + (t + m * SH::T) * S];
-  }
-  AccTile<C, XC, XC> acc{sm, col};
-  fft_line<A, N, +1>(v, t, tw, acc);
-  const bool scaled = scale != nullptr;
-  typename A::S s{};
-  if (scaled) s = A::load_scale(scale, scale_f);
+  for (int m = 0; m < SH::E; ++m) cf[m] = uin[base + (t + m * SH::T) * S];
   typename A::Acc nacc;
   typename A::Full facc;
-#pragma unroll
-  for (int m = 0; m < SH::E; ++m) {
-    const int64_t idx = base + (t + m * SH::T) * S;
-    C nw;
-    if constexpr (EARLY_K) nw = A::update(ps[m], v[m], A::coef_from(cf[m], upar));
-    else nw = A::update(ps[m], v[m], A::coef_from(uin[idx], upar));
-    if (scaled) nw = cscale(nw, s);
-    psi[idx] = nw;
-    v[m] = nw;
-    if constexpr (STATS == STATS_NORM) nacc.add_norm(nw);
-    if constexpr (STATS == STATS_FULL) facc.add(nw, V[idx]);
-  }
-  fft_line<A, N, -1>(v, t, tw, acc);
-#pragma unroll
-  for (int m = 0; m < SH::E; ++m) W[base + (t + m * SH::T) * S] = v[m];
+  update_x_core<A, N, STATS, XC>(v, ps, cf, t, col, base, W, psi, upar, V, scale, scale_f, tw, sm, nacc, facc);
   if constexpr (STATS == STATS_NORM) norm_reduce_store<A>(nacc, part);
   if constexpr (STATS == STATS_FULL) full_store<A>(facc, part);
 }

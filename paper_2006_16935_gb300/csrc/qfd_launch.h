@@ -59,12 +59,20 @@ struct LaunchArgs {
   int offgrid = 0;             // reflection about the off-grid centre
   const double* sums = nullptr;  // overlaps (2 doubles per lower state)
   void* dst = nullptr;         // projected state output
-  // launch shapes (autotuner): y tiles of the default width (0) or twice it
-  // (1); z-pass line groups of the policy default (-1), 1 (0) or 2 (1); pass A
-  // tiles of the default width (0) or half of it with two CTAs per SM (1)
+  // launch shapes (autotuner): y tiles of the default width (0), twice it (1)
+  // or the two-stage radix schedule (2); z-pass line groups of the policy
+  // default (-1), 1 (0), 2 (1) or the two-stage schedule (2); pass A tiles of
+  // the default width (0), half of it with two CTAs per SM (1), or the
+  // TMA-staged persistent kernel (2)
   int vy = 0;
   int vz = -1;
   int vx = 0;
+  // the TMA-staged pass A: device addresses of the tensor maps of W, psi and
+  // the update input, the plan's error flag, and the test switch that arms
+  // its barriers without issuing copies
+  const void* tmap[3] = {};
+  int* err = nullptr;
+  int tma_test = 0;
 };
 
 // Each launcher returns cudaSuccess or the launch error; *nblocks receives the
@@ -85,7 +93,8 @@ template <class A, int N> struct Launch {
   static cudaError_t fft_y_batch(const BatchY& b, int count, int dir, int vy, cudaStream_t st);
   static cudaError_t zpass_batch(const BatchZ& b, int count, int parseval, int vz, cudaStream_t st, int* nblocks);
   static cudaError_t update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, int vx, cudaStream_t st,
-                                    int* nblocks);
+                                    int* nblocks, int tma_test = 0);
+  static int tma_xt();  // tile width of the TMA-staged pass A (vx = 2), 0 where it does not exist
 };
 
 template <int N> struct Tag {
@@ -138,9 +147,18 @@ cudaError_t launch_zpass_batch(int64_t n, const BatchZ& b, int count, int parsev
 }
 template <class A>
 cudaError_t launch_update_x_batch(int64_t n, const BatchU& b, int count, uint32_t scaled, int stats, int vx,
-                                  cudaStream_t st, int* nb) {
-  return dispatch_n(
-      n, [&](auto t) { return Launch<A, decltype(t)::value>::update_x_batch(b, count, scaled, stats, vx, st, nb); });
+                                  cudaStream_t st, int* nb, int tma_test = 0) {
+  return dispatch_n(n, [&](auto t) {
+    return Launch<A, decltype(t)::value>::update_x_batch(b, count, scaled, stats, vx, st, nb, tma_test);
+  });
+}
+template <class A> int launch_tma_xt(int64_t n) {
+  int out = 0;
+  dispatch_n(n, [&](auto t) {
+    out = Launch<A, decltype(t)::value>::tma_xt();
+    return cudaSuccess;
+  });
+  return out;
 }
 template <class A> int max_partials(int64_t n) {
   int out = 0;

@@ -4,6 +4,7 @@
 
 #include "qfd_kernels.cuh"
 #include "qfd_launch.h"
+#include "qfd_tma.cuh"
 
 namespace qfd {
 
@@ -27,7 +28,14 @@ cudaError_t Launch<A, N>::update_x(const LaunchArgs& a, int* nblocks) {
   b.tw[0] = a.tw;
   b.part[0] = a.part;
   if (a.up) b.up[0] = *a.up;
-  return update_x_batch(b, 1, a.scale ? 1u : 0u, a.stats, a.vx, a.stream, nblocks);
+  for (int j = 0; j < 3; ++j) b.tmap[0][j] = a.tmap[j];
+  b.err[0] = a.err;
+  return update_x_batch(b, 1, a.scale ? 1u : 0u, a.stats, a.vx, a.stream, nblocks, a.tma_test);
+}
+
+template <class A, int N>
+int Launch<A, N>::tma_xt() {
+  return TmaShape<A, N>::OK ? TmaShape<A, N>::XT : 0;
 }
 
 template <class A, int N>
@@ -169,9 +177,29 @@ cudaError_t Launch<A, N>::zpass_batch(const BatchZ& b, int count, int parseval, 
 
 template <class A, int N>
 cudaError_t Launch<A, N>::update_x_batch(const BatchU& b, int count, uint32_t scaled, int stats, int vx,
-                                         cudaStream_t st, int* nblocks) {
+                                         cudaStream_t st, int* nblocks, int tma_test) {
   using C = typename A::C;
   using SH = Shape<A, N>;
+  if constexpr (TmaShape<A, N>::OK) {
+    if (vx == 2) {  // the TMA-staged persistent pass A: one CTA per SM and lattice
+      using TS = TmaShape<A, N>;
+      int dev = 0, sms = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      constexpr int NT = N * N / TS::XT;
+      const int grid = sms < NT ? sms : NT;
+      auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::SMEM);
+        kern<<<dim3(grid, count), TS::THREADS, TS::SMEM, st>>>(b, scaled, tma_test);
+      };
+      if (stats == STATS_FULL) go(k_update_x_tma<A, N, STATS_FULL>);
+      else if (stats == STATS_NORM) go(k_update_x_tma<A, N, STATS_NORM>);
+      else go(k_update_x_tma<A, N, STATS_NONE>);
+      if (nblocks) *nblocks = grid;
+      return cudaGetLastError();
+    }
+  }
   auto go = [&](auto kern, int xc) {
     const size_t smem = (size_t)N * xc * sizeof(C);
     const int grid = (int)((int64_t)N * N / xc);

@@ -107,6 +107,8 @@ def load():
         "qfd_set_limits": (I, [P, I64, D, D]),
         "qfd_autotune": (I, [P, ctypes.POINTER(D)]),
         "qfd_set_tuning": (I, [P, I, I, I, I]),
+        "qfd_has_tma": (I, [P]),
+        "qfd_set_tma_test": (I, [P, I]),
         "qfd_snapshot_states": (I, [P, I, I, I64, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "qfd_get_history": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), I, ctypes.POINTER(I)]),
         "qfd_get_stats": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D)]),
@@ -305,15 +307,24 @@ class Plan:
         """qfd_autotune; returns {policy: {"y": [default, wide, two-stage radix],
         "z": [1 group, 2 groups, two-stage radix], "x": [default, half width]}} in
         ms (NaN where not timed: the two-stage schedule exists for complex64 at
-        n = 128..1024, "x" needs a potential)."""
-        ms = (ctypes.c_double * 24)()
+        n = 128..1024, the TMA pass A ("x"[2]) for complex64 at 256..1024, "x"
+        needs a potential)."""
+        ms = (ctypes.c_double * 27)()
         self._check(self.lib.qfd_autotune(self.h, ms))
         out = {}
         for pid, name in enumerate(("c128", "c64", "df64")):
-            v = list(ms[8 * pid:8 * pid + 8])
+            v = list(ms[9 * pid:9 * pid + 9])
             if not all(x != x for x in v):
-                out[name] = {"y": v[:3], "z": v[3:6], "x": v[6:8]}
+                out[name] = {"y": v[:3], "z": v[3:6], "x": v[6:9]}
         return out
+
+    def has_tma(self):
+        """qfd_has_tma: whether the TMA-staged pass A is available to this plan."""
+        return bool(self.lib.qfd_has_tma(self.h))
+
+    def set_tma_test(self, arm_without_copies):
+        """qfd_set_tma_test: 1 makes every bounded wait of the TMA pass A run out."""
+        self._check(self.lib.qfd_set_tma_test(self.h, int(arm_without_copies)))
 
     def set_tuning(self, policy, y_variant, z_variant, x_variant=0):
         self._check(self.lib.qfd_set_tuning(self.h, int(policy), int(y_variant), int(z_variant), int(x_variant)))

@@ -179,7 +179,7 @@ def test_batch_rejections_step_nothing(qfdlib):
         assert np.array_equal(p.get_psi(0), before)
 
 
-@pytest.mark.parametrize("vx", [0, 1])
+@pytest.mark.parametrize("vx", [0, 1, 2])
 def test_batch_of_one_512_lattice_equals_qfd_step(qfdlib, vx):
     # the benchmark's lattice size, through the batch entry point, with either
     # pass-A tile width: the same kernels as qfd_step, so the same bits

@@ -75,3 +75,29 @@ def test_server_watchdog_ends_an_overrunning_request_with_timeout(qfdlib):
         rid = sv.submit(quick)
         res = sv.run_until_done(1)
         assert res[rid]["status"] == Q.OK and np.isfinite(res[rid]["energy"][0])
+
+
+def test_tma_pass_a_bounded_wait_reports_timeout_and_recovers(qfdlib):
+    # the TMA-staged pass A with its barriers armed but no copy issued: every
+    # wait runs out (about a second), the kernel stops with no copy in flight,
+    # and the step reports QFD_ERR_TIMEOUT; afterwards the plan steps normally
+    n, a, m, dt = 256, 0.05, 1.0, 5e-4
+    psi0 = inputs.uniform_psi(n, 3)
+    with Q.Plan(n, a, m, dt, 2, precision="c64", ortho_every=2) as p, \
+            Q.Plan(n, a, m, dt, 2, precision="c64", ortho_every=2) as ref:
+        assert p.has_tma()
+        for q in (p, ref):
+            q.fill_potential("softcoul", (0.01,))
+        p.set_tuning(1, 0, -1, 2)
+        p.set_psi(0, psi0)
+        p.set_tma_test(1)
+        with pytest.raises(Q.QfdError) as ei:
+            p.step(0, 1)
+        assert ei.value.status == Q.ERR_TIMEOUT
+        p.set_tma_test(0)
+        p.set_psi(0, psi0)
+        p.step(0, 3)
+        ref.set_psi(0, psi0)
+        ref.step(0, 3)
+        got, want = p.get_psi(0), ref.get_psi(0)
+        assert np.linalg.norm(got - want) <= 2e-6 * np.linalg.norm(want)

@@ -105,18 +105,22 @@ def oracle_512(kin):
 
 
 # "c64-r1": complex64 with the two-stage radix schedule (radix 32.16) in the y
-# and z passes and half-width pass-A tiles, the shapes the autotuner may pick
+# and z passes and half-width pass-A tiles; "c64-tma": two-stage y passes,
+# two-group z pass and the TMA-staged pass A (shapes the autotuner may pick)
+TUNINGS = {"c64-r1": (1, 2, 2, 1), "c64-tma": (1, 2, 1, 2)}
+
+
 @pytest.mark.parametrize("prec,tol,etol", [("c128", 1e-10, 1e-9), ("df64", 1e-10, 1e-9), ("c64", 2e-6, 2e-6),
-                                           ("c64-r1", 2e-6, 2e-6)])
+                                           ("c64-r1", 2e-6, 2e-6), ("c64-tma", 2e-6, 2e-6)])
 @pytest.mark.parametrize("kin", [2, 3])
 def test_random_state_steps_512_against_library_fft_oracle(qfdlib, kin, prec, tol, etol):
     n = 512
     c = CASES_512[kin]
     psi0, ref, e_ref = oracle_512(kin)
-    two_stage = prec.endswith("-r1")
-    with Q.Plan(n, c["a"], c["m"], c["dt"], kin, precision=prec.replace("-r1", ""), ortho_every=2) as p:
-        if two_stage:
-            p.set_tuning(1, 2, 2, 1)
+    with Q.Plan(n, c["a"], c["m"], c["dt"], kin, precision=prec.split("-")[0], ortho_every=2) as p:
+        if prec in TUNINGS:
+            p.set_tuning(*TUNINGS[prec])
+            assert prec != "c64-tma" or p.has_tma()
         p.fill_potential("softcoul", (0.01,))
         p.set_psi(0, psi0)
         p.set_parity(0, 1)
@@ -149,8 +153,9 @@ def test_plane_wave_step_1024(qfdlib, prec, tol):
             psi[s0:s0 + 128] += complex(c) * e[0][s0:s0 + 128, None, None] * yz[None, :, :]
         del yz
     with Q.Plan(n, a, m, dt, kin, precision=prec.replace("-r1", ""), ortho_every=1000) as p:
-        if prec.endswith("-r1"):  # the two-stage radix schedule (32.32) in the y and z passes
-            p.set_tuning(1, 2, 2, 1)
+        if prec.endswith("-r1"):  # the two-stage radix schedule (32.32) in y and z, the TMA pass A
+            p.set_tuning(1, 2, 2, 2)
+            assert p.has_tma()
         p.fill_potential("softcoul", (0.01,))
         p.set_psi(0, psi.view(-1))
         p.step(0, 1)
