@@ -5,7 +5,7 @@
 
 Used as the target of ncu captures of single kernels on a lattice larger than
 L2 but small enough for a multi-pass capture.  --tuning y,z,x sets the launch
-shapes of the plan's step arithmetic (qfd_set_tuning: y 0..2, z -1..2, x 0..1)
+shapes of the plan's step arithmetic (qfd_set_tuning: y 0..2, z -1..2, x 0..2)
 so that a capture sees the variant the autotuner picks at full size.
 """
 from __future__ import annotations
