@@ -239,14 +239,15 @@ def workload_config(args, prec):
             "parallelism": f"replicas x{args.gpus}"}
 
 
-def time_precision(torch, Q, args, prec, dev, want_roofline):
+def time_precision(torch, Q, args, prec, dev, want_roofline, n=N):
     """The timed region: args.steps bench steps through qfd_solve_states with no
     per-launch instrumentation (CUDA events on the plan's stream, which is
     torch's current stream).  With want_roofline, a second run of the same
     length from the same start, with every launch bracketed by events, gives
-    the per-pass durations of the roofline; it is not part of the timed value."""
+    the per-pass durations of the roofline; it is not part of the timed value.
+    n: lattice size (the workload's other parameters unchanged)."""
     stream = torch.cuda.current_stream(dev)
-    plan = Q.Plan(N, A, MASS, DTAU, KIN, precision=prec, ortho_every=STEPS_PER_BENCH_STEP,
+    plan = Q.Plan(n, A, MASS, DTAU, KIN, precision=prec, ortho_every=STEPS_PER_BENCH_STEP,
                   check_every=STEPS_PER_BENCH_STEP, max_steps=STEPS_PER_BENCH_STEP * max(1, args.warmup), tol=-1,
                   stream=stream.cuda_stream)
     plan.fill_potential(*POT)
@@ -292,13 +293,13 @@ DRAM_BYTES_PER_SITE = {
 }
 
 
-def step_hbm(prec, ms_per_imaginary_step, peaks):
+def step_hbm(prec, ms_per_imaginary_step, peaks, n=N):
     """HBM roofline of the whole step: the design traffic of the four passes
     (update with the x transforms, y, z with T(k), y) per site times the
     sites, over the measured time of one imaginary-time step (cadence and
     energy-check work included in the time, not in the bytes)."""
     per_site = sum(PASS_BYTES[prec][p] for p in ("update_x", "fwd_y", "z_kinetic", "inv_y"))
-    gbs = per_site * float(N) ** 3 / (ms_per_imaginary_step / 1e3) / 1e9
+    gbs = per_site * float(n) ** 3 / (ms_per_imaginary_step / 1e3) / 1e9
     return {"bytes_per_site": per_site, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
             "frac": gbs / peaks["hbm_gbs"]}
 
@@ -452,17 +453,41 @@ def run_qfd(args):
                                       args.serve_precisions.split(","), cohorts=not args.serve_streams)
     if args.batched_step:
         line["batched_step"] = batched_step_section(torch, Q, dev)
+    if args.step_n:
+        line["step_at_n"] = steps_at_n(torch, Q, args, dev, args.step_n)
     if args.solve:
         c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
             others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
-        # the complex128 step time at another size: scaled by the sites and the
-        # transform length (5 N log2 N flops a line); stated as an estimate
-        scale = (args.solve_n / N) ** 3 * np.log2(args.solve_n) / np.log2(N)
-        line["solve"] = full_solves(torch, Q, dev, args.solve.split(","), c128_ms * scale, n=args.solve_n)
+        if args.solve_n != N and line.get("step_at_n", {}).get("n") == args.solve_n:
+            c128_ms = line["step_at_n"]["c128"]["ms_per_imaginary_step"]  # measured at that size
+        elif args.solve_n != N:
+            # the complex128 step time at another size: scaled by the sites and
+            # the transform length (5 N log2 N flops a line); an estimate
+            c128_ms *= (args.solve_n / N) ** 3 * np.log2(args.solve_n) / np.log2(N)
+        line["solve"] = full_solves(torch, Q, dev, args.solve.split(","), c128_ms, n=args.solve_n)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
     return 0
+
+
+def steps_at_n(torch, Q, args, dev, n):
+    """The bench step (10 imaginary steps, projection, normalisation and an
+    energy check) of every arithmetic at lattice size n, autotuned and timed
+    as the headline is (args.warmup untimed, args.steps timed, CUDA events),
+    with the clocks sampled over the three timed regions."""
+    out = {"n": n, "imaginary_steps_per_step": STEPS_PER_BENCH_STEP}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    for prec in ("c128", "df64", "c64"):
+        plan, ms, steps, energy, _, _ = time_precision(torch, Q, args, prec, dev, False, n=n)
+        tuning = plan.tuning
+        plan.close()
+        out[prec] = {"site_updates_per_s": float(n) ** 3 * steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "ms_per_imaginary_step": ms / steps, "energy_at_end": energy,
+                     "step_hbm": step_hbm(prec, ms / steps, read_peaks()[0], n=n), "autotune_ms": tuning}
+    out["clocks"] = clocks.stop()
+    return out
 
 
 def full_solves(torch, Q, dev, which, ms_step_c128=None, n=N):
@@ -704,6 +729,8 @@ def main():
     ap.add_argument("--solve", default="", help="comma list of precisions for full 1e-9 solves "
                     "(e.g. c64_refine_df,c64_refine,df64; minutes each)")
     ap.add_argument("--solve-n", type=int, default=N, help="lattice size of the --solve runs (512 or 1024)")
+    ap.add_argument("--step-n", type=int, default=0,
+                    help="also time the bench step of every arithmetic at this lattice size (e.g. 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=10, help="requests of the serving sample (0: none)")
     ap.add_argument("--serve-sizes", default="64,128")
