@@ -455,6 +455,9 @@ def run_qfd(args):
         line["batched_step"] = batched_step_section(torch, Q, dev)
     if args.step_n:
         line["step_at_n"] = steps_at_n(torch, Q, args, dev, args.step_n)
+    if args.c128_sample:
+        line["c128_solve_cadence"] = [c128_solve_cadence(torch, Q, dev, int(nk.split(":")[0]), int(nk.split(":")[1]))
+                                      for nk in args.c128_sample.split(",")]
     if args.solve:
         c128_ms = (ms / args.steps / STEPS_PER_BENCH_STEP) if prec == "c128" else \
             others["c128"]["ms_per_step"] / STEPS_PER_BENCH_STEP
@@ -488,6 +491,36 @@ def steps_at_n(torch, Q, args, dev, n):
                      "step_hbm": step_hbm(prec, ms / steps, read_peaks()[0], n=n), "autotune_ms": tuning}
     out["clocks"] = clocks.stop()
     return out
+
+
+def c128_solve_cadence(torch, Q, dev, n, steps):
+    """The complex128 step under a solve's own cadence (normalisation and
+    parity every 10 steps, an energy check every 100): `steps` steps of the
+    workload's ground-state solve at lattice size n with no early stop,
+    autotuned, timed with CUDA events after 100 untimed steps.  Gives the
+    per-step time for the native FP64 solve estimate (steps x this time)."""
+    stream = torch.cuda.current_stream(dev)
+    plan = Q.Plan(n, A, MASS, DTAU, KIN, precision="c128", ortho_every=10, check_every=100, max_steps=100, tol=-1,
+                  stream=stream.cuda_stream)
+    plan.fill_potential(*POT)
+    tuning = plan.autotune()
+    plan.fill_psi_uniform(0, SEED)
+    plan.solve_states(1, [1], allow_unconverged=True)
+    plan.set_limits(steps, -1)
+    plan.fill_psi_uniform(0, SEED)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, done, _ = plan.solve_states(1, [1], allow_unconverged=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    plan.close()
+    return {"n": n, "steps": done[0], "ms_per_step": ms / done[0],
+            "site_updates_per_s": float(n) ** 3 * done[0] / (ms / 1e3), "clocks": clk, "autotune_ms": tuning}
 
 
 def full_solves(torch, Q, dev, which, ms_step_c128=None, n=N):
@@ -731,6 +764,8 @@ def main():
     ap.add_argument("--solve-n", type=int, default=N, help="lattice size of the --solve runs (512 or 1024)")
     ap.add_argument("--step-n", type=int, default=0,
                     help="also time the bench step of every arithmetic at this lattice size (e.g. 1024)")
+    ap.add_argument("--c128-sample", default="",
+                    help="n:steps[,n:steps]: time native complex128 steps under a solve's cadence at size n")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=10, help="requests of the serving sample (0: none)")
     ap.add_argument("--serve-sizes", default="64,128")
