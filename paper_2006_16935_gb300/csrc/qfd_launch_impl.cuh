@@ -181,6 +181,10 @@ cudaError_t Launch<A, N>::update_x_batch(const BatchU& b, int count, uint32_t sc
   using C = typename A::C;
   using SH = Shape<A, N>;
   if constexpr (TmaShape<A, N>::OK) {
+    // the TMA variant needs every lattice's tensor maps and error flag: without
+    // them the default width runs
+    for (int i = 0; i < count && vx == 2; ++i)
+      if (!b.tmap[i][0] || !b.tmap[i][1] || !b.tmap[i][2] || !b.err[i]) vx = 0;
     if (vx == 2) {  // the TMA-staged persistent pass A: one CTA per SM and lattice
       using TS = TmaShape<A, N>;
       int dev = 0, sms = 0;
