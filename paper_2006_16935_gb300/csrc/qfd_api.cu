@@ -1180,7 +1180,7 @@ size_t plan_device_bytes(const qfd_params& p) {
   const size_t n = (size_t)p.n, n3 = n * n * n;
   const size_t npart = (size_t)std::max(
       std::max(std::max(max_partials<F64>(p.n), max_partials<F32>(p.n)), max_partials<DF>(p.n)), GS_BLOCKS);
-  size_t b = n3 * 16 + n3 * 8 + n * (16 + 8 + 16 + 8 + 4 + 8) + npart * 8 * (3 + 2 * MAX_LOWER) + 1024;
+  size_t b = n3 * 16 + n3 * 8 + n * (48 + 8 + 16 + 8 + 4 + 8) + npart * 8 * (3 + 2 * MAX_LOWER) + 1024;
   if (uses16(p.precision)) b += (size_t)(p.nstates + 1) * n3 * 16;
   if (uses32(p.precision)) b += (size_t)(p.nstates + 1) * n3 * 8;
   if (needs_coef16(p)) b += n3 * 16;
@@ -1512,7 +1512,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   std::vector<Alloc> allocs = {
       {(void**)&pl->W, (size_t)n3 * 16},
       {(void**)&pl->V, (size_t)n3 * sizeof(double)},
-      {(void**)&pl->tw64, (size_t)n * sizeof(double2)},
+      {(void**)&pl->tw64, (size_t)3 * n * sizeof(double2)},  // plain twiddles + the scaled radix-8 block
       {(void**)&pl->tw32, (size_t)n * sizeof(float2)},
       {(void**)&pl->twdf, (size_t)n * sizeof(dfc)},
       {(void**)&pl->ktab64, (size_t)n * sizeof(double)},
@@ -1546,7 +1546,7 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
   }
   pl->spare16 = pl->psi16 ? (char*)pl->psi16 + (size_t)p.nstates * n3 * 16 : nullptr;
   pl->spare32 = pl->psi32 ? (char*)pl->psi32 + (size_t)p.nstates * n3 * sizeof(float2) : nullptr;
-  std::vector<double2> tw(n);
+  std::vector<double2> tw(3 * n);
   std::vector<float2> tw32(n);
   std::vector<dfc> twdf(n);
   std::vector<float> kt32(n);
@@ -1560,7 +1560,8 @@ qfd_status qfd_plan(const qfd_params* params, qfd_plan_t* out) {
     kt32[e] = (float)ktab[e];
     ktdf[e] = host_split(ktab[e]);
   }
-  bool ok = cudaMemcpy(pl->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice) == cudaSuccess &&
+  scaled_twiddle_table(n, tw.data(), tw.data() + n);
+  bool ok = cudaMemcpy(pl->tw64, tw.data(), 3 * n * sizeof(double2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->tw32, tw32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->twdf, twdf.data(), n * sizeof(dfc), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(pl->ktab64, ktab.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&

@@ -545,6 +545,67 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft_smal
   if constexpr (RAD == 8) dft8<DIR>(x);
 }
 
+// Twiddled radix-8 butterfly of the complex128 stages with scaled twiddles
+// (the tangent form of Linzer and Feig).  Each twiddle is w_r = s_r q_r with
+// q_r = 1 + i tan(theta_r) where |cos| >= |sin|, else q_r = cot(theta_r) + i,
+// so |s_r| >= 1/sqrt 2 and |tan|, |cot| <= 1.  x_r q_r takes two FMAs, and the
+// real factors s_r enter, as ratios, the multiply-adds that replace the
+// DFT-8's additions: 70 FP64 operations a butterfly against 84 for seven
+// complex products and the DFT-8 (the FP64 pipe bounds the complex128 passes).
+// The host table after the N plain twiddles holds, per direction (forward,
+// then inverse) and e0 < N/8, eight double2: the form bits (bit r set: cot
+// form, stored as the low word of a double), tan or cot of w^r for r = 1..7,
+// s_1, s_2, s_4, s_3/s_1, s_5/s_1, s_6/s_2, s_7/s_3 and s_1/sqrt 2.
+__device__ __forceinline__ double neg_bits(double v) {  // -v by the sign bit (no FP64 operation)
+  return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+}
+__device__ __forceinline__ double2 rot_q(double2 a, double tc, bool cot) {
+  // tan form: (a.x - tc a.y, a.y + tc a.x); cot form: (tc a.x - a.y, tc a.y + a.x)
+  const double p = cot ? a.x : a.y, c = cot ? neg_bits(a.y) : a.x, tr = cot ? tc : neg_bits(tc);
+  const double m = cot ? a.y : a.x, d = cot ? a.x : a.y;
+  return double2{fma(tr, p, c), fma(tc, m, d)};
+}
+__device__ __forceinline__ double2 axpy2(double2 a, double s, double2 b) {  // a + s b
+  return double2{fma(s, b.x, a.x), fma(s, b.y, a.y)};
+}
+// (1 + DIR i) a: the additions of the multiplication by exp(DIR 2 pi i / 8) without 1/sqrt 2
+template <int DIR> __device__ __forceinline__ double2 w8_sum(double2 a) {
+  return DIR > 0 ? double2{a.x - a.y, a.x + a.y} : double2{a.x + a.y, a.y - a.x};
+}
+template <int DIR, int N>
+__device__ __forceinline__ void scaled_bfly8(double2 (&x)[8], const double2* __restrict__ tw, int e0) {
+  const double2* te = tw + N + (DIR < 0 ? 0 : N) + e0 * 8;
+  double2 q[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) q[i] = __ldg(te + i);
+  const int fl = __double2loint(q[0].x);
+  const double tc[8] = {0.0, q[0].y, q[1].x, q[1].y, q[2].x, q[2].y, q[3].x, q[3].y};
+  const double s1 = q[4].x, s2 = q[4].y, s4 = q[5].x, r13 = q[5].y, r15 = q[6].x, r26 = q[6].y, r37 = q[7].x,
+               kap = q[7].y;
+  double2 z[8];
+  z[0] = x[0];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) z[r] = rot_q(x[r], tc[r], (fl >> r) & 1);
+  // even inputs (z0, s2 z2, s4 z4, s2 r26 z6): DFT-4 with s2 folded in
+  const double2 s0 = axpy2(z[0], s4, z[4]), d0 = axpy2(z[0], -s4, z[4]);
+  const double2 s1p = axpy2(z[2], r26, z[6]), d1p = mul_i<DIR>(axpy2(z[2], -r26, z[6]));
+  const double2 E0 = axpy2(s0, s2, s1p), E2 = axpy2(s0, -s2, s1p);
+  const double2 E1 = axpy2(d0, s2, d1p), E3 = axpy2(d0, -s2, d1p);
+  // odd inputs over s1: (z1, r13 z3, r15 z5, r13 r37 z7)
+  const double2 t0 = axpy2(z[1], r15, z[5]), u0 = axpy2(z[1], -r15, z[5]);
+  const double2 t1 = axpy2(z[3], r37, z[7]), u1 = mul_i<DIR>(axpy2(z[3], -r37, z[7]));
+  const double2 O0 = axpy2(t0, r13, t1), O2 = mul_i<DIR>(axpy2(t0, -r13, t1));
+  const double2 O1 = w8_sum<DIR>(axpy2(u0, r13, u1)), O3 = mul_i<DIR>(w8_sum<DIR>(axpy2(u0, -r13, u1)));
+  x[0] = axpy2(E0, s1, O0);
+  x[4] = axpy2(E0, -s1, O0);
+  x[2] = axpy2(E2, s1, O2);
+  x[6] = axpy2(E2, -s1, O2);
+  x[1] = axpy2(E1, kap, O1);
+  x[5] = axpy2(E1, -kap, O1);
+  x[3] = axpy2(E3, kap, O3);
+  x[7] = axpy2(E3, -kap, O3);
+}
+
 // One Stockham stage on the register-resident canonical set v[m] = x[t + m N/E].
 // Butterfly b = t + u N/E (u < E/RAD) takes x[b + r N/RAD] = v[u + r (E/RAD)],
 // multiplies input r by w_N^{(b mod NS) r N/(NS RAD)}, and applies DFT_RAD.
@@ -558,11 +619,20 @@ __device__ __forceinline__ void stage_compute(typename A::C (&v)[FftPlan<N, R>::
   using C = typename A::C;
   constexpr int E = FftPlan<N, R>::E;
   constexpr int NB = E / RAD;
+  // complex128 twiddled radix-8 stages: the scaled-twiddle butterfly
+  constexpr bool SCALED = A::id == 0 && RAD == 8 && NS > 1 && R == 0;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     C x[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) x[r] = v[u + r * NB];
+    if constexpr (SCALED) {
+      const int b = t + u * (N / E);
+      scaled_bfly8<DIR, N>(x, tw, (b % NS) * (N / (NS * RAD)));
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) v[u + r * NB] = x[r];
+      continue;
+    }
     if (NS > 1) {
       const int b = t + u * (N / E);
       const int e0 = (b % NS) * (N / (NS * RAD));

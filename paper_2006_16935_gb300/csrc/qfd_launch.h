@@ -9,7 +9,47 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <cstring>
+
 namespace qfd {
+
+// The scaled twiddles of the complex128 radix-8 stages (scaled_bfly8 in
+// qfd_kernels.cuh), built from the plain table tw[e] = exp(-2 pi i e / n):
+// 2 n double2 (forward block, then inverse), each e0 < n / 8 eight double2.
+// The complex128 twiddle table of a lattice is tw followed by this block.
+// Quotients are formed in long double and rounded once.
+inline void scaled_twiddle_table(int64_t n, const double2* tw, double2* out) {
+  using LD = long double;
+  for (int d = 0; d < 2; ++d)
+    for (int64_t e0 = 0; e0 < n / 8; ++e0) {
+      double sig[8] = {1.0, 0, 0, 0, 0, 0, 0, 0}, tc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int64_t bits = 0;
+      for (int r = 1; r < 8; ++r) {
+        const double2 w = tw[(e0 * r) % n];
+        const double c = w.x, sn = d == 0 ? w.y : -w.y;
+        if (std::fabs(c) >= std::fabs(sn)) {  // w = c (1 + i sn/c)
+          sig[r] = c;
+          tc[r] = (double)((LD)sn / (LD)c);
+        } else {  // w = sn (c/sn + i)
+          sig[r] = sn;
+          tc[r] = (double)((LD)c / (LD)sn);
+          bits |= (int64_t)1 << r;
+        }
+      }
+      double fl;
+      std::memcpy(&fl, &bits, sizeof(fl));
+      double2* q = out + d * n + e0 * 8;
+      q[0] = double2{fl, tc[1]};
+      q[1] = double2{tc[2], tc[3]};
+      q[2] = double2{tc[4], tc[5]};
+      q[3] = double2{tc[6], tc[7]};
+      q[4] = double2{sig[1], sig[2]};
+      q[5] = double2{sig[4], (double)((LD)sig[3] / (LD)sig[1])};
+      q[6] = double2{(double)((LD)sig[5] / (LD)sig[1]), (double)((LD)sig[6] / (LD)sig[2])};
+      q[7] = double2{(double)((LD)sig[7] / (LD)sig[3]), (double)((LD)sig[1] * 0.70710678118654752440084436210485L)};
+    }
+}
 
 struct KinParams;
 struct UpdParams;

@@ -48,7 +48,7 @@ constexpr size_t MAX_PART = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N;  // >= CTAs o
 constexpr size_t OFF_PA = align_up(OFF_W + SZ_W);                   // 2 partials per CTA (norm, <V>)
 constexpr size_t OFF_PC = align_up(OFF_PA + 2 * MAX_PART * sizeof(double));
 constexpr size_t OFF_TW = align_up(OFF_PC + MAX_PART * sizeof(double));
-constexpr size_t OFF_KT = align_up(OFF_TW + NOALLOC_MAX_N * sizeof(double2));
+constexpr size_t OFF_KT = align_up(OFF_TW + 3 * NOALLOC_MAX_N * sizeof(double2));  // + the scaled block
 constexpr size_t OFF_SC = align_up(OFF_KT + NOALLOC_MAX_N * sizeof(double));
 constexpr size_t SCRATCH_BYTES = align_up(OFF_SC + 4 * sizeof(double));
 
@@ -134,7 +134,7 @@ extern "C" qfd_status qfd_energy_noalloc(const double* psi, const double* V, int
   cudaStream_t st = (cudaStream_t)stream;
 
   // per-axis tables of Eqs. (HK1)-(HK3) and the twiddles, copied into the array
-  double2 tw[NOALLOC_MAX_N];
+  double2 tw[3 * NOALLOC_MAX_N];
   double kt[NOALLOC_MAX_N];
   for (int64_t j = 0; j < n; ++j) {
     double c, s;
@@ -156,7 +156,8 @@ extern "C" qfd_status qfd_energy_noalloc(const double* psi, const double* V, int
   kin.am2 = (a * mass) * (a * mass);
   kin.inv_a_n3 = 1.0 / (a * n3d);
   kin.m0_n3 = rest_mass ? 0.0 : mass / n3d;
-  if ((err = cudaMemcpyAsync(base + OFF_TW, tw, n * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+  scaled_twiddle_table(n, tw, tw + n);
+  if ((err = cudaMemcpyAsync(base + OFF_TW, tw, 3 * n * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (err = cudaMemcpyAsync(base + OFF_KT, kt, n * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return QFD_ERR_CUDA;
 
