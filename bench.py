@@ -287,7 +287,7 @@ def time_precision(torch, Q, args, prec, dev, want_roofline, n=N):
 # launch moves 512^3 times this.  An entry is left out (traffic null) when the
 # kernel has changed since it was captured.
 DRAM_BYTES_PER_SITE = {
-    ("c128", "update_x"): (805.4e6 + 485.5e6) / 256 ** 3,
+    ("c128", "update_x"): (805.4e6 + 485.3e6) / 256 ** 3,
     ("df64", "update_x"): (671.3e6 + 477.1e6) / 256 ** 3,
     ("c64", "update_x"): (335.6e6 + 208.2e6) / 256 ** 3,
 }
